@@ -1,0 +1,311 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things other than itself: the values the paper
+prints for its worked example and for code counts, closed-form space
+overheads, a pointer-based tree built by recursion on the sequence, pure-Python
+definitions of access/rank/select, the textbook invariants, and a second
+algorithm for the codes (Algorithm 3 against the recursive split).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _ceil_lg(x):
+    return 0 if x <= 1 else int(x - 1).bit_length()
+
+
+# --------------------------------------------------------------------------
+# codes (Section 5.1, Algorithm 3)
+# --------------------------------------------------------------------------
+
+def test_alg3_matches_recursive_split():
+    for sigma in range(1, 5001):
+        c1, l1, L1 = oracle.codes_split(sigma)
+        c2, l2, L2 = oracle.codes_alg3(sigma)
+        assert L1 == L2 == _ceil_lg(sigma), sigma
+        assert np.array_equal(c1, c2), sigma
+        assert np.array_equal(l1, l2), sigma
+
+
+@pytest.mark.parametrize("sigma", list(range(1, 300)) + [1000, 4095, 4097, 65535, 65536, 96, (1 << 20) - 3])
+def test_code_properties(sigma):
+    code, ln, L = oracle.codes_split(sigma)
+    code = code[:sigma].astype(object)
+    ln = ln[:sigma].astype(int)
+    assert L == _ceil_lg(sigma)
+    if sigma == 1:
+        assert ln[0] == 0
+        return
+    # lengths never increase with the symbol (Section 5.1)
+    assert all(ln[s] >= ln[s + 1] for s in range(sigma - 1))
+    # every internal node has two children: Kraft sum is exactly one
+    assert sum(2 ** (L - int(x)) for x in ln) == 2 ** L
+    # codes are strictly increasing and prefix-free as left-aligned values
+    for s in range(sigma - 1):
+        assert code[s] + 2 ** (L - ln[s]) <= code[s + 1]
+    if sigma & (sigma - 1) == 0:
+        assert all(int(code[s]) == s for s in range(sigma)) and all(x == L for x in ln)
+
+
+def test_shorter_code_counts_from_paper():
+    facts = _golden("paper_facts.json")["shorter_code_counts"]
+    for k, expected in facts.items():
+        if k.startswith("_"):
+            continue
+        sigma = int(k)
+        _, ln, L = oracle.codes_split(sigma)
+        assert int((ln[:sigma] < L).sum()) == expected, sigma
+
+
+# --------------------------------------------------------------------------
+# worked example of Sections 5.2-5.4
+# --------------------------------------------------------------------------
+
+def test_worked_example():
+    g = _golden("worked_example.json")
+    alpha = g["alphabet"]
+    S = np.array([alpha.index(ch) for ch in g["text"]], np.uint8)
+    sigma = len(alpha)
+    t = oracle.O2Tree(S, sigma, K=2)
+    o1 = oracle.O1(S, sigma)
+    C = t.export(oracle.EXPORT_C)
+
+    # levels equal the pointer-based tree concatenated level by level
+    ref = brute.pointer_tree_levels(list(S), sigma)
+    assert t.L == len(ref) == 2
+    for l in range(t.L):
+        assert list(t.bits(l)) == ref[l]
+
+    a = g["access"]
+    i = a["i"]
+    assert t.access([i])[0] == alpha.index(a["answer"]) == o1.access([i])[0]
+    assert t.bits(0)[i] == 1  # goes right at the root
+    i1 = t.rank_b(0, 1, i) - t.rank_b(0, 1, int(C[0]))
+    assert i1 == a["level1_index_in_node"]
+    node1 = int(C[2])  # right child of the root starts at symbol c
+    assert t.bits(1)[node1 + i1] == a["level1_bit"]
+
+    r = g["rank"]
+    c = alpha.index(r["c"])
+    after0 = r["i"] - (t.rank_b(0, 0, r["i"]) - t.rank_b(0, 0, 0))
+    assert after0 == r["after_level0"]
+    res = t.rank_b(1, 0, node1 + after0) - t.rank_b(1, 0, node1)
+    assert res == r["answer"] == t.rank([c], [r["i"]])[0] == o1.rank([c], [r["i"]])[0]
+
+    s = g["select"]
+    c = alpha.index(s["c"])
+    k1 = t.rank_b(1, 0, node1) + s["j"]
+    assert s["level1_select"] == {"bit": 0, "k": s["j"]}
+    pos1 = t.select_b(1, 0, k1) - node1
+    assert pos1 == s["level1_index_in_node"]
+    k0 = t.rank_b(0, 1, 0) + pos1 + 1
+    assert k0 == s["level0_select"]["k"]
+    ans = t.select_b(0, 1, k0)
+    assert ans == t.select([c], [s["j"]])[0] == o1.select([c], [s["j"]])[0] == brute.select(list(S), c, s["j"])
+
+
+# --------------------------------------------------------------------------
+# brute force on small inputs
+# --------------------------------------------------------------------------
+
+def _check_all_queries(S, sigma, K):
+    Sl = [int(x) for x in S]
+    n = len(Sl)
+    t = oracle.O2Tree(S, sigma, K=K)
+    o1 = oracle.O1(S, sigma)
+    # access
+    if n:
+        idx = np.arange(n, dtype=np.uint64)
+        want = np.array(Sl, np.uint32)
+        assert np.array_equal(t.access(idx), want)
+        assert np.array_equal(o1.access(idx), want)
+    # rank for every (c, i)
+    cs = np.repeat(np.arange(sigma, dtype=np.uint32), n + 1)
+    ii = np.tile(np.arange(n + 1, dtype=np.uint64), sigma)
+    want = np.array([brute.rank(Sl, int(c), int(i)) for c, i in zip(cs, ii)], np.uint64)
+    assert np.array_equal(t.rank(cs, ii), want)
+    assert np.array_equal(o1.rank(cs, ii), want)
+    # select for every valid (c, j)
+    pairs = [(c, j) for c in range(sigma) for j in range(1, Sl.count(c) + 1)]
+    if pairs:
+        cs = np.array([p[0] for p in pairs], np.uint32)
+        js = np.array([p[1] for p in pairs], np.uint64)
+        want = np.array([brute.select(Sl, c, j) for c, j in pairs], np.uint64)
+        assert np.array_equal(t.select(cs, js), want)
+        assert np.array_equal(o1.select(cs, js), want)
+    # out-of-range queries report the sentinel
+    assert t.access([n])[0] == np.iinfo(np.uint32).max
+    assert t.rank([0], [n + 1])[0] == np.iinfo(np.uint64).max
+    assert t.rank([sigma], [0])[0] == np.iinfo(np.uint64).max
+    assert t.select([0], [0])[0] == np.iinfo(np.uint64).max
+    assert t.select([0], [Sl.count(0) + 1])[0] == np.iinfo(np.uint64).max
+    # level bits equal the pointer-based tree; counters and samples by counting
+    ref = brute.pointer_tree_levels(Sl, sigma)
+    assert t.L == (len(ref) if n else t.L)
+    for l in range(t.L):
+        bits = [int(x) for x in t.bits(l)]
+        if n:
+            assert bits == ref[l], (l, sigma)
+        L1, L2, s0, s1 = brute.counters(bits, K)
+        assert list(t.export(oracle.EXPORT_L1, l)) == L1
+        assert list(t.export(oracle.EXPORT_L2, l)) == L2
+        assert list(t.export(oracle.EXPORT_S0, l)) == s0
+        assert list(t.export(oracle.EXPORT_S1, l)) == s1
+    # node table: start = C[a], r0 = zeros before start, mid = C[a + prevPow2(b-a)]
+    _check_nodes(t, Sl, sigma)
+    return t
+
+
+def _check_nodes(t, Sl, sigma):
+    nodes = t.export(oracle.EXPORT_NODES)
+    C = [0] * (sigma + 1)
+    for s in Sl:
+        C[s + 1] += 1
+    for c in range(sigma):
+        C[c + 1] += C[c]
+
+    def pp2(x):
+        p = 1
+        while p * 2 < x:
+            p *= 2
+        return p
+
+    seen = set()
+    frontier = [(0, sigma, 0, 0)]
+    while frontier:
+        nxt = []
+        for a, b, d, p in frontier:
+            if b - a < 2:
+                continue
+            slot = (1 << d) - 1 + p
+            seen.add(slot)
+            start, r0, mid, valid = (int(x) for x in nodes[slot])
+            assert valid == 1
+            assert start == C[a]
+            bits = [int(x) for x in t.bits(d)]
+            assert r0 == bits[:start].count(0)
+            m = a + pp2(b - a)
+            assert mid == C[m]
+            nxt += [(a, m, d + 1, 2 * p), (m, b, d + 1, 2 * p + 1)]
+        frontier = nxt
+    for slot in range(nodes.shape[0]):
+        if slot not in seen:
+            assert nodes[slot][3] == 0
+
+
+@pytest.mark.parametrize("sigma", range(1, 9))
+def test_brute_tiny_exhaustive_sizes(sigma):
+    rng = np.random.default_rng(1000 + sigma)
+    for n in range(0, 65):
+        S = rng.integers(0, sigma, n).astype(np.uint8)
+        _check_all_queries(S, sigma, K=3)
+
+
+@pytest.mark.parametrize("sigma", [1, 2, 3, 5, 6, 7, 11, 25, 96, 100, 129, 200, 243, 255, 256, 257, 300])
+def test_brute_random(sigma):
+    rng = np.random.default_rng(sigma)
+    for n in (1, 17, 500, 1500):
+        dt = np.uint8 if sigma <= 256 else np.uint16
+        S = rng.integers(0, sigma, n).astype(dt)
+        _check_all_queries(S, sigma, K=7)
+
+
+def test_invariants_medium():
+    rng = np.random.default_rng(7)
+    sigma = 96
+    p = 1.0 / np.arange(1, sigma + 1)
+    S = rng.choice(sigma, size=1 << 16, p=p / p.sum()).astype(np.uint8)
+    n = S.size
+    t = oracle.O2Tree(S, sigma, K=64)
+    o1 = oracle.O1(S, sigma)
+    C = o1.C.astype(np.int64)
+    cs, js = [], []
+    for c in range(sigma):
+        cnt = int(C[c + 1] - C[c])
+        if cnt:
+            for j in sorted(set(rng.integers(1, cnt + 1, 20).tolist()) | {1, cnt}):
+                cs.append(c)
+                js.append(j)
+    cs = np.array(cs, np.uint32)
+    js = np.array(js, np.uint64)
+    sel = t.select(cs, js)
+    assert np.array_equal(sel, o1.select(cs, js))
+    assert np.array_equal(S[sel.astype(np.int64)], cs.astype(np.uint8))
+    # with the exclusive rank of Section 4: rank_c(select_c(j)) = j - 1 and rank_c(select_c(j) + 1) = j
+    assert np.array_equal(t.rank(cs, sel), js - 1)
+    assert np.array_equal(t.rank(cs, sel + 1), js)
+    # sum over c of rank_c(i) = i
+    ii = rng.integers(0, n + 1, 200).astype(np.uint64)
+    tot = np.zeros(ii.size, np.uint64)
+    for c in range(sigma):
+        tot += t.rank(np.full(ii.size, c, np.uint32), ii)
+    assert np.array_equal(tot, ii)
+    # access(i) = S[i]
+    idx = rng.integers(0, n, 5000).astype(np.uint64)
+    assert np.array_equal(t.access(idx), S[idx.astype(np.int64)].astype(np.uint32))
+    # total tree bits = sum over symbols of hist * code length
+    _, ln, _ = oracle.codes_split(sigma)
+    hist = np.diff(C)
+    assert sum(t.level_size(l) for l in range(t.L)) == int((hist * ln[:sigma].astype(np.int64)).sum())
+
+
+def test_node_start_alg8_matches_recursion():
+    for sigma in list(range(2, 300)) + [1000, 4097, 5000]:
+        t = oracle.O2Tree(np.zeros(1, np.uint16), sigma)
+        code, ln, L = oracle.codes_split(sigma)
+
+        def pp2(x):
+            p = 1
+            while p * 2 < x:
+                p *= 2
+            return p
+
+        for c in range(sigma):
+            starts = []  # start symbol of the node holding c at each depth
+            a, b = 0, sigma
+            while b - a >= 2:
+                starts.append(a)
+                m = a + pp2(b - a)
+                if c < m:
+                    b = m
+                else:
+                    a = m
+            assert len(starts) == ln[c]
+            start_symbol = c
+            for l in range(int(ln[c]) - 1, -1, -1):
+                if (int(code[c]) >> (L - 1 - l)) & 1:
+                    start_symbol = t.node_start(start_symbol, l)
+                assert start_symbol == starts[l], (sigma, c, l)
+
+
+# --------------------------------------------------------------------------
+# closed-form space overheads (Sections 4.1, 6.2, 6.3)
+# --------------------------------------------------------------------------
+
+def test_space_overheads_from_paper():
+    facts = _golden("paper_facts.json")
+    n = 1 << 24
+    S = (np.random.default_rng(3).integers(0, 2, n)).astype(np.uint8)
+    t = oracle.O2Tree(S, 2, K=16384)
+    l1 = t.export(oracle.EXPORT_L1, 0).size
+    l2 = t.export(oracle.EXPORT_L2, 0).size
+    rank_pct = 100.0 * (l1 * 64 + l2 * 16) / n
+    assert round(rank_pct, 2) == facts["rank_overhead"]["percent"]
+    for row in facts["rank_select_overhead"]:
+        t = oracle.O2Tree(S, 2, K=row["sample"])
+        samples = t.export(oracle.EXPORT_S0, 0).size + t.export(oracle.EXPORT_S1, 0).size
+        pct = 100.0 * (l1 * 64 + l2 * 16 + samples * 64) / n
+        assert round(pct, 1) == row["percent"]
