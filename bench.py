@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark: wavelet-tree build + batched access/rank/select on one GB300.
+
+A step is one pass of the whole hot path over one synthetic input: build the
+tree of the text workload (n = 2^30 uint8 symbols, Zipf(s=1.0) over sigma = 96,
+7 levels with reduced codes), then 10M access, 10M rank and 10M select
+queries, then free the tree.  ``value`` is queries per second over whole steps
+(build time included), in Mqueries/s; the per-phase rates (build GB/s,
+access/rank/select Mq/s) are reported under "phases".
+
+  python bench.py [--steps K] [--warmup W] [--workload text|plain|large_alphabet|learned]
+  python bench.py --impl reference      # the CPU oracle on a bounded sample
+
+Under torchrun (N > 1) every rank builds the same tree (the build does not
+shard: replicas) and answers its own query batch (queries shard with no
+collective), so the scaling is weak in queries.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "access/rank/select Mqueries/s, build GB/s; learned vs sampled select"
+UNIT = "Mqueries/s"
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="text")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if shutil.which("nvidia-smi"):
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic traffic models
+# --------------------------------------------------------------------------
+
+def level_pass_bytes(sizes, w, K):
+    """Bytes one level pass must move: read T_l, write bits, counters and
+    samples, write T_{l+1} (none at the last level)."""
+    out = []
+    L = len(sizes)
+    for l, sz in enumerate(sizes):
+        b = sz * w + (sz + 7) // 8 + (sz // 65536 + 1) * 8 + (sz // 512 + 1) * 2 + (sz // K + 2) * 8
+        if l + 1 < L:
+            b += sizes[l + 1] * w
+        out.append(b)
+    return out
+
+
+def build_bytes(n, w, sizes, K):
+    """Algorithmic bytes of the level-wise build: histogram read + every level pass."""
+    return n * w + sum(level_pass_bytes(sizes, w, K))
+
+
+def query_sectors(kind, L, mean_len):
+    """32-byte DRAM sectors per query (counters, node tables and C cache-resident):
+    per level one L2-counter sector and on average 1.5 word sectors for a rank;
+    access reads a single bit at its last level; a sampled select reads about
+    one sample, four L2-search and 1.5 word sectors per level."""
+    if kind == "rank":
+        return 2.5 * mean_len
+    if kind == "access":
+        return 2.5 * (L - 1) + 1
+    return 6.5 * mean_len
+
+
+# --------------------------------------------------------------------------
+# the CPU oracle as baseline (bounded sample, scaled to the metric's unit)
+# --------------------------------------------------------------------------
+
+def oracle_sample_rate(wl, n_sample=1 << 21, q_sample=20000, seed_off=0):
+    import numpy as np
+    import oracle
+    from paper_2505_03372_gb300 import workloads
+
+    sym = workloads.make_symbols(n_sample, wl.sigma, wl.symbol_bytes, wl.dist, wl.zipf_s,
+                                 seed=workloads.SEED_BASE + wl.index + seed_off, device="cpu")
+    S = sym.numpy().view({1: np.uint8, 2: np.uint16, 4: np.uint32}[wl.symbol_bytes])
+    w2 = workloads.Workload(wl.name, wl.index, n_sample, wl.sigma, wl.symbol_bytes, wl.dist, wl.zipf_s,
+                            {"access": q_sample, "rank": q_sample, "select": q_sample}, wl.sample_k)
+    q = workloads.make_queries(w2, sym)
+    t0 = time.perf_counter()
+    tree = oracle.O2Tree(S, wl.sigma, K=wl.sample_k)
+    t1 = time.perf_counter()
+    tree.access(q["access_i"].numpy())
+    tree.rank(q["rank_c"].numpy(), q["rank_i"].numpy())
+    tree.select(q["select_c"].numpy(), q["select_j"].numpy())
+    t2 = time.perf_counter()
+    Q = sum(wl.queries.values())
+    t_full = (t1 - t0) * (wl.n / n_sample) + (t2 - t1) * (Q / (3 * q_sample))
+    return {"value": Q / t_full / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"naive level-wise tree (Algorithms 3-8) built on the first {n_sample} symbols of the same "
+                       f"distribution plus {q_sample} each of access/rank/select tree walks; build time scaled by "
+                       f"n/{n_sample}, query time by {Q}/{3 * q_sample}"),
+            "build_s_sample": t1 - t0, "query_s_sample": t2 - t1}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2505_03372_gb300 import workloads
+
+    oracle.build()
+    wl = workloads.WORKLOADS[args.workload]
+    times = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        info = oracle_sample_rate(wl, n_sample=1 << 20, q_sample=10000, seed_off=s)
+        if s >= args.warmup:
+            times.append(info["value"])
+    v = statistics.median(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": wl.describe(), "sample_k": wl.sample_k},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": info["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2505_03372_gb300 import binding as wt
+    from paper_2505_03372_gb300 import workloads
+
+    wl = workloads.WORKLOADS[args.workload]
+    sym = workloads.make_symbols(wl.n, wl.sigma, wl.symbol_bytes, wl.dist, wl.zipf_s,
+                                 seed=workloads.SEED_BASE + wl.index, device="cuda")
+    counts = workloads.symbol_counts(sym, wl.sigma)
+    q = workloads.make_queries(wl, sym, seed=workloads.SEED_BASE + 0x100 + wl.index + 7919 * rank, counts=counts)
+    dev = torch.device("cuda", local)
+    outs = {}
+    for k, v in q.items():
+        if k.endswith("_i") and k.startswith("access"):
+            outs["access"] = torch.empty(v.numel(), dtype=torch.int32, device=dev)
+        elif k in ("rank_i", "select_j", "mixed_arg"):
+            outs[k.split("_")[0]] = torch.empty(v.numel(), dtype=torch.int64, device=dev)
+    Q = sum(v.numel() for k, v in q.items() if k in ("access_i", "rank_i", "select_j", "mixed_arg"))
+
+    def step(sym_dev, qd, od):
+        t = wt.build(sym_dev, wl.sigma, sample_k=wl.sample_k)
+        if "access_i" in qd:
+            t.access(qd["access_i"], out=od["access"])
+        if "rank_i" in qd:
+            t.rank(qd["rank_c"], qd["rank_i"], out=od["rank"])
+        if "select_j" in qd:
+            t.select(qd["select_c"], qd["select_j"], out=od["select"])
+        if "mixed_arg" in qd:
+            t.query_mixed(qd["mixed_kind"], qd["mixed_c"], qd["mixed_arg"], out=od["mixed"])
+        return t
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- warm-up ----
+    t = None
+    for _ in range(max(args.warmup, 3)):
+        t = step(sym, q, outs)
+        st = t.status_sync()
+        if st != wt.WT_OK:
+            raise RuntimeError("device status after warm-up: " + wt.status_str(st))
+        inf = t.info()
+        t.close()
+    sizes = [inf.level_size[l] for l in range(inf.levels)]
+
+    # ---- timed region (device-resident inputs; input 1 GiB and tree ~0.9 GiB exceed the 126 MiB L2) ----
+    wt.profile_reset()
+    wt.profile_enable(True)
+    clocks = ClockSampler(local) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        t = step(sym, q, outs)
+        t.close()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    launches = wt.profile_launches()
+    rep = wt.profile_report()
+    wt.profile_enable(False)
+    ms_step = ms_total / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    value = world * Q / (ms_step * 1e-3) / 1e6
+
+    # ---- phases and roofline of the dominant kernel ----
+    peak, peak_kind = peaks()
+    w = wl.symbol_bytes
+    lp_bytes = level_pass_bytes(sizes, w, wl.sample_k)
+    b_build = build_bytes(wl.n, w, sizes, wl.sample_k)
+    code_len = _mean_code_len(wl, q, counts)
+    L = len(sizes)
+    kern = {k: v for k, v in rep.items()}
+    build_ms = sum(v["ms"] for k, v in kern.items() if k not in ("access", "rank", "select", "mixed")) / args.steps
+    phases = {"build_ms": build_ms, "build_GBps": b_build / (build_ms * 1e-3) / 1e9,
+              "build_input_GBps": wl.n * w / (build_ms * 1e-3) / 1e9}
+    for kind, qk in (("access", "access_i"), ("rank", "rank_i"), ("select", "select_j"), ("mixed", "mixed_arg")):
+        if kind in kern and kern[kind]["launches"]:
+            ms = kern[kind]["ms"] / kern[kind]["launches"]
+            phases[f"{kind}_ms"] = ms
+            phases[f"{kind}_Mqps"] = q[qk].numel() / (ms * 1e-3) / 1e6
+    lp_name = {1: "level_pass_u8", 2: "level_pass_u16", 4: "level_pass_u32"}[w]
+    cands = []
+    if lp_name in kern:
+        cands.append((kern[lp_name]["ms"], lp_name))
+    for kind in ("access", "rank", "select", "mixed"):
+        if kind in kern:
+            cands.append((kern[kind]["ms"], kind))
+    dom_ms, dom = max(cands)
+    nlaunch = kern[dom]["launches"]
+    if dom == lp_name:
+        per_launch_bytes = sum(lp_bytes) / len(lp_bytes)
+        achieved = sum(lp_bytes) * args.steps / (dom_ms * 1e-3) / 1e9
+    else:
+        qk = {"access": "access_i", "rank": "rank_i", "select": "select_j", "mixed": "mixed_arg"}[dom]
+        nq = q[qk].numel()
+        sec = query_sectors(dom, L, code_len) if dom != "mixed" else statistics.mean(
+            [query_sectors(k, L, code_len) for k in ("access", "rank", "select")])
+        per_launch_bytes = nq * sec * 32
+        achieved = per_launch_bytes * nlaunch / (dom_ms * 1e-3) / 1e9
+    for k in list(kern):
+        kern[k]["share"] = kern[k]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": dom_ms / nlaunch, "traffic": None}
+    if lp_name in kern:
+        roof["level_pass_frac"] = (sum(lp_bytes) * args.steps / (kern[lp_name]["ms"] * 1e-3) / 1e9) / peak
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8" if w == 1 else f"u{8 * w}",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": wl.describe(), "queries_per_step_per_gpu": Q, "sample_k": wl.sample_k,
+                   "l2_flush": "inputs larger than L2 (1 GiB symbols, ~0.9 GiB tree, 0.5 GiB queries)",
+                   "parallelism": "replicated build, sharded queries" if world > 1 else "1 GPU"},
+        "phases": phases, "roofline": roof, "kernels": kern, "gpu_launches": launches, "clocks": clk,
+    }
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    if not args.no_e2e:
+        line["e2e"] = _e2e(args, wl, sym, q, outs, step, barrier, dist, world, Q)
+    # ---- CPU oracle baseline (rank 0, N = 1) ----
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        cb = oracle_sample_rate(wl)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _mean_code_len(wl, q, counts):
+    import numpy as np
+    import oracle
+
+    try:
+        _, ln, _ = oracle.codes_split(wl.sigma)
+    except Exception:
+        return 0.0
+    cs = [q[k].cpu().numpy().view(np.uint32) for k in ("rank_c", "select_c", "mixed_c") if k in q]
+    if not cs:
+        return float(np.log2(max(wl.sigma, 2)))
+    c = np.concatenate(cs)
+    return float(ln[c].astype(np.float64).mean())
+
+
+def _e2e(args, wl, sym, q, outs, step, barrier, dist, world, Q):
+    import torch
+
+    h_sym = sym.cpu().pin_memory()
+    h_q = {k: v.cpu().pin_memory() for k, v in q.items()}
+    h_out = {k: torch.empty(v.numel(), dtype=v.dtype, pin_memory=True) for k, v in outs.items()}
+    d_sym = torch.empty_like(sym)
+    d_q = {k: torch.empty_like(v) for k, v in q.items()}
+    h2d = h_sym.numel() * h_sym.element_size() + sum(v.numel() * v.element_size() for v in h_q.values())
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values())
+
+    def e2e_step():
+        d_sym.copy_(h_sym, non_blocking=True)
+        for k in d_q:
+            d_q[k].copy_(h_q[k], non_blocking=True)
+        t = step(d_sym, d_q, outs)
+        for k in h_out:
+            h_out[k].copy_(outs[k], non_blocking=True)
+        t.close()
+
+    for _ in range(1):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return {"value": world * Q / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "path": "pinned host symbols and queries -> H2D -> wt_build -> wt_access/rank/select -> D2H results"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * libwt — level-wise wavelet tree on one GB300 GPU (sm_103a).
+ *
+ * C ABI of the library built from paper_2505_03372_gb300/csrc.  All compute
+ * runs in hand-written CUDA kernels; there is no CPU fallback.  Section and
+ * algorithm numbers refer to M. Franzreb Salgado, "GPU Implementation of the
+ * Wavelet Tree", arXiv 2505.03372 (2025).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are device pointers (cudaMalloc / cudaMallocAsync /
+ *    PyTorch CUDA tensors); h_* are host pointers.  The caller owns them; the
+ *    library never frees or retains them past the call (or, for asynchronous
+ *    calls, past the completion of the work it enqueued on `stream`).
+ *  - `stream` is a CUDA stream (the same type as cudaStream_t); NULL means the
+ *    legacy default stream.  Work is enqueued on it; calls return before the
+ *    GPU finishes unless stated otherwise.
+ *  - Host-detectable argument errors (null pointers, bad sizes, a freed
+ *    handle) return a status synchronously and enqueue nothing.
+ *  - Data-dependent errors (a symbol >= sigma, a query out of range, a
+ *    bounded device wait that gave up) are found on the GPU: the affected
+ *    output gets a sentinel (UINT32_MAX / UINT64_MAX) and a sticky status word
+ *    in the tree records the error; wt_status_sync() reports and clears it.
+ *    No kernel traps.
+ *  - Positions and counts are 0-based and 64-bit; rank is exclusive
+ *    (Section 1 / Section 4, following SDSL): rank_c(i) counts positions < i.
+ *  - Symbol arrays and the tree's bit arrays use 1, 2 or 4 bytes per symbol.
+ *    Device symbol pointers must be 16-byte aligned (they are read with TMA
+ *    bulk copies).  Limits: n < 2^40, 1 <= sigma <= 2^26 and
+ *    sigma <= 2^(8*symbol_bytes).
+ */
+#ifndef WT_H
+#define WT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* wt_stream; /* identical to cudaStream_t */
+typedef struct wt_tree_s* wt_tree;     /* opaque, owned by libwt, immutable after build */
+
+typedef enum {
+    WT_OK = 0,
+    WT_EINVAL = 1,      /* bad argument: null pointer, sigma == 0, width not 1/2/4, limits exceeded, misaligned pointer */
+    WT_ESYMBOL = 2,     /* some input symbol is >= sigma (found by the build's histogram pass) */
+    WT_ENOMEM = 3,      /* device allocation failed */
+    WT_ECUDA = 4,       /* a CUDA runtime call failed (launch error, ...) */
+    WT_EQUERY = 5,      /* some query argument was out of range; that output holds a sentinel */
+    WT_ETIMEOUT = 6,    /* a bounded device-side wait gave up; results of that call are not valid */
+    WT_EUNSUPPORTED = 7 /* operation not available for this tree (e.g. no trained select model) */
+} wt_status;
+
+/* Build options.  Zero-initialised fields take the default. */
+typedef struct {
+    uint32_t sample_k; /* select sample interval K: the position of every K-th one and every K-th
+                          zero is stored (Section 4.2).  Power of two in [256, 2^20]; default 4096,
+                          the value of the paper's wavelet-tree experiments (Section 6.3). */
+    uint32_t reserved[7];
+} wt_options;
+
+/* Size of the rank blocks (Section 4.1): L1 blocks of 65536 bits with a 64-bit
+ * count of ones before the block; L2 blocks of 512 bits with a 16-bit count of
+ * ones from the start of their L1 block.  |L2| = 512 is the value of every
+ * experiment in Section 6. */
+#define WT_L1_BITS 65536u
+#define WT_L2_BITS 512u
+#define WT_MAX_LEVELS 26u
+
+/*
+ * wt_build — construct the extended level-wise wavelet tree of Section 5
+ * (Algorithm 4) with reduced codes (Section 5.1, Algorithm 3) over the
+ * sequence S = d_symbols[0..n) drawn from [0, sigma).
+ *
+ * Level l (0 <= l < L = ceil(lg sigma)) stores bit l (from the top) of the code
+ * of every symbol of S stably sorted by its first l code bits, for the symbols
+ * whose code is longer than l; bits are packed LSB-first in 64-bit words and
+ * each level starts on a 128-byte boundary (Section 4).  The same pass per
+ * level writes the L1/L2 rank counters (Section 4.1) and the select samples
+ * (Section 4.2), and stably partitions the level's symbols into the next
+ * level's order.  The cumulative histogram C and the rank of every node
+ * start are stored (the "extended" tree and precomputed node ranks, Section 5
+ * and Section 5.2.1).
+ *
+ *  d_symbols     device, n symbols of symbol_bytes bytes each, 16-byte aligned;
+ *                read only, not retained after the call returns.
+ *  n             number of symbols, 0 <= n < 2^40.
+ *  sigma         alphabet size, symbols must be < sigma.
+ *  symbol_bytes  1, 2 or 4.
+ *  opt           NULL for defaults.
+ *  out           receives the handle (NULL on error).
+ *
+ * The call synchronises `stream` once (to read back the level sizes, which
+ * fix the tree's allocation) and returns with the remaining work enqueued.
+ * Returns WT_ESYMBOL, without a tree, if some symbol is >= sigma.
+ */
+wt_status wt_build(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                   const wt_options* opt, wt_stream stream, wt_tree* out);
+
+/* Release all device memory of the tree (stream-ordered on the build stream). */
+void wt_destroy(wt_tree tree);
+
+/*
+ * wt_access — Algorithm 5: d_out[k] = S[d_i[k]] for k < q.
+ *  d_i    device, q positions; a position >= n yields UINT32_MAX and WT_EQUERY.
+ *  d_out  device, q symbols (uint32).
+ */
+wt_status wt_access(wt_tree tree, const uint64_t* d_i, uint32_t* d_out, uint64_t q, wt_stream stream);
+
+/*
+ * wt_rank — Algorithm 6: d_out[k] = #{ j < d_i[k] : S[j] = d_c[k] }.
+ *  d_c    device, q symbols; d_c[k] >= sigma yields UINT64_MAX and WT_EQUERY.
+ *  d_i    device, q positions in [0, n]; larger yields UINT64_MAX and WT_EQUERY.
+ *  d_out  device, q counts.
+ */
+wt_status wt_rank(wt_tree tree, const uint32_t* d_c, const uint64_t* d_i, uint64_t* d_out, uint64_t q,
+                  wt_stream stream);
+
+/*
+ * wt_select — Algorithms 7 and 8 over the sampled binary select of
+ * Algorithm 2: d_out[k] = position of the d_j[k]-th (1-based) occurrence of
+ * d_c[k].  d_j[k] outside [1, count(d_c[k])] or d_c[k] >= sigma yields
+ * UINT64_MAX and WT_EQUERY.
+ */
+wt_status wt_select(wt_tree tree, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out, uint64_t q,
+                    wt_stream stream);
+
+/*
+ * wt_query_mixed — one launch over a mixed batch: d_kind[k] = 0 access(d_arg[k]),
+ * 1 rank(d_c[k], d_arg[k]), 2 select(d_c[k], d_arg[k]).  Results are widened to
+ * uint64 in d_out (access results are symbols).  d_c is ignored for access.
+ * Any other kind yields UINT64_MAX and WT_EQUERY.
+ */
+wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_c, const uint64_t* d_arg,
+                         uint64_t* d_out, uint64_t q, wt_stream stream);
+
+/* Synchronise `stream`, then return and clear the tree's sticky device status
+ * (WT_OK if no data-dependent error happened since the last call). */
+wt_status wt_status_sync(wt_tree tree, wt_stream stream);
+
+typedef struct {
+    uint64_t n;
+    uint32_t sigma;
+    uint32_t levels;       /* L = ceil(lg sigma); 0 for sigma == 1 */
+    uint32_t symbol_bytes;
+    uint32_t sample_k;
+    uint64_t level_size[WT_MAX_LEVELS]; /* bits in level l = #symbols whose code is longer than l */
+    uint64_t level_ones[WT_MAX_LEVELS];
+    uint64_t tree_bytes;   /* device bytes held by the tree */
+} wt_info_t;
+
+/* Host-side metadata; no device work. */
+wt_status wt_info(wt_tree tree, wt_info_t* out);
+
+/*
+ * wt_export — copy logical contents to host memory, for comparison with a
+ * reference.  Synchronous (device-to-host copies on the build stream).
+ *  what = WT_EXPORT_BITS   level bits, ceil(size/64) uint64 words, tail bits zero
+ *         WT_EXPORT_L1     floor(size/65536)+1 uint64: ones in B[0, 65536 k)
+ *         WT_EXPORT_L2     floor(size/512)+1 uint16: ones from the start of the
+ *                          enclosing L1 block to position 512 m
+ *         WT_EXPORT_S0/S1  floor(zeros/K)+1 (ones) uint64: [0] = 0 and [m] =
+ *                          position of the (m K)-th zero (one)
+ *         WT_EXPORT_C      sigma+1 uint64 cumulative histogram (level ignored)
+ *         WT_EXPORT_CODES  sigma uint64 codes left-aligned in L bits
+ *         WT_EXPORT_LENS   sigma uint8 code lengths
+ *         WT_EXPORT_NODES  (2^L - 1) x 4 uint64 in heap order, slot 2^d - 1 + p
+ *                          for the node at depth d with code prefix p:
+ *                          {start = C[a], r0 = rank_0(d, start), mid =
+ *                          C[a + prevPow2(b - a)], valid}
+ *  h_dst  host buffer or NULL; *count receives the element count either way.
+ */
+enum {
+    WT_EXPORT_BITS = 0,
+    WT_EXPORT_L1 = 1,
+    WT_EXPORT_L2 = 2,
+    WT_EXPORT_S0 = 3,
+    WT_EXPORT_S1 = 4,
+    WT_EXPORT_C = 5,
+    WT_EXPORT_CODES = 6,
+    WT_EXPORT_LENS = 7,
+    WT_EXPORT_NODES = 8
+};
+wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, uint64_t* count);
+
+/* Human-readable name of a status code (static storage). */
+const char* wt_status_str(wt_status s);
+
+/*
+ * Launch accounting and kernel timing (tracing support; no effect on results).
+ *  wt_profile_enable(1) brackets every kernel launch with CUDA events on its
+ *  stream; wt_profile_report() synchronises those events and writes a JSON
+ *  object {"kernel name": {"launches": L, "ms": T}, ...} into buf (cap bytes,
+ *  NUL-terminated, truncated if short) and returns the length needed.
+ *  wt_profile_launches() counts every kernel this library launched since load
+ *  (or since the last reset), whether or not timing is enabled.
+ */
+void wt_profile_enable(int on);
+void wt_profile_reset(void);
+uint64_t wt_profile_launches(void);
+size_t wt_profile_report(char* buf, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WT_H */

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libwt (include/wt.h).
+
+Argument marshalling only: every step of construction and every query runs in
+libwt's CUDA kernels.  PyTorch supplies device memory and the current stream.
+If libwt.so is missing or cannot be loaded this module raises at import of the
+first call; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwt.so")
+
+WT_OK, WT_EINVAL, WT_ESYMBOL, WT_ENOMEM, WT_ECUDA, WT_EQUERY, WT_ETIMEOUT, WT_EUNSUPPORTED = range(8)
+EXPORT_BITS, EXPORT_L1, EXPORT_L2, EXPORT_S0, EXPORT_S1, EXPORT_C, EXPORT_CODES, EXPORT_LENS, EXPORT_NODES = range(9)
+MAX_LEVELS = 26
+
+# every symbol include/wt.h declares (checked by the ABI test)
+EXPORTED = (
+    "wt_build", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync",
+    "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
+    "wt_profile_report",
+)
+
+
+class WTError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)}" if what else status_str(status))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("sample_k", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("sigma", ctypes.c_uint32),
+        ("levels", ctypes.c_uint32),
+        ("symbol_bytes", ctypes.c_uint32),
+        ("sample_k", ctypes.c_uint32),
+        ("level_size", ctypes.c_uint64 * MAX_LEVELS),
+        ("level_ones", ctypes.c_uint64 * MAX_LEVELS),
+        ("tree_bytes", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libwt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libwt.so not found at {LIB_PATH}: run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        L.wt_build.argtypes = [vp, u64, u32, u32, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+        L.wt_destroy.argtypes = [vp]
+        L.wt_destroy.restype = None
+        L.wt_access.argtypes = [vp, vp, vp, u64, vp]
+        L.wt_rank.argtypes = [vp, vp, vp, vp, u64, vp]
+        L.wt_select.argtypes = [vp, vp, vp, vp, u64, vp]
+        L.wt_query_mixed.argtypes = [vp, vp, vp, vp, vp, u64, vp]
+        L.wt_status_sync.argtypes = [vp, vp]
+        L.wt_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.wt_export.argtypes = [vp, u32, u32, vp, ctypes.POINTER(u64)]
+        L.wt_status_str.argtypes = [ctypes.c_int]
+        L.wt_status_str.restype = ctypes.c_char_p
+        L.wt_profile_enable.argtypes = [ctypes.c_int]
+        L.wt_profile_enable.restype = None
+        L.wt_profile_reset.argtypes = []
+        L.wt_profile_reset.restype = None
+        L.wt_profile_launches.argtypes = []
+        L.wt_profile_launches.restype = u64
+        L.wt_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+        L.wt_profile_report.restype = ctypes.c_size_t
+        for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync", "wt_info",
+                  "wt_export"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_str(s: int) -> str:
+    return lib().wt_status_str(s).decode()
+
+
+def _check(st: int, what: str):
+    if st != WT_OK:
+        raise WTError(st, what)
+
+
+def _stream(stream=None) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dptr(t, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _as_u64(t, name):
+    import torch
+
+    if t.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise TypeError(f"{name} must be int64/uint64 (positions are 64-bit)")
+    return _dptr(t, name)
+
+
+def _as_u32(t, name):
+    import torch
+
+    if t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise TypeError(f"{name} must be int32/uint32")
+    return _dptr(t, name)
+
+
+class Tree:
+    """Handle of a wavelet tree built on the GPU (wt_build)."""
+
+    def __init__(self, symbols, sigma: int, sample_k: int = 4096, stream=None):
+        import torch
+
+        if not symbols.is_cuda or symbols.dim() != 1:
+            raise TypeError("symbols must be a 1-D CUDA tensor")
+        w = symbols.element_size()
+        if w not in (1, 2, 4) or symbols.dtype.is_floating_point:
+            raise TypeError("symbols must be an integer tensor of 1, 2 or 4 bytes per element")
+        self._keep = symbols.contiguous()
+        self.n = symbols.numel()
+        self.sigma = int(sigma)
+        self.symbol_bytes = w
+        self._stream = stream
+        opt = Options(sample_k=sample_k)
+        h = ctypes.c_void_p()
+        ptr = self._keep.data_ptr() if self.n else None
+        st = lib().wt_build(ptr, self.n, self.sigma, w, ctypes.byref(opt), _stream(stream), ctypes.byref(h))
+        self._keep = None  # the input is not retained after the call (it has synchronised once)
+        _check(st, "wt_build")
+        self._h = h
+        self.levels = self.info().levels
+
+    # ---- lifecycle ----
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().wt_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- queries (outputs allocated with torch on the current device) ----
+    def access(self, i, out=None, stream=None):
+        import torch
+
+        q = i.numel()
+        if out is None:
+            out = torch.empty(q, dtype=torch.int32, device=i.device)
+        if q:
+            _check(lib().wt_access(self._h, _as_u64(i, "i"), _dptr(out, "out"), q, _stream(stream)), "wt_access")
+        return out
+
+    def rank(self, c, i, out=None, stream=None):
+        import torch
+
+        q = i.numel()
+        if c.numel() != q:
+            raise ValueError("c and i must have the same length")
+        if out is None:
+            out = torch.empty(q, dtype=torch.int64, device=i.device)
+        if q:
+            _check(lib().wt_rank(self._h, _as_u32(c, "c"), _as_u64(i, "i"), _dptr(out, "out"), q, _stream(stream)),
+                   "wt_rank")
+        return out
+
+    def select(self, c, j, out=None, stream=None):
+        import torch
+
+        q = j.numel()
+        if c.numel() != q:
+            raise ValueError("c and j must have the same length")
+        if out is None:
+            out = torch.empty(q, dtype=torch.int64, device=j.device)
+        if q:
+            _check(lib().wt_select(self._h, _as_u32(c, "c"), _as_u64(j, "j"), _dptr(out, "out"), q,
+                                   _stream(stream)), "wt_select")
+        return out
+
+    def query_mixed(self, kind, c, arg, out=None, stream=None):
+        import torch
+
+        q = arg.numel()
+        if kind.numel() != q or c.numel() != q:
+            raise ValueError("kind, c and arg must have the same length")
+        if kind.dtype != torch.uint8:
+            raise TypeError("kind must be uint8")
+        if out is None:
+            out = torch.empty(q, dtype=torch.int64, device=arg.device)
+        if q:
+            _check(lib().wt_query_mixed(self._h, _dptr(kind, "kind"), _as_u32(c, "c"), _as_u64(arg, "arg"),
+                                        _dptr(out, "out"), q, _stream(stream)), "wt_query_mixed")
+        return out
+
+    # ---- status / metadata ----
+    def status_sync(self, stream=None) -> int:
+        """Synchronise the stream; return and clear the sticky device status."""
+        return lib().wt_status_sync(self._h, _stream(stream))
+
+    def info(self) -> Info:
+        inf = Info()
+        _check(lib().wt_info(self._h, ctypes.byref(inf)), "wt_info")
+        return inf
+
+    def export(self, what: int, level: int = 0) -> np.ndarray:
+        cnt = ctypes.c_uint64()
+        _check(lib().wt_export(self._h, level, what, None, ctypes.byref(cnt)), "wt_export")
+        dt = {EXPORT_L2: np.uint16, EXPORT_LENS: np.uint8}.get(what, np.uint64)
+        width = 4 if what == EXPORT_NODES else 1
+        out = np.zeros(cnt.value * width, dt)
+        if cnt.value:
+            _check(lib().wt_export(self._h, level, what, out.ctypes.data, ctypes.byref(cnt)), "wt_export")
+        return out.reshape(-1, 4) if what == EXPORT_NODES else out
+
+
+def build(symbols, sigma: int, sample_k: int = 4096, stream=None) -> Tree:
+    """wt_build: construct the tree of a 1-D CUDA tensor of symbols in [0, sigma)."""
+    return Tree(symbols, sigma, sample_k=sample_k, stream=stream)
+
+
+# ---- launch accounting / kernel timing ----
+def profile_enable(on: bool = True):
+    lib().wt_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().wt_profile_reset()
+
+
+def profile_launches() -> int:
+    return int(lib().wt_profile_launches())
+
+
+def profile_report() -> dict:
+    need = lib().wt_profile_report(None, 0)
+    buf = ctypes.create_string_buffer(int(need) + 16)
+    lib().wt_profile_report(buf, len(buf))
+    return json.loads(buf.value.decode())

@@ -1,0 +1,356 @@
+// extern "C" entry points of libwt (declared in include/wt.h), device memory
+// and launch accounting.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wt_internal.hpp"
+
+namespace wt {
+
+// ---------------------------------------------------------------------------
+// device memory: stream-ordered pool allocations, kept cached in the pool
+// ---------------------------------------------------------------------------
+
+static std::once_flag g_pool_once;
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    std::call_once(g_pool_once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;  // keep freed blocks for reuse by later builds
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+    if (bytes == 0) bytes = 256;
+    return cudaMallocAsync(p, bytes, s);
+}
+
+void dev_free(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// launch accounting and optional event timing
+// ---------------------------------------------------------------------------
+
+struct KStat {
+    uint64_t launches = 0;
+    double ms = 0.0;
+};
+struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+static std::mutex g_mu;
+static std::map<std::string, KStat> g_stats;
+static std::vector<Pending> g_pending;
+static std::vector<cudaEvent_t> g_free_events;
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_timing{0};
+static thread_local cudaEvent_t tl_start = nullptr;
+
+static cudaEvent_t take_event() {
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_before(const char* name, cudaStream_t s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stats[name].launches++;
+    if (g_timing.load()) {
+        tl_start = take_event();
+        cudaEventRecord(tl_start, s);
+    }
+}
+
+void prof_after(const char* name, cudaStream_t s) {
+    if (!g_timing.load() || !tl_start) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaEvent_t b = take_event();
+    cudaEventRecord(b, s);
+    g_pending.push_back({name, tl_start, b});
+    tl_start = nullptr;
+}
+
+static void collect_pending() {
+    for (auto& p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+            g_stats[p.name].ms += ms;
+        g_free_events.push_back(p.a);
+        g_free_events.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+
+// True if p is memory a kernel on this device may dereference.
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static bool tree_ok(const wt_tree_s* t) { return t && t->magic == kTreeMagic; }
+
+}  // namespace wt
+
+using namespace wt;
+
+extern "C" {
+
+const char* wt_status_str(wt_status s) {
+    switch (s) {
+        case WT_OK: return "WT_OK";
+        case WT_EINVAL: return "WT_EINVAL: invalid argument";
+        case WT_ESYMBOL: return "WT_ESYMBOL: input symbol >= sigma";
+        case WT_ENOMEM: return "WT_ENOMEM: device allocation failed";
+        case WT_ECUDA: return "WT_ECUDA: CUDA runtime error";
+        case WT_EQUERY: return "WT_EQUERY: query argument out of range";
+        case WT_ETIMEOUT: return "WT_ETIMEOUT: bounded device wait gave up";
+        case WT_EUNSUPPORTED: return "WT_EUNSUPPORTED: operation not available";
+    }
+    return "unknown wt_status";
+}
+
+wt_status wt_build(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_options* opt,
+                   wt_stream stream, wt_tree* out) {
+    if (!out) return WT_EINVAL;
+    *out = nullptr;
+    if (symbol_bytes != 1 && symbol_bytes != 2 && symbol_bytes != 4) return WT_EINVAL;
+    if (sigma == 0 || sigma > (1u << kMaxSigmaLog)) return WT_EINVAL;
+    if (symbol_bytes < 4 && (uint64_t)sigma > (1ull << (8 * symbol_bytes))) return WT_EINVAL;
+    if (n >= (1ull << 40)) return WT_EINVAL;
+    if (n) {
+        if (!is_device_ptr(d_symbols)) return WT_EINVAL;
+        if (reinterpret_cast<uintptr_t>(d_symbols) & 15u) return WT_EINVAL;
+    }
+    uint32_t K = (opt && opt->sample_k) ? opt->sample_k : 4096u;
+    if (K < 256 || K > (1u << 20) || (K & (K - 1))) return WT_EINVAL;
+
+    wt_tree_s* t = new wt_tree_s();
+    memset(&t->desc, 0, sizeof(t->desc));
+    cudaGetDevice(&t->device);
+    t->stream = stream;
+    t->magic = kTreeMagic;
+    wt_status st = build_tree(d_symbols, n, sigma, symbol_bytes, K, stream, t);
+    if (st != WT_OK) {
+        dev_free(t->hdr_mem, stream);
+        dev_free(t->lvl_mem, stream);
+        t->magic = 0;
+        delete t;
+        return st;
+    }
+    *out = t;
+    return WT_OK;
+}
+
+void wt_destroy(wt_tree tree) {
+    if (!tree_ok(tree)) return;
+    dev_free(tree->hdr_mem, tree->stream);
+    dev_free(tree->lvl_mem, tree->stream);
+    tree->magic = 0;
+    delete tree;
+}
+
+wt_status wt_access(wt_tree tree, const uint64_t* d_i, uint32_t* d_out, uint64_t q, wt_stream stream) {
+    if (!tree_ok(tree)) return WT_EINVAL;
+    if (!q) return WT_OK;
+    if (!is_device_ptr(d_i) || !is_device_ptr(d_out)) return WT_EINVAL;
+    return launch_access(tree, d_i, d_out, q, stream);
+}
+
+wt_status wt_rank(wt_tree tree, const uint32_t* d_c, const uint64_t* d_i, uint64_t* d_out, uint64_t q,
+                  wt_stream stream) {
+    if (!tree_ok(tree)) return WT_EINVAL;
+    if (!q) return WT_OK;
+    if (!is_device_ptr(d_c) || !is_device_ptr(d_i) || !is_device_ptr(d_out)) return WT_EINVAL;
+    return launch_rank(tree, d_c, d_i, d_out, q, stream);
+}
+
+wt_status wt_select(wt_tree tree, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out, uint64_t q,
+                    wt_stream stream) {
+    if (!tree_ok(tree)) return WT_EINVAL;
+    if (!q) return WT_OK;
+    if (!is_device_ptr(d_c) || !is_device_ptr(d_j) || !is_device_ptr(d_out)) return WT_EINVAL;
+    return launch_select(tree, d_c, d_j, d_out, q, stream);
+}
+
+wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_c, const uint64_t* d_arg,
+                         uint64_t* d_out, uint64_t q, wt_stream stream) {
+    if (!tree_ok(tree)) return WT_EINVAL;
+    if (!q) return WT_OK;
+    if (!is_device_ptr(d_kind) || !is_device_ptr(d_c) || !is_device_ptr(d_arg) || !is_device_ptr(d_out))
+        return WT_EINVAL;
+    return launch_mixed(tree, d_kind, d_c, d_arg, d_out, q, stream);
+}
+
+wt_status wt_status_sync(wt_tree tree, wt_stream stream) {
+    if (!tree_ok(tree)) return WT_EINVAL;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return WT_ECUDA;
+    uint32_t bits = 0;
+    if (cudaMemcpy(&bits, tree->desc.status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return WT_ECUDA;
+    if (bits) {
+        if (cudaMemset(tree->desc.status, 0, 4) != cudaSuccess) return WT_ECUDA;
+    }
+    if (bits & kStTimeout) return WT_ETIMEOUT;
+    if (bits & kStSymbol) return WT_ESYMBOL;
+    if (bits & kStQuery) return WT_EQUERY;
+    return WT_OK;
+}
+
+wt_status wt_info(wt_tree tree, wt_info_t* out) {
+    if (!tree_ok(tree) || !out) return WT_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->n = tree->desc.n;
+    out->sigma = tree->desc.cp.sigma;
+    out->levels = tree->desc.cp.L;
+    out->symbol_bytes = tree->symbol_bytes;
+    out->sample_k = tree->sample_k;
+    for (uint32_t l = 0; l < tree->desc.cp.L; l++) {
+        out->level_size[l] = tree->level_size[l];
+        out->level_ones[l] = tree->level_ones[l];
+    }
+    out->tree_bytes = tree->hdr_bytes + tree->lvl_bytes;
+    return WT_OK;
+}
+
+wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, uint64_t* count) {
+    if (!tree_ok(tree) || !count) return WT_EINVAL;
+    const TreeDesc& d = tree->desc;
+    const uint32_t L = d.cp.L, sigma = d.cp.sigma;
+    const void* src = nullptr;
+    size_t esz = 8;
+    uint64_t cnt = 0;
+    if (what == WT_EXPORT_C) {
+        cnt = sigma + 1ull;
+        src = d.C;
+    } else if (what == WT_EXPORT_CODES || what == WT_EXPORT_LENS) {
+        cnt = sigma;
+        *count = cnt;
+        if (h_dst) {
+            for (uint32_t s = 0; s < sigma; s++) {
+                uint32_t code, len;
+                encode(d.cp, s, code, len);
+                if (what == WT_EXPORT_CODES) reinterpret_cast<uint64_t*>(h_dst)[s] = code;
+                else reinterpret_cast<uint8_t*>(h_dst)[s] = (uint8_t)len;
+            }
+        }
+        return WT_OK;
+    } else if (what == WT_EXPORT_NODES) {
+        cnt = L ? ((1ull << L) - 1) : 0;
+        *count = cnt;
+        if (h_dst && cnt) {
+            std::vector<NodeEntry> tmp(cnt);
+            if (cudaMemcpyAsync(tmp.data(), d.nodes, cnt * sizeof(NodeEntry), cudaMemcpyDeviceToHost, tree->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(tree->stream) != cudaSuccess)
+                return WT_ECUDA;
+            uint64_t* o = reinterpret_cast<uint64_t*>(h_dst);
+            for (uint64_t slot = 0; slot < cnt; slot++) {
+                uint32_t l = 63u - (uint32_t)__builtin_clzll(slot + 1);
+                uint64_t p = slot + 1 - (1ull << l), a = 0;
+                uint64_t w = node_info(d.cp, l, p, a);
+                const NodeEntry& e = tmp[slot];
+                bool valid = w >= 2;
+                o[4 * slot + 0] = valid ? e.start : 0;
+                o[4 * slot + 1] = valid ? e.r0 : 0;
+                o[4 * slot + 2] = valid ? e.off1 - e.r0 + e.start : 0;
+                o[4 * slot + 3] = valid ? 1 : 0;
+            }
+        }
+        return WT_OK;
+    } else {
+        if (level >= L) return WT_EINVAL;
+        const LevelDesc& v = d.lv[level];
+        const uint64_t size = v.size, ones = v.ones, zeros = size - ones;
+        switch (what) {
+            case WT_EXPORT_BITS: cnt = (size + 63) / 64; src = v.words; break;
+            case WT_EXPORT_L1: cnt = size / kL1Bits + 1; src = v.l1; break;
+            case WT_EXPORT_L2: cnt = size / kL2Bits + 1; src = v.l2; esz = 2; break;
+            case WT_EXPORT_S0: cnt = (zeros >> d.k_log2) + 1; src = v.s0; break;
+            case WT_EXPORT_S1: cnt = (ones >> d.k_log2) + 1; src = v.s1; break;
+            default: return WT_EINVAL;
+        }
+    }
+    *count = cnt;
+    if (h_dst && cnt) {
+        if (cudaMemcpyAsync(h_dst, src, cnt * esz, cudaMemcpyDeviceToHost, tree->stream) != cudaSuccess ||
+            cudaStreamSynchronize(tree->stream) != cudaSuccess)
+            return WT_ECUDA;
+    }
+    return WT_OK;
+}
+
+void wt_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timing.store(on ? 1 : 0);
+}
+
+void wt_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    collect_pending();
+    g_stats.clear();
+    g_launches.store(0);
+}
+
+uint64_t wt_profile_launches(void) { return g_launches.load(); }
+
+size_t wt_profile_report(char* buf, size_t cap) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    collect_pending();
+    std::string s = "{";
+    bool first = true;
+    char tmp[256];
+    for (auto& kv : g_stats) {
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %llu, \"ms\": %.6f}", first ? "" : ", ", kv.first.c_str(),
+                 (unsigned long long)kv.second.launches, kv.second.ms);
+        s += tmp;
+        first = false;
+    }
+    s += "}";
+    if (buf && cap) {
+        size_t k = s.size() < cap - 1 ? s.size() : cap - 1;
+        memcpy(buf, s.data(), k);
+        buf[k] = 0;
+    }
+    return s.size() + 1;
+}
+
+}  // extern "C"

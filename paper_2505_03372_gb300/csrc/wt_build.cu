@@ -1,0 +1,930 @@
+// Construction of the extended level-wise wavelet tree (Section 5.1,
+// Algorithm 4) on one GB300.
+//
+// Pipeline (all on the device, one stream):
+//   1. histogram of S with symbol validation (Section 5.1.1: shared-memory
+//      sub-histograms, persistent grid);
+//   2. C = exclusive prefix sum of the histogram;
+//   3. node table: for every node (depth l, code prefix p) its start C[a],
+//      the precomputed rank_0 at the start (Section 5.2.1) and the two
+//      partition offsets, derived from C alone (the number of zeros before a
+//      node start is the total size of the left children of the earlier nodes
+//      of that level);
+//   4. one fused pass per level l: read T_l (S for l = 0, re-encoded with the
+//      reduced codes on the fly), write the packed bits of level l, its L1/L2
+//      rank counters (Section 4.1) and its select samples (Section 4.2), and
+//      stably partition T_l by the level bit into T_{l+1} -- the radix-sort step
+//      of Algorithm 4 done as a one-bit split per level.  The global prefix of
+//      ones that the counters and the partition need comes from a decoupled
+//      look-back over tiles, so every level reads T_l once and writes T_{l+1}
+//      once.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "wt_internal.hpp"
+
+namespace wt {
+
+// ===========================================================================
+// small device utilities
+// ===========================================================================
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1-D TMA bulk copy global -> shared, completion signalled on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// bit i of x -> bit 2i
+__device__ __forceinline__ uint64_t spread2(uint32_t x) {
+    uint64_t v = x;
+    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+// bit i (i < 16) of x -> bit 4i
+__device__ __forceinline__ uint64_t spread4(uint32_t x) {
+    uint64_t v = x & 0xFFFFu;
+    v = (v | (v << 24)) & 0x000000FF000000FFull;
+    v = (v | (v << 12)) & 0x000F000F000F000Full;
+    v = (v | (v << 6)) & 0x0303030303030303ull;
+    v = (v | (v << 3)) & 0x1111111111111111ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ===========================================================================
+// 1. histogram + validation
+// ===========================================================================
+
+template <typename T>
+__global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint64_t n, uint32_t sigma, uint32_t sbins,
+                                                   uint32_t copies, unsigned long long* __restrict__ hist,
+                                                   uint32_t* __restrict__ status) {
+    extern __shared__ uint32_t sh[];
+    for (uint32_t i = threadIdx.x; i < sbins * copies; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    uint32_t* mine = sh + (threadIdx.x % copies) * sbins;
+    bool bad = false;
+    constexpr int V = 16 / sizeof(T);
+    const uint64_t nvec = n / V;
+    const uint4* S4 = reinterpret_cast<const uint4*>(S);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    auto add = [&](uint32_t s) {
+        if (s >= sigma) bad = true;
+        else if (s < sbins) atomicAdd(mine + s, 1u);
+        else atomicAdd(hist + s, 1ull);
+    };
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+        uint4 x = __ldg(S4 + v);
+        const T* e = reinterpret_cast<const T*>(&x);
+#pragma unroll
+        for (int k = 0; k < V; k++) add((uint32_t)e[k]);
+    }
+    for (uint64_t j = nvec * V + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) add((uint32_t)S[j]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStSymbol);
+    for (uint32_t b = threadIdx.x; b < sbins; b += blockDim.x) {
+        uint32_t c = 0;
+        for (uint32_t k = 0; k < copies; k++) c += sh[k * sbins + b];
+        if (c) atomicAdd(hist + b, (unsigned long long)c);
+    }
+}
+
+// ===========================================================================
+// 2. device-wide exclusive scan of uint64 (out has count + 1 entries)
+// ===========================================================================
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = kScanThreads * kScanPer;
+
+// Exclusive scan of one chunk by one block (out[i] = carry + sum in[0, i));
+// returns the chunk total.
+__device__ uint64_t block_scan_chunk(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t carry) {
+    __shared__ uint64_t wsum[32];
+    __shared__ uint64_t s_total;
+    uint64_t v[kScanPer];
+    const uint64_t base = (uint64_t)threadIdx.x * kScanPer;
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        v[k] = (base + k < count) ? in[base + k] : 0;
+        s += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t x = wsum[lane];
+        uint64_t y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        wsum[lane] = y - x;
+        if (lane == 31) s_total = y;
+    }
+    __syncthreads();
+    uint64_t run = carry + wsum[warp] + (inc - s);
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        if (base + k < count) out[base + k] = run;
+        run += v[k];
+    }
+    const uint64_t tot = s_total;
+    __syncthreads();  // wsum and s_total are reused by the next chunk
+    return tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(const uint64_t* in, uint64_t count,
+                                                                     uint64_t* partial) {
+    const uint64_t base = (uint64_t)blockIdx.x * kScanChunk;
+    uint64_t s = 0;
+    const uint64_t end = umin64(count, base + kScanChunk);
+    for (uint64_t i = base + threadIdx.x; i < end; i += kScanThreads) s += in[i];
+    s = warp_sum_u64(s);
+    __shared__ uint64_t ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint64_t x = warp_sum_u64(ws[threadIdx.x]);
+        if (threadIdx.x == 0) partial[blockIdx.x] = x;
+    }
+}
+
+// Single block: exclusive scan of in[0, count) into out[0, count], out[count] = total.
+__global__ void __launch_bounds__(kScanThreads) scan_single_kernel(const uint64_t* in, uint64_t* out, uint64_t count) {
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < count; base += kScanChunk) {
+        uint64_t c = umin64((uint64_t)kScanChunk, count - base);
+        carry += block_scan_chunk(in + base, out + base, c, carry);
+    }
+    if (threadIdx.x == 0) out[count] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint64_t* in, uint64_t* out, uint64_t count,
+                                                                  const uint64_t* partial_excl) {
+    const uint64_t base = (uint64_t)blockIdx.x * kScanChunk;
+    uint64_t c = umin64((uint64_t)kScanChunk, count - base);
+    block_scan_chunk(in + base, out + base, c, partial_excl[blockIdx.x]);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[count] = partial_excl[gridDim.x];
+}
+
+// tmp must hold ceil(count / kScanChunk) + 1 + ceil(count / kScanChunk) + 1 entries
+static void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s) {
+    if (count <= (uint64_t)kScanChunk * 4) {
+        ProfScope ps("scan_single", s);
+        scan_single_kernel<<<1, kScanThreads, 0, s>>>(in, out, count);
+        return;
+    }
+    uint64_t nb = (count + kScanChunk - 1) / kScanChunk;
+    uint64_t* part = tmp;
+    uint64_t* part_ex = tmp + nb + 1;
+    {
+        ProfScope ps("scan_partials", s);
+        scan_partials_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, count, part);
+    }
+    {
+        ProfScope ps("scan_single", s);
+        scan_single_kernel<<<1, kScanThreads, 0, s>>>(part, part_ex, nb);
+    }
+    {
+        ProfScope ps("scan_apply", s);
+        scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, count, part_ex);
+    }
+}
+
+// ===========================================================================
+// 3. node table
+// ===========================================================================
+
+// slot = 2^l - 1 + p.  left[slot] = size of the left child (0 for non-nodes).
+__global__ void node_start_kernel(const CodeParams cp, const uint64_t* __restrict__ C, NodeEntry* __restrict__ nodes,
+                                  uint64_t* __restrict__ left, uint64_t nslots) {
+    uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= nslots) return;
+    uint32_t l = 63u - (uint32_t)__clzll((long long)(slot + 1));
+    uint64_t p = slot + 1 - (1ull << l);
+    uint64_t a = 0;
+    uint64_t w = node_info(cp, l, p, a);
+    NodeEntry e = {0, 0, 0, 0};
+    uint64_t lf = 0;
+    if (w >= 2) {
+        uint64_t m = node_mid(a, w);
+        e.start = C[a];
+        lf = C[m] - e.start;
+    }
+    nodes[slot] = e;
+    left[slot] = lf;
+}
+
+// excl = exclusive scan of left over all slots (nslots + 1 entries).
+// r0(slot) = zeros before the node = sum of left-child sizes of the earlier
+// nodes of its level.  Also writes per-level metadata.
+__global__ void node_finish_kernel(NodeEntry* __restrict__ nodes, const uint64_t* __restrict__ left,
+                                   const uint64_t* __restrict__ excl, uint64_t nslots) {
+    uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= nslots) return;
+    uint32_t l = 63u - (uint32_t)__clzll((long long)(slot + 1));
+    uint64_t lvl0 = (1ull << l) - 1;
+    NodeEntry e = nodes[slot];
+    uint64_t r0 = excl[slot] - excl[lvl0];
+    e.r0 = r0;
+    e.off0 = e.start - r0;
+    e.off1 = left[slot] + r0;
+    nodes[slot] = e;
+}
+
+struct MetaArgs {
+    uint64_t s0[kMaxLevels];  // first symbol whose code has length <= l (sigma if none)
+};
+
+// meta[2l] = size_l = C[s0_l]; meta[2l+1] = zeros_l = sum of left-child sizes at level l.
+__global__ void meta_kernel(const MetaArgs ma, uint32_t L, const uint64_t* __restrict__ C,
+                            const uint64_t* __restrict__ excl, uint64_t* __restrict__ meta) {
+    uint32_t l = threadIdx.x;
+    if (l >= L) return;
+    meta[2 * l] = C[ma.s0[l]];
+    meta[2 * l + 1] = excl[(2ull << l) - 1] - excl[(1ull << l) - 1];
+}
+
+// ===========================================================================
+// 4. the fused level pass
+// ===========================================================================
+
+constexpr int kTileBytes = 32768;
+constexpr int kLpThreads = 512;
+constexpr uint64_t kFlagAgg = 1, kFlagIncl = 2;
+
+// look-back state word: flag (2 bits) | aggregate (19 bits) | inclusive prefix (43 bits)
+__device__ __forceinline__ uint64_t lb_pack(uint64_t flag, uint64_t agg, uint64_t incl) {
+    return flag | (agg << 2) | (incl << 21);
+}
+__device__ __forceinline__ uint64_t lb_flag(uint64_t s) { return s & 3u; }
+__device__ __forceinline__ uint64_t lb_agg(uint64_t s) { return (s >> 2) & ((1u << 19) - 1); }
+__device__ __forceinline__ uint64_t lb_incl(uint64_t s) { return s >> 21; }
+
+struct LevelPassArgs {
+    const void* src;   // T_l
+    void* dst;         // T_{l+1}, or null at the last level
+    uint64_t size;     // size_l
+    uint64_t size_next;
+    uint64_t ntiles;
+    uint64_t words_alloc;
+    uint64_t* words;
+    uint64_t* l1;
+    uint16_t* l2;
+    uint64_t* s0;
+    uint64_t* s1;
+    uint64_t n_s0, n_s1;     // allocated sample entries (writes beyond are dropped)
+    const NodeEntry* nodes;  // level-l slice of the node table
+    uint64_t* state;         // ntiles look-back words, zeroed
+    uint32_t* counter;       // tile counter, zeroed
+    uint32_t* status;
+    uint32_t level;
+    uint32_t shift_bit;  // L - 1 - l
+    uint32_t pshift;     // L - l (prefix = code >> pshift), unused at level 0
+    uint32_t k_log2;
+    CodeParams cp;       // used when re-encoding at level 0
+};
+
+template <typename T, bool ENCODE>
+__global__ void __launch_bounds__(kLpThreads, 2) level_pass_kernel(const __grid_constant__ LevelPassArgs a) {
+    constexpr int W = sizeof(T);
+    constexpr int EPL = 4 / W;                  // elements per lane per round
+    constexpr int TE = kTileBytes / W;          // elements per tile
+    constexpr int ROUNDS = kTileBytes / 128;    // one round = one 128-byte row = 32 lanes x 4 bytes
+    constexpr int NWARP = kLpThreads / 32;
+    constexpr int RPW = ROUNDS / NWARP;
+    constexpr int EPR = 32 * EPL;               // elements per round
+    constexpr int TPL1 = 65536 / TE;            // tiles per L1 block
+    constexpr int RPL2 = 512 / EPR;             // rounds per L2 block
+    constexpr int WORDS = TE / 64;
+    constexpr int VE = 16 / W;                  // elements per 16 bytes
+    constexpr uint32_t EMASK = (W == 4) ? 0xFFFFFFFFu : ((1u << (8 * W)) - 1u);
+
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint32_t* in32 = reinterpret_cast<uint32_t*>(smem);
+    uint8_t* outb = smem + kTileBytes;
+    uint64_t* words = reinterpret_cast<uint64_t*>(smem + 2 * kTileBytes + 64);
+    uint32_t* bal = reinterpret_cast<uint32_t*>(words + WORDS);
+    uint32_t* rpre = bal + ROUNDS * EPL;  // ROUNDS + 1
+
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint64_t s_tile, s_E, s_EL1, s_ones, s_p;
+    __shared__ uint32_t s_single;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid == 0) {
+        s_tile = atomicAdd(a.counter, 1u);
+        mbar_init(&mbar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= a.ntiles) return;
+    const uint64_t t0 = tile * TE;
+    const uint32_t count = (uint32_t)umin64((uint64_t)TE, a.size - t0);
+    const uint32_t bytes = count * W;
+    const uint32_t b16 = bytes & ~15u;
+    const uint8_t* srcb = reinterpret_cast<const uint8_t*>(a.src) + t0 * W;
+
+    // ---- phase 0: tile -> shared memory (TMA bulk copy + ragged tail) ----
+    if (tid == 0 && b16) {
+        mbar_expect_tx(&mbar, b16);
+        bulk_g2s(smem, srcb, b16, &mbar);
+    }
+    for (uint32_t i = b16 + tid; i < bytes; i += kLpThreads) smem[i] = srcb[i];
+    if (b16) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(&mbar, 0)) {
+            if (++spins > kSpinCap) {
+                if (lane == 0) set_status(a.status, kStTimeout);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 1: level bits per round (ballots), round counts ----
+    const uint32_t shift = a.shift_bit;
+    for (int rr = 0; rr < RPW; rr++) {
+        const int r = warp * RPW + rr;
+        uint32_t v = in32[r * 32 + lane];
+        const uint32_t j0 = r * EPR + lane * EPL;
+        if (ENCODE) {
+            uint32_t nv = 0;
+#pragma unroll
+            for (int k = 0; k < EPL; k++) {
+                uint32_t e = (v >> (8 * W * k)) & EMASK;
+                uint32_t code = 0, len;
+                if (j0 + k < count) encode(a.cp, e, code, len);
+                nv |= (code & EMASK) << (8 * W * k);
+            }
+            v = nv;
+            in32[r * 32 + lane] = v;
+        }
+        uint32_t bl[EPL];
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int k = 0; k < EPL; k++) {
+            uint32_t e = (v >> (8 * W * k)) & EMASK;
+            bool bit = (j0 + k < count) && ((e >> shift) & 1u);
+            bl[k] = __ballot_sync(0xffffffffu, bit);
+            cnt += __popc(bl[k]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < EPL; k++) bal[r * EPL + k] = bl[k];
+            rpre[r] = cnt;
+            if (EPL == 1) {
+                reinterpret_cast<uint32_t*>(words)[r] = bl[0];
+            } else if (EPL == 2) {
+                words[r] = spread2(bl[0]) | (spread2(bl[EPL > 1 ? 1 : 0]) << 1);
+            } else {
+                uint64_t w0 = 0, w1 = 0;
+#pragma unroll
+                for (int k = 0; k < EPL; k++) {
+                    w0 |= spread4(bl[k]) << k;
+                    w1 |= spread4(bl[k] >> 16) << k;
+                }
+                words[2 * r] = w0;
+                words[2 * r + 1] = w1;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: tile scan + look-back (warp 0) || word stores (other warps) ----
+    if (warp == 0) {
+        constexpr int PER = ROUNDS / 32;
+        uint32_t loc[PER];
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            loc[k] = rpre[lane * PER + k];
+            s += loc[k];
+        }
+        uint32_t inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        uint32_t run = inc - s;
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            rpre[lane * PER + k] = run;
+            run += loc[k];
+        }
+        const uint64_t ones = __shfl_sync(0xffffffffu, inc, 31);
+        if (lane == 0) rpre[ROUNDS] = (uint32_t)ones;
+        // publish the aggregate, then look back for the exclusive prefix
+        if (lane == 0) st_relaxed_u64(a.state + tile, tile == 0 ? lb_pack(kFlagIncl, ones, ones) : lb_pack(kFlagAgg, ones, 0));
+        uint64_t excl = 0;
+        if (tile > 0) {
+            int64_t base = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (true) {
+                const int64_t idx = base - lane;
+                uint64_t st = idx >= 0 ? ld_relaxed_u64(a.state + idx) : lb_pack(kFlagIncl, 0, 0);
+                while (__any_sync(0xffffffffu, lb_flag(st) == 0)) {
+                    if (++spins > kSpinCap) {
+                        if (lane == 0) set_status(a.status, kStTimeout);
+                        if (lb_flag(st) == 0) st = lb_pack(kFlagIncl, 0, 0);
+                        break;
+                    }
+                    __nanosleep(20);
+                    if (lb_flag(st) == 0) st = ld_relaxed_u64(a.state + idx);
+                }
+                const uint32_t im = __ballot_sync(0xffffffffu, lb_flag(st) == kFlagIncl);
+                if (im) {
+                    const int first = __ffs(im) - 1;
+                    uint64_t v = lane < first ? lb_agg(st) : (lane == first ? lb_incl(st) : 0);
+                    excl += warp_sum_u64(v);
+                    break;
+                }
+                excl += warp_sum_u64(lb_agg(st));
+                base -= 32;
+            }
+            if (lane == 0) st_relaxed_u64(a.state + tile, lb_pack(kFlagIncl, ones, excl + ones));
+        }
+        // ones before the enclosing L1 block
+        const uint32_t q = (uint32_t)(tile % TPL1);
+        uint64_t sub = 0;
+        if (q && lane < (int)q) sub = lb_agg(ld_relaxed_u64(a.state + tile - q + lane));
+        sub = warp_sum_u64(sub);
+        if (lane == 0) {
+            s_E = excl;
+            s_EL1 = excl - sub;
+            s_ones = ones;
+        }
+    } else {
+        const uint32_t nw = (count + 63) / 64;
+        for (uint32_t i = tid - 32; i < nw; i += kLpThreads - 32) a.words[tile * WORDS + i] = words[i];
+        if (warp == 1 && lane == 0) {
+            // does the tile lie inside one node of this level?
+            if (a.level == 0) {
+                s_single = 1;
+                s_p = 0;
+            } else {
+                const T* te = reinterpret_cast<const T*>(smem);
+                uint64_t p0 = (uint64_t)te[0] >> a.pshift;
+                uint64_t p1 = (uint64_t)te[count - 1] >> a.pshift;
+                s_single = p0 == p1;
+                s_p = p0;
+            }
+        }
+        if (tile == a.ntiles - 1) {
+            // zero the padding words after the level's last word
+            const uint64_t first_pad = (a.size + 63) / 64;
+            for (uint64_t i = first_pad + (tid - 32); i < a.words_alloc; i += kLpThreads - 32) a.words[i] = 0;
+        }
+    }
+    __syncthreads();
+
+    const uint64_t E = s_E, EL1 = s_EL1, ones = s_ones;
+    const uint64_t zeros = count - ones;
+    const uint64_t R0 = t0 - E;  // zeros before the tile
+
+    // ---- phase 3: L1/L2 counters and select samples ----
+    {
+        const uint32_t nl2 = (count + 511) / 512;
+        for (uint32_t b = tid; b < nl2; b += kLpThreads)
+            a.l2[(t0 >> 9) + b] = (uint16_t)(E - EL1 + rpre[b * RPL2]);
+        if (tid == 0) {
+            if (tile % TPL1 == 0) a.l1[t0 >> 16] = E;
+            if (tile == a.ntiles - 1) {
+                const uint64_t end = t0 + count;
+                if ((end & 511) == 0) {
+                    if ((end & 65535) == 0) {
+                        a.l1[end >> 16] = E + ones;
+                        a.l2[end >> 9] = 0;
+                    } else {
+                        a.l2[end >> 9] = (uint16_t)(E + ones - EL1);
+                    }
+                }
+            }
+            if (tile == 0) {
+                a.s0[0] = 0;
+                a.s1[0] = 0;
+            }
+        }
+        const uint32_t kl = a.k_log2;
+        const uint64_t m1lo = (E >> kl) + 1, m1hi = (E + ones) >> kl;
+        const uint64_t m0lo = (R0 >> kl) + 1, m0hi = (R0 + zeros) >> kl;
+        const uint64_t ns1 = m1hi + 1 - m1lo, ns0 = m0hi + 1 - m0lo;
+        for (uint64_t idx = tid; idx < ns1 + ns0; idx += kLpThreads) {
+            const uint32_t b = idx < ns1;
+            const uint64_t m = b ? m1lo + idx : m0lo + (idx - ns1);
+            const uint32_t t = (uint32_t)((m << kl) - (b ? E : R0));  // 1-based rank within the tile
+            int lo = 0, hi = ROUNDS - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                uint32_t c = b ? rpre[mid] : (uint32_t)(mid * EPR) - rpre[mid];
+                if (c < t) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint32_t before = b ? rpre[lo] : (uint32_t)(lo * EPR) - rpre[lo];
+            const uint32_t tt = t - before;
+            uint64_t w0, w1 = 0;
+            if (EPL == 4) {
+                w0 = words[2 * lo];
+                w1 = words[2 * lo + 1];
+            } else if (EPL == 2) {
+                w0 = words[lo];
+            } else {
+                w0 = reinterpret_cast<const uint32_t*>(words)[lo];
+            }
+            if (!b) {
+                w0 = ~w0;
+                w1 = ~w1;
+                if (EPL == 1) w0 &= 0xFFFFFFFFull;
+                if (EPL <= 2) w1 = 0;
+            }
+            const uint32_t c0 = __popcll(w0);
+            const uint32_t pin = c0 >= tt ? select_in_word(w0, tt) : 64 + select_in_word(w1, tt - c0);
+            if (m < (b ? a.n_s1 : a.n_s0)) (b ? a.s1 : a.s0)[m] = t0 + (uint64_t)lo * EPR + pin;
+        }
+    }
+
+    if (a.dst == nullptr) return;
+
+    // ---- phase 4: stable partition of the tile by the level bit (shared memory) ----
+    const bool single = s_single != 0;
+    uint64_t D0 = 0, D1 = 0;
+    uint32_t pad0 = 0, OB = (uint32_t)zeros;
+    if (single) {
+        const NodeEntry* ne = a.nodes + s_p;
+        D0 = __ldg(&ne->off0) + R0;
+        D1 = __ldg(&ne->off1) + E;
+        pad0 = (uint32_t)(D0 % VE);
+        OB = ((pad0 + (uint32_t)zeros + VE - 1) / VE) * VE + (uint32_t)(D1 % VE);
+    }
+    T* out = reinterpret_cast<T*>(outb);
+    const uint32_t ltmask = (1u << lane) - 1u;
+    for (int rr = 0; rr < RPW; rr++) {
+        const int r = warp * RPW + rr;
+        const uint32_t v = in32[r * 32 + lane];
+        const uint32_t j0 = r * EPR + lane * EPL;
+        uint32_t ob = rpre[r];
+        uint32_t bl[EPL];
+#pragma unroll
+        for (int k = 0; k < EPL; k++) {
+            bl[k] = bal[r * EPL + k];
+            ob += __popc(bl[k] & ltmask);
+        }
+#pragma unroll
+        for (int k = 0; k < EPL; k++) {
+            const uint32_t j = j0 + k;
+            if (j < count) {
+                const uint32_t bit = (bl[k] >> lane) & 1u;
+                const uint32_t idx = bit ? OB + ob : pad0 + j - ob;
+                out[idx] = (T)((v >> (8 * W * k)) & EMASK);
+                ob += bit;
+            }
+        }
+    }
+    __syncthreads();
+
+    T* dst = reinterpret_cast<T*>(a.dst);
+    const uint64_t lim = a.size_next;
+    if (single) {
+        // two runs with the same alignment in shared and global memory: 16-byte copies
+#pragma unroll
+        for (int run = 0; run < 2; run++) {
+            uint64_t D = run ? D1 : D0;
+            uint64_t len = run ? ones : zeros;
+            const uint32_t so = run ? OB : pad0;  // element offset in shared memory
+            if (D >= lim || len == 0) continue;
+            len = umin64(len, lim - D);
+            const uint64_t gb = D * W, ge = (D + len) * W;
+            const uint64_t hb = umin64((gb + 15) & ~(uint64_t)15, ge);
+            const uint64_t be = umax64(hb, ge & ~(uint64_t)15);
+            uint8_t* db = reinterpret_cast<uint8_t*>(dst);
+            const uint64_t sbase = (uint64_t)so * W;  // shared byte of global byte g: sbase + (g - gb)
+            for (uint64_t g = gb + (uint64_t)tid * W; g < hb; g += (uint64_t)kLpThreads * W)
+                *reinterpret_cast<T*>(db + g) = *reinterpret_cast<const T*>(outb + sbase + (g - gb));
+            for (uint64_t g = hb + (uint64_t)tid * 16; g < be; g += (uint64_t)kLpThreads * 16)
+                *reinterpret_cast<uint4*>(db + g) = *reinterpret_cast<const uint4*>(outb + sbase + (g - gb));
+            for (uint64_t g = be + (uint64_t)tid * W; g < ge; g += (uint64_t)kLpThreads * W)
+                *reinterpret_cast<T*>(db + g) = *reinterpret_cast<const T*>(outb + sbase + (g - gb));
+        }
+    } else {
+        // several nodes: every element finds its node's offsets from its own code
+        const uint32_t ps = a.pshift;
+        for (uint32_t i = tid; i < zeros; i += kLpThreads) {
+            const T x = out[i];
+            const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off0) + R0 + i;
+            if (Dx < lim) dst[Dx] = x;
+        }
+        for (uint32_t i = tid; i < ones; i += kLpThreads) {
+            const T x = out[OB + i];
+            const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off1) + E + i;
+            if (Dx < lim) dst[Dx] = x;
+        }
+    }
+}
+
+template <typename T, bool ENC>
+static size_t level_pass_smem() {
+    constexpr int W = sizeof(T);
+    constexpr int TE = kTileBytes / W;
+    constexpr int ROUNDS = kTileBytes / 128;
+    return 2 * kTileBytes + 64 + (TE / 64) * 8 + ROUNDS * (4 / W) * 4 + (ROUNDS + 1) * 4;
+}
+
+template <typename T, bool ENC>
+static cudaError_t launch_level_pass(const LevelPassArgs& a, cudaStream_t s) {
+    static bool configured = false;
+    size_t sm = level_pass_smem<T, ENC>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<T, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    ProfScope ps(sizeof(T) == 1 ? "level_pass_u8" : (sizeof(T) == 2 ? "level_pass_u16" : "level_pass_u32"), s);
+    level_pass_kernel<T, ENC><<<(unsigned)a.ntiles, kLpThreads, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_hist(const void* S, uint64_t n, uint32_t sigma, unsigned long long* hist, uint32_t* status,
+                               cudaStream_t s) {
+    const uint32_t budget = 64 * 1024;  // bytes of shared memory for sub-histograms
+    uint32_t sbins = std::min<uint32_t>(sigma, budget / 4);
+    uint32_t copies = std::max<uint32_t>(1, std::min<uint32_t>(16, budget / (4 * std::max<uint32_t>(sbins, 1))));
+    size_t sm = (size_t)sbins * copies * 4;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(hist_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        configured = true;
+    }
+    int blocks = sm_count() * 3;
+    ProfScope ps("histogram", s);
+    hist_kernel<T><<<blocks, 512, sm, s>>>(reinterpret_cast<const T*>(S), n, sigma, sbins, copies, hist, status);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// host orchestration
+// ===========================================================================
+
+static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t w, uint32_t sample_k, cudaStream_t s,
+                     wt_tree_s* t) {
+    const CodeParams cp = make_code_params(sigma);
+    const uint32_t L = cp.L;
+    uint32_t k_log2 = 0;
+    while ((1u << k_log2) < sample_k) k_log2++;
+
+    t->desc.cp = cp;
+    t->desc.n = n;
+    t->desc.k_log2 = k_log2;
+    t->symbol_bytes = w;
+    t->sample_k = sample_k;
+
+    // ---- header memory: status, C, node table, meta ----
+    const uint64_t nslots = L ? ((1ull << L) - 1) : 0;
+    size_t off_status = 0;
+    size_t off_C = 256;
+    size_t off_nodes = align_up(off_C + (sigma + 1ull) * 8, 256);
+    size_t hdr = align_up(off_nodes + std::max<uint64_t>(nslots, 1) * sizeof(NodeEntry), 256);
+    WT_CUDA_TRY(dev_alloc(&t->hdr_mem, hdr, s));
+    t->hdr_bytes = hdr;
+    uint8_t* H = reinterpret_cast<uint8_t*>(t->hdr_mem);
+    t->desc.status = reinterpret_cast<uint32_t*>(H + off_status);
+    uint64_t* C = reinterpret_cast<uint64_t*>(H + off_C);
+    NodeEntry* nodes = reinterpret_cast<NodeEntry*>(H + off_nodes);
+    t->desc.C = C;
+    t->desc.nodes = nodes;
+
+    // ---- scratch for steps 1-3 ----
+    const uint64_t scan_n = std::max<uint64_t>(sigma, nslots);
+    const uint64_t scan_tmp = 2 * ((scan_n + kScanChunk - 1) / kScanChunk + 2);
+    size_t s_hist = 0;
+    size_t s_left = align_up(s_hist + (uint64_t)sigma * 8, 256);
+    size_t s_excl = align_up(s_left + std::max<uint64_t>(nslots, 1) * 8, 256);
+    size_t s_tmp = align_up(s_excl + (nslots + 1) * 8, 256);
+    size_t s_meta = align_up(s_tmp + scan_tmp * 8, 256);
+    size_t s_end = align_up(s_meta + 2 * kMaxLevels * 8, 256);
+    void* scratch = nullptr;
+    WT_CUDA_TRY(dev_alloc(&scratch, s_end, s));
+    uint8_t* X = reinterpret_cast<uint8_t*>(scratch);
+    uint64_t* hist = reinterpret_cast<uint64_t*>(X + s_hist);
+    uint64_t* left = reinterpret_cast<uint64_t*>(X + s_left);
+    uint64_t* excl = reinterpret_cast<uint64_t*>(X + s_excl);
+    uint64_t* tmp = reinterpret_cast<uint64_t*>(X + s_tmp);
+    uint64_t* meta = reinterpret_cast<uint64_t*>(X + s_meta);
+
+    WT_CUDA_TRY(cudaMemsetAsync(t->hdr_mem, 0, hdr, s));
+    WT_CUDA_TRY(cudaMemsetAsync(hist, 0, (uint64_t)sigma * 8, s));
+
+    // 1. histogram
+    if (n) {
+        cudaError_t e = w == 1 ? launch_hist<uint8_t>(d_symbols, n, sigma, (unsigned long long*)hist, t->desc.status, s)
+                        : w == 2 ? launch_hist<uint16_t>(d_symbols, n, sigma, (unsigned long long*)hist, t->desc.status, s)
+                                 : launch_hist<uint32_t>(d_symbols, n, sigma, (unsigned long long*)hist, t->desc.status, s);
+        if (e != cudaSuccess) { dev_free(scratch, s); return WT_ECUDA; }
+    }
+    // 2. C
+    device_exclusive_scan(hist, C, sigma, tmp, s);
+    // 3. nodes + meta
+    if (L) {
+        {
+            ProfScope ps("node_start", s);
+            node_start_kernel<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(cp, C, nodes, left, nslots);
+        }
+        device_exclusive_scan(left, excl, nslots, tmp, s);
+        {
+            ProfScope ps("node_finish", s);
+            node_finish_kernel<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(nodes, left, excl, nslots);
+        }
+        MetaArgs ma;
+        for (uint32_t l = 0; l < L; l++) {
+            // first segment whose code length is <= l (lengths never increase with the symbol)
+            uint64_t s0 = sigma;
+            for (uint32_t i = 0; i < cp.r; i++) {
+                uint32_t len = (i + 1 < cp.r || cp.pow2) ? (cp.pow2 ? cp.L : i + 1 + cp.e[i]) : (cp.r - 1 + cp.e[i]);
+                if (len <= l) { s0 = cp.P[i]; break; }
+            }
+            ma.s0[l] = s0;
+        }
+        ProfScope ps("meta", s);
+        meta_kernel<<<1, 32, 0, s>>>(ma, L, C, excl, meta);
+    }
+    WT_CUDA_TRY(cudaGetLastError());
+    uint64_t hmeta[2 * kMaxLevels] = {0};
+    uint32_t hstatus = 0;
+    if (L) WT_CUDA_TRY(cudaMemcpyAsync(hmeta, meta, 2 * L * 8, cudaMemcpyDeviceToHost, s));
+    WT_CUDA_TRY(cudaMemcpyAsync(&hstatus, t->desc.status, 4, cudaMemcpyDeviceToHost, s));
+    WT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hstatus & kStSymbol) {
+        dev_free(scratch, s);
+        return WT_ESYMBOL;
+    }
+
+    // ---- level memory ----
+    struct Lay { size_t words, l1, l2, s0, s1; uint64_t walloc; };
+    std::vector<Lay> lay(L);
+    size_t off = 0;
+    for (uint32_t l = 0; l < L; l++) {
+        const uint64_t size = hmeta[2 * l], zeros = hmeta[2 * l + 1], ones = size - zeros;
+        t->level_size[l] = size;
+        t->level_ones[l] = ones;
+        Lay& y = lay[l];
+        y.walloc = align_up((size + 63) / 64 + 16, 16);
+        y.words = off;
+        off = align_up(off + y.walloc * 8, 256);
+        y.l1 = off;
+        off = align_up(off + (size / kL1Bits + 1) * 8, 256);
+        y.l2 = off;
+        off = align_up(off + (size / kL2Bits + 1) * 2, 256);
+        y.s0 = off;
+        off = align_up(off + ((zeros >> k_log2) + 1) * 8, 256);
+        y.s1 = off;
+        off = align_up(off + ((ones >> k_log2) + 1) * 8, 256);
+    }
+    t->lvl_bytes = std::max<size_t>(off, 256);
+    if (dev_alloc(&t->lvl_mem, t->lvl_bytes, s) != cudaSuccess) {
+        dev_free(scratch, s);
+        return WT_ENOMEM;
+    }
+    uint8_t* M = reinterpret_cast<uint8_t*>(t->lvl_mem);
+    for (uint32_t l = 0; l < L; l++) {
+        LevelDesc& d = t->desc.lv[l];
+        d.words = reinterpret_cast<uint64_t*>(M + lay[l].words);
+        d.l1 = reinterpret_cast<uint64_t*>(M + lay[l].l1);
+        d.l2 = reinterpret_cast<uint16_t*>(M + lay[l].l2);
+        d.s0 = reinterpret_cast<uint64_t*>(M + lay[l].s0);
+        d.s1 = reinterpret_cast<uint64_t*>(M + lay[l].s1);
+        d.size = t->level_size[l];
+        d.ones = t->level_ones[l];
+    }
+
+    // ---- level passes ----
+    if (L && n) {
+        const uint64_t te = kTileBytes / w;
+        const uint64_t max_tiles = (n + te - 1) / te;
+        const uint64_t tbytes = align_up(n * w, 256);
+        const size_t b_state = align_up(max_tiles * 8, 256);
+        void* work = nullptr;
+        const size_t work_bytes = 2 * tbytes + b_state + 256;
+        if (dev_alloc(&work, work_bytes, s) != cudaSuccess) {
+            dev_free(scratch, s);
+            return WT_ENOMEM;
+        }
+        uint8_t* Wm = reinterpret_cast<uint8_t*>(work);
+        void* buf[2] = {Wm, Wm + tbytes};
+        uint64_t* state = reinterpret_cast<uint64_t*>(Wm + 2 * tbytes);
+        uint32_t* counters = reinterpret_cast<uint32_t*>(Wm + 2 * tbytes + b_state);
+        WT_CUDA_TRY(cudaMemsetAsync(counters, 0, 256, s));
+        for (uint32_t l = 0; l < L; l++) {
+            const uint64_t size = t->level_size[l];
+            if (size == 0) continue;
+            LevelPassArgs a;
+            memset(&a, 0, sizeof(a));
+            a.src = l == 0 ? d_symbols : buf[(l - 1) & 1];
+            a.dst = (l + 1 < L) ? buf[l & 1] : nullptr;
+            a.size = size;
+            a.size_next = (l + 1 < L) ? t->level_size[l + 1] : 0;
+            a.ntiles = (size + te - 1) / te;
+            a.words_alloc = lay[l].walloc;
+            a.words = reinterpret_cast<uint64_t*>(M + lay[l].words);
+            a.l1 = reinterpret_cast<uint64_t*>(M + lay[l].l1);
+            a.l2 = reinterpret_cast<uint16_t*>(M + lay[l].l2);
+            a.s0 = reinterpret_cast<uint64_t*>(M + lay[l].s0);
+            a.s1 = reinterpret_cast<uint64_t*>(M + lay[l].s1);
+            a.n_s0 = ((size - t->level_ones[l]) >> k_log2) + 1;
+            a.n_s1 = (t->level_ones[l] >> k_log2) + 1;
+            a.nodes = nodes + ((1ull << l) - 1);
+            a.state = state;
+            a.counter = counters + l;
+            a.status = t->desc.status;
+            a.level = l;
+            a.shift_bit = L - 1 - l;
+            a.pshift = L - l;
+            a.k_log2 = k_log2;
+            a.cp = cp;
+            WT_CUDA_TRY(cudaMemsetAsync(state, 0, a.ntiles * 8, s));
+            const bool enc = (l == 0) && !cp.pow2;
+            cudaError_t e;
+            if (w == 1) e = enc ? launch_level_pass<uint8_t, true>(a, s) : launch_level_pass<uint8_t, false>(a, s);
+            else if (w == 2) e = enc ? launch_level_pass<uint16_t, true>(a, s) : launch_level_pass<uint16_t, false>(a, s);
+            else e = enc ? launch_level_pass<uint32_t, true>(a, s) : launch_level_pass<uint32_t, false>(a, s);
+            if (e != cudaSuccess) {
+                dev_free(work, s);
+                dev_free(scratch, s);
+                return WT_ECUDA;
+            }
+        }
+        dev_free(work, s);
+    } else {
+        // empty levels still need their first counter / sample entries
+        for (uint32_t l = 0; l < L; l++) {
+            WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].words, 0, lay[l].walloc * 8, s));
+            WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].l1, 0, 8, s));
+            WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].l2, 0, 2, s));
+            WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].s0, 0, 8, s));
+            WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].s1, 0, 8, s));
+        }
+    }
+    dev_free(scratch, s);
+    return WT_OK;
+}
+
+}  // namespace wt

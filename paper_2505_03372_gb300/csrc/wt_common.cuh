@@ -1,0 +1,316 @@
+// Shared definitions of libwt's CUDA sources.
+//
+// Reduced codes (Section 5.1, Algorithm 3) are not tabulated: they follow in
+// closed form from the binary expansion of sigma.  Write
+// sigma = 2^e[0] + 2^e[1] + ... + 2^e[r-1] with e[0] > ... > e[r-1] and
+// P[i] = 2^e[0] + ... + 2^e[i-1].  The alphabet split of Section 5.1 (a node
+// [a,b) sends [a, a+prevPow2(b-a)) left) peels these powers off the right
+// spine, so [0, sigma) falls into r segments [P[i], P[i+1]), each a complete
+// subtree of depth e[i].  A symbol of segment i < r-1 has the code
+// 1^i 0 (e[i] low bits of s) and length i + 1 + e[i]; a symbol of the last
+// segment has 1^(r-1) (e[r-1] low bits) and length r - 1 + e[r-1].  For sigma
+// a power of two (r = 1) this is the identity code of length L = lg sigma.
+// Segment i of a symbol s is found from the highest bit where s and sigma
+// differ (sigma has a one there and s a zero).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wt.h"
+
+namespace wt {
+
+constexpr uint32_t kL1Bits = WT_L1_BITS;  // Section 4.1
+constexpr uint32_t kL2Bits = WT_L2_BITS;  // Section 6: |L2| = 512
+constexpr uint32_t kMaxLevels = WT_MAX_LEVELS;
+constexpr uint32_t kMaxSigmaLog = 26;
+
+// sticky device status bits (one per wt_status value)
+constexpr uint32_t kStSymbol = 1u << WT_ESYMBOL;
+constexpr uint32_t kStQuery = 1u << WT_EQUERY;
+constexpr uint32_t kStTimeout = 1u << WT_ETIMEOUT;
+
+// iteration cap of every device-side spin wait
+constexpr uint32_t kSpinCap = 1u << 22;
+
+struct CodeParams {
+    uint32_t sigma;
+    uint32_t L;     // ceil(lg sigma)
+    uint32_t r;     // popcount(sigma); 1 for a power of two
+    uint32_t pow2;  // sigma is a power of two (identity codes)
+    uint32_t e[32]; // exponents of sigma's set bits, descending; e[0] = L for a power of two
+    uint64_t P[33]; // P[i] = sum_{k < i} 2^e[k]
+};
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+__host__ __device__ inline uint32_t clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __clz(x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+__host__ __device__ inline uint32_t popc32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __popc(x);
+#else
+    return __builtin_popcount(x);
+#endif
+}
+__host__ __device__ inline uint32_t popc64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return __popcll(x);
+#else
+    return __builtin_popcountll(x);
+#endif
+}
+
+inline CodeParams make_code_params(uint32_t sigma) {
+    CodeParams cp = {};
+    cp.sigma = sigma;
+    uint32_t L = 0;
+    while ((1ull << L) < sigma) L++;
+    cp.L = L;
+    cp.pow2 = (sigma & (sigma - 1)) == 0;
+    if (cp.pow2) {
+        cp.r = 1;
+        cp.e[0] = L;
+    } else {
+        uint32_t r = 0;
+        for (int b = 31; b >= 0; b--)
+            if (sigma >> b & 1u) cp.e[r++] = (uint32_t)b;
+        cp.r = r;
+    }
+    cp.P[0] = 0;
+    for (uint32_t i = 0; i < cp.r; i++) cp.P[i + 1] = cp.P[i] + (1ull << cp.e[i]);
+    return cp;
+}
+
+// Code of symbol s (s < sigma), left-aligned in L bits, and its length.
+__host__ __device__ inline void encode(const CodeParams& cp, uint32_t s, uint32_t& code, uint32_t& len) {
+    if (cp.pow2) {
+        code = s;
+        len = cp.L;
+        return;
+    }
+    uint32_t d = s ^ cp.sigma;
+    uint32_t e = 31u - clz32(d);                   // segment exponent
+    uint32_t j = popc32((uint32_t)((uint64_t)cp.sigma >> (e + 1)));  // segment index
+    uint32_t low = s & ((1u << e) - 1u);
+    uint64_t str;
+    if (cp.sigma & ((1u << e) - 1u)) {  // not the last segment: 1^j 0 low
+        str = ((((uint64_t)1 << j) - 1) << (e + 1)) | low;
+        len = j + 1 + e;
+    } else {  // last segment: 1^(r-1) low
+        str = ((((uint64_t)1 << j) - 1) << e) | low;
+        len = j + e;
+    }
+    code = (uint32_t)(str << (cp.L - len));
+}
+
+// Node at depth l with code prefix p (l bits): first symbol a and width
+// (number of symbols below it).  Returns width 0 if no node of the
+// (reduced) tree has this prefix.  A width of 1 is a leaf.
+__host__ __device__ inline uint64_t node_info(const CodeParams& cp, uint32_t l, uint64_t p, uint64_t& a) {
+    uint32_t r = cp.r;
+    uint32_t j = 0;  // leading ones of p as an l-bit string
+    if (l > 0) {
+        uint64_t x = ~(p << (64 - l));
+#ifdef __CUDA_ARCH__
+        j = (uint32_t)__clzll((long long)x);
+#else
+        j = x ? (uint32_t)__builtin_clzll(x) : 64u;
+#endif
+        if (j > l) j = l;
+    }
+    if (j + 1 >= r) {  // inside the last segment's complete subtree (always for a power of two)
+        uint32_t t = l - (r - 1);
+        uint32_t er = cp.e[r - 1];
+        if (t > er) return 0;
+        uint64_t low = p & ((1ull << t) - 1);
+        a = cp.P[r - 1] + (low << (er - t));
+        return 1ull << (er - t);
+    }
+    if (j == l) {  // on the right spine above the last segment: [P[l], sigma)
+        a = cp.P[l];
+        return (uint64_t)cp.sigma - cp.P[l];
+    }
+    uint32_t t = l - j - 1;  // free bits inside segment j
+    uint32_t ek = cp.e[j];
+    if (t > ek) return 0;
+    uint64_t low = p & ((1ull << t) - 1);
+    a = cp.P[j] + (low << (ek - t));
+    return 1ull << (ek - t);
+}
+
+// Split point of an internal node [a, a+width): a + prevPow2(width).
+__host__ __device__ inline uint64_t node_mid(uint64_t a, uint64_t width) {
+    uint64_t p = 1;
+#ifdef __CUDA_ARCH__
+    p = 1ull << (63 - __clzll((long long)(width - 1)));
+#else
+    while (p * 2 < width) p *= 2;
+#endif
+    return a + p;
+}
+
+// Per-node entry, heap-indexed: slot 2^l - 1 + p for depth l, prefix p.
+struct NodeEntry {
+    uint64_t start;  // C[a]: first position of the node in level l
+    uint64_t r0;     // rank_0(l, start): precomputed node-start rank (Section 5.2.1)
+    uint64_t off0;   // start - r0: next-level position of a zero = off0 + rank_0(pos)
+    uint64_t off1;   // C[mid] - start + r0: next-level position of a one = off1 + rank_1(pos)
+};
+
+struct LevelDesc {
+    const uint64_t* words;  // bits, LSB-first, 128-byte aligned
+    const uint64_t* l1;     // floor(size/65536) + 1 entries
+    const uint16_t* l2;     // floor(size/512) + 1 entries
+    const uint64_t* s0;     // floor(zeros/K) + 1 entries, s0[0] = 0
+    const uint64_t* s1;     // floor(ones/K) + 1 entries, s1[0] = 0
+    uint64_t size;
+    uint64_t ones;
+};
+
+// Everything a query kernel needs, passed by value as a __grid_constant__.
+struct TreeDesc {
+    CodeParams cp;
+    uint64_t n;
+    uint32_t k_log2;  // select sample interval K = 2^k_log2
+    uint32_t pad;
+    const NodeEntry* nodes;
+    const uint64_t* C;  // sigma + 1
+    uint32_t* status;
+    LevelDesc lv[kMaxLevels];
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ ulonglong2 ldg_nc_v2(const uint64_t* p) {
+    ulonglong2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
+    return v;
+}
+
+// Binary rank_1 (Algorithm 1 with 64-bit words): ones in B_l[0, pos), and the
+// bit at pos (needed by access, returned with the rank as in Section 5.2.1).
+// Reads the L1 and L2 counters and the words of pos's 512-bit block up to pos.
+__device__ __forceinline__ uint64_t rank1_bit(const LevelDesc& lv, uint64_t pos, uint32_t& bit) {
+    const uint64_t blk = pos >> 9;
+    const uint32_t wi = (uint32_t)(pos >> 6) & 7u;
+    const uint32_t bi = (uint32_t)pos & 63u;
+    const uint64_t* base = lv.words + (blk << 3);
+    uint64_t w[8];
+    ulonglong2 v = ldg_nc_v2(base);
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = w[3] = w[4] = w[5] = w[6] = w[7] = 0;
+    if (wi >= 2) { v = ldg_nc_v2(base + 2); w[2] = v.x; w[3] = v.y; }
+    if (wi >= 4) { v = ldg_nc_v2(base + 4); w[4] = v.x; w[5] = v.y; }
+    if (wi >= 6) { v = ldg_nc_v2(base + 6); w[6] = v.x; w[7] = v.y; }
+    uint64_t r = __ldg(lv.l1 + (pos >> 16)) + (uint64_t)__ldg(lv.l2 + blk);
+    uint32_t c = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < 8; k++) {
+        uint64_t m = k < wi ? ~0ull : (k == wi ? ((1ull << bi) - 1ull) : 0ull);
+        c += __popcll(w[k] & m);
+    }
+    uint64_t cur = w[0];
+#pragma unroll
+    for (uint32_t k = 1; k < 8; k++) cur = (k == wi) ? w[k] : cur;
+    bit = (uint32_t)(cur >> bi) & 1u;
+    return r + c;
+}
+
+__device__ __forceinline__ uint64_t rank1(const LevelDesc& lv, uint64_t pos) {
+    uint32_t b;
+    return rank1_bit(lv, pos, b);
+}
+
+__device__ __forceinline__ uint32_t bit_at(const LevelDesc& lv, uint64_t pos) {
+    return (uint32_t)(__ldg(lv.words + (pos >> 6)) >> (pos & 63)) & 1u;
+}
+
+// Position (0..63) of the k-th (1-based) set bit of x; popc(x) >= k.  Binary
+// halving with popcounts, six steps for a 64-bit word (Section 5.4.1).
+__device__ __forceinline__ uint32_t select_in_word(uint64_t x, uint32_t k) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t wdt = 32; wdt >= 1; wdt >>= 1) {
+        uint32_t c = __popcll(x & ((1ull << wdt) - 1ull));
+        if (k > c) {
+            k -= c;
+            x >>= wdt;
+            pos += wdt;
+        }
+    }
+    return pos;
+}
+
+// Binary select (Algorithm 2, with the readings of the design notes): the
+// position of the k-th (1-based) bit equal to b in level lv, 1 <= k <= count_b.
+// The samples around k bound the L1 blocks (linear scan, usually one or two)
+// and the L2 blocks (binary search); the word scan ends with select_in_word.
+__device__ __forceinline__ uint64_t select_b(const LevelDesc& lv, uint32_t b, uint64_t k, uint32_t k_log2) {
+    const uint64_t* S = b ? lv.s1 : lv.s0;
+    const uint64_t total = b ? lv.ones : lv.size - lv.ones;
+    const uint64_t m = k >> k_log2;
+    const uint64_t lo_pos = __ldg(S + m);
+    const uint64_t hi_pos = (((m + 1) << k_log2) <= total) ? __ldg(S + m + 1) : lv.size - 1;
+    // L1: last block i1 in [lo_pos>>16, hi_pos>>16] whose start has fewer than k b-bits before it
+    uint64_t i1 = lo_pos >> 16;
+    const uint64_t hi1 = hi_pos >> 16;
+    while (i1 < hi1) {
+        uint64_t nx = i1 + 1;
+        uint64_t c1 = __ldg(lv.l1 + nx);
+        uint64_t cb = b ? c1 : (nx << 16) - c1;
+        if (cb < k) i1 = nx;
+        else break;
+    }
+    const uint64_t c1 = __ldg(lv.l1 + i1);
+    const uint64_t base1 = b ? c1 : (i1 << 16) - c1;
+    uint64_t kk = k - base1;
+    // L2: last block in the range with fewer than kk b-bits (relative to the L1 block)
+    uint64_t lo2 = umax64(i1 << 7, lo_pos >> 9);
+    uint64_t hi2 = umin64((i1 << 7) + 127, hi_pos >> 9);
+    while (lo2 < hi2) {
+        uint64_t mid = (lo2 + hi2 + 1) >> 1;
+        uint64_t c2 = __ldg(lv.l2 + mid);
+        uint64_t cb = b ? c2 : ((mid << 9) - (i1 << 16)) - c2;
+        if (cb < kk) lo2 = mid;
+        else hi2 = mid - 1;
+    }
+    {
+        uint64_t c2 = __ldg(lv.l2 + lo2);
+        kk -= b ? c2 : ((lo2 << 9) - (i1 << 16)) - c2;
+    }
+    // words of the 512-bit block
+    const uint64_t* wp = lv.words + (lo2 << 3);
+    uint32_t kw = (uint32_t)kk;
+    uint64_t wv = 0;
+    uint32_t wi = 0;
+#pragma unroll 1
+    for (; wi < 8; wi += 2) {
+        ulonglong2 v = ldg_nc_v2(wp + wi);
+        uint64_t a0 = b ? v.x : ~v.x, a1 = b ? v.y : ~v.y;
+        uint32_t p0 = __popcll(a0);
+        if (p0 >= kw) { wv = a0; break; }
+        kw -= p0;
+        uint32_t p1 = __popcll(a1);
+        if (p1 >= kw) { wv = a1; wi += 1; break; }
+        kw -= p1;
+    }
+    return ((lo2 << 9) + ((uint64_t)wi << 6)) + select_in_word(wv, kw);
+}
+
+__device__ __forceinline__ void set_status(uint32_t* st, uint32_t bits) { atomicOr(st, bits); }
+
+#endif  // __CUDACC__
+
+}  // namespace wt

@@ -1,0 +1,178 @@
+"""Seeded synthetic workloads (symbols and query batches).
+
+This module is shared by the GPU tests, the benchmark and the oracle checks.
+It holds random-number generation and sampling only -- none of the wavelet
+tree's arithmetic.  To draw valid select queries (j in [1, count(c)]) it needs
+per-symbol counts, which it takes from torch.bincount, a library routine.
+
+The inputs stand in for the paper's uniform random texts and its real texts
+(Section 6.1), which are not available here: uniform symbols over sigma, or a
+Zipf law P(k) proportional to 1/(k+1)^s over [0, sigma) for text-like inputs.
+Random draws are made with a torch.Generator seeded per workload (Philox on
+CUDA), so a workload is reproducible on a given device type and torch version.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+SEED_BASE = 0x5EED0000
+
+
+@dataclass
+class Workload:
+    name: str
+    index: int
+    n: int
+    sigma: int
+    symbol_bytes: int
+    dist: str            # "uniform" or "zipf"
+    zipf_s: float = 0.0
+    queries: dict = field(default_factory=dict)  # kind -> count; "mixed" = thirds of access/rank/select
+    sample_k: int = 4096
+
+    @property
+    def dtype(self):
+        return {1: torch.uint8, 2: torch.int16, 4: torch.int32}[self.symbol_bytes]
+
+    def describe(self) -> str:
+        d = "uniform" if self.dist == "uniform" else f"Zipf(s={self.zipf_s})"
+        q = ", ".join(f"{v} {k}" for k, v in self.queries.items())
+        return f"n={self.n} u{8 * self.symbol_bytes} {d} over sigma={self.sigma}; queries: {q}"
+
+
+# The five workload shapes: plain, text-like, large alphabet, batched, learned select.
+WORKLOADS = {
+    "plain": Workload("plain", 0, 1 << 20, 256, 1, "uniform", queries={"access": 100_000, "rank": 100_000, "select": 100_000}),
+    "text": Workload("text", 1, 1 << 30, 96, 1, "zipf", 1.0, queries={"access": 10_000_000, "rank": 10_000_000, "select": 10_000_000}),
+    "large_alphabet": Workload("large_alphabet", 2, 1 << 28, 1 << 20, 4, "uniform", queries={"mixed": 20_000_000}),
+    "learned": Workload("learned", 4, 1 << 30, 65536, 2, "zipf", 1.2, queries={"select": 100_000_000}),
+}
+
+
+def generator(seed: int, device) -> torch.Generator:
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return g
+
+
+def zipf_cdf(sigma: int, s: float, device) -> torch.Tensor:
+    k = torch.arange(1, sigma + 1, dtype=torch.float64, device=device)
+    p = k.pow(-s)
+    c = torch.cumsum(p, 0)
+    return c / c[-1]
+
+
+def _from_cdf(cdf: torch.Tensor, count: int, g: torch.Generator, device) -> torch.Tensor:
+    u = torch.rand(count, dtype=torch.float64, generator=g, device=device)
+    idx = torch.searchsorted(cdf, u, right=True)
+    return idx.clamp_(max=cdf.numel() - 1)
+
+
+def make_symbols(n: int, sigma: int, symbol_bytes: int, dist: str = "uniform", zipf_s: float = 1.0,
+                 seed: int = SEED_BASE, device="cuda", chunk: int = 1 << 26) -> torch.Tensor:
+    """n symbols in [0, sigma) stored in 1, 2 or 4 bytes (u16/u32 as int16/int32 bit patterns)."""
+    dtype = {1: torch.uint8, 2: torch.int16, 4: torch.int32}[symbol_bytes]
+    out = torch.empty(n, dtype=dtype, device=device)
+    g = generator(seed, device)
+    cdf = zipf_cdf(sigma, zipf_s, device) if dist == "zipf" else None
+    for a in range(0, n, chunk):
+        m = min(chunk, n - a)
+        if cdf is None:
+            v = torch.randint(0, sigma, (m,), generator=g, device=device, dtype=torch.int64)
+        else:
+            v = _from_cdf(cdf, m, g, device)
+        if symbol_bytes == 2:
+            v = torch.where(v >= 32768, v - 65536, v)
+        out[a:a + m] = v.to(dtype)
+    return out
+
+
+def symbols_as_int64(sym: torch.Tensor) -> torch.Tensor:
+    """Unsigned symbol values of a symbol tensor (u16/u32 stored as int16/int32)."""
+    if sym.dtype == torch.int16:
+        return sym.to(torch.int64) & 0xFFFF
+    if sym.dtype == torch.int32:
+        return sym.to(torch.int64) & 0xFFFFFFFF
+    return sym.to(torch.int64)
+
+
+def symbol_counts(sym: torch.Tensor, sigma: int, chunk: int = 1 << 26) -> torch.Tensor:
+    cnt = torch.zeros(sigma, dtype=torch.int64, device=sym.device)
+    for a in range(0, sym.numel(), chunk):
+        cnt += torch.bincount(symbols_as_int64(sym[a:a + chunk]), minlength=sigma)[:sigma]
+    return cnt
+
+
+def make_queries(w: Workload, sym: torch.Tensor, seed: int = None, counts: torch.Tensor = None,
+                 scale: float = 1.0) -> dict:
+    """Query batches of a workload; ``scale`` shrinks the counts (for quick runs).
+
+    access: i uniform in [0, n).  rank: c uniform (or from the Zipf law), i
+    uniform in [0, n).  select: c drawn like rank's c but only among symbols
+    that occur, j uniform in [1, count(c)].  mixed: each query independently
+    access, rank or select with probability 1/3.
+    """
+    device = sym.device
+    n, sigma = sym.numel(), w.sigma
+    g = generator(SEED_BASE + 0x100 + w.index if seed is None else seed, device)
+    if counts is None:
+        counts = symbol_counts(sym, sigma)
+    base = zipf_cdf(sigma, w.zipf_s, device) if w.dist == "zipf" else None
+
+    def draw_c(q):
+        if base is None:
+            return torch.randint(0, sigma, (q,), generator=g, device=device, dtype=torch.int64)
+        return _from_cdf(base, q, g, device)
+
+    present = (counts > 0).to(torch.float64)
+    if base is None:
+        wsel = present
+    else:
+        pdf = torch.diff(base, prepend=torch.zeros(1, dtype=torch.float64, device=device))
+        wsel = pdf * present
+    csel = torch.cumsum(wsel, 0)
+    csel = csel / csel[-1] if csel[-1] > 0 else csel
+
+    def draw_select(q):
+        c = _from_cdf(csel, q, g, device)
+        u = torch.rand(q, dtype=torch.float64, generator=g, device=device)
+        j = (u * counts[c].to(torch.float64)).to(torch.int64) + 1
+        j = torch.minimum(j, counts[c]).clamp_(min=1)
+        return c, j
+
+    out = {}
+    for kind, q in w.queries.items():
+        q = max(1, int(q * scale))
+        if kind == "access":
+            out["access_i"] = torch.randint(0, max(n, 1), (q,), generator=g, device=device, dtype=torch.int64)
+        elif kind == "rank":
+            out["rank_c"] = draw_c(q).to(torch.int32)
+            out["rank_i"] = torch.randint(0, max(n, 1), (q,), generator=g, device=device, dtype=torch.int64)
+        elif kind == "select":
+            c, j = draw_select(q)
+            out["select_c"] = c.to(torch.int32)
+            out["select_j"] = j
+        elif kind == "mixed":
+            k = torch.randint(0, 3, (q,), generator=g, device=device, dtype=torch.int64)
+            c_r = draw_c(q)
+            c_s, j_s = draw_select(q)
+            i_a = torch.randint(0, max(n, 1), (q,), generator=g, device=device, dtype=torch.int64)
+            c = torch.where(k == 1, c_r, torch.where(k == 2, c_s, torch.zeros_like(c_r)))
+            arg = torch.where(k == 2, j_s, i_a)
+            out["mixed_kind"] = k.to(torch.uint8)
+            out["mixed_c"] = c.to(torch.int32)
+            out["mixed_arg"] = arg
+    return out
+
+
+def make_workload(name: str, device="cuda", n: int = None, scale_queries: float = 1.0):
+    """Symbols and queries of a named workload (optionally with a smaller n)."""
+    w = WORKLOADS[name]
+    if n is not None and n != w.n:
+        w = Workload(w.name, w.index, n, w.sigma, w.symbol_bytes, w.dist, w.zipf_s, dict(w.queries), w.sample_k)
+    sym = make_symbols(w.n, w.sigma, w.symbol_bytes, w.dist, w.zipf_s, SEED_BASE + w.index, device)
+    counts = symbol_counts(sym, w.sigma)
+    q = make_queries(w, sym, counts=counts, scale=scale_queries)
+    return w, sym, q, counts
