@@ -306,6 +306,7 @@ __global__ void meta_kernel(const MetaArgs ma, uint32_t L, const uint64_t* __res
 
 constexpr int kTileBytes = 32768;
 constexpr int kLpThreads = 512;
+constexpr int kLpBlocksPerSM = 3;
 constexpr uint64_t kFlagAgg = 1, kFlagIncl = 2;
 
 // look-back state word: flag (2 bits) | aggregate (19 bits) | inclusive prefix (43 bits)
@@ -337,47 +338,123 @@ struct LevelPassArgs {
     uint32_t shift_bit;  // L - 1 - l
     uint32_t pshift;     // L - l (prefix = code >> pshift), unused at level 0
     uint32_t k_log2;
+    uint32_t ctab_n;     // level 0 re-encoding: table size (0 = compute codes arithmetically)
     CodeParams cp;       // used when re-encoding at level 0
 };
 
-template <typename T, bool ENCODE>
-__global__ void __launch_bounds__(kLpThreads, 2) level_pass_kernel(const __grid_constant__ LevelPassArgs a) {
+// 32-bit shared-memory addressing for the byte / half / word scatter stores
+__device__ __forceinline__ void sts_elem(uint32_t addr, uint8_t v) {
+    asm volatile("st.shared.u8 [%0], %1;" ::"r"(addr), "h"((unsigned short)v) : "memory");
+}
+__device__ __forceinline__ void sts_elem(uint32_t addr, uint16_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+}
+__device__ __forceinline__ void sts_elem(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Partition one group (32 lanes x 16 bytes) of a tile into the shared-memory
+// image: the lane's element with level bit b goes to slot A1 + (ones before it
+// in the lane) if b = 1, else to A0 + (zeros before it in the lane).  Slots of
+// two elements travel as a 16-bit pair.  For one-byte symbols
+// the in-word ranks come from byte-wise prefix counts of the level bits.
+template <typename T, bool FULL>
+__device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V, uint32_t m, uint32_t A0, uint32_t A1,
+                                              uint32_t j0, uint32_t count, uint32_t shift) {
     constexpr int W = sizeof(T);
-    constexpr int EPL = 4 / W;                  // elements per lane per round
+    constexpr int EPW = 4 / W;
+    const uint32_t wv[4] = {V.x, V.y, V.z, V.w};
+    const uint32_t A0x2 = A0 * 0x00010001u, A1x2 = A1 * 0x00010001u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint32_t w = wv[i];
+        const uint32_t jw = j0 + i * EPW;
+        // ones among the lane's earlier words
+        const uint32_t ci = (i == 0) ? 0u : __popc(m & ((1u << (i * EPW)) - 1u));
+        const uint32_t b1 = A1x2 + ci * 0x00010001u;                                 // one-slot base, paired
+        const uint32_t b0 = (A0x2 + (uint32_t)(i * EPW) * 0x00010001u) - ci * 0x00010001u;  // zero-slot base, paired
+        if (W == 1) {
+            // bytes of y: level bits of the word's 4 elements; pre: ones before each element
+            const uint32_t y = (w >> shift) & 0x01010101u;
+            const uint32_t pre = y * 0x01010100u;
+            const uint32_t sel = y * 0xFFu;
+            const uint32_t off = (pre & sel) | ((0x03020100u - pre) & ~sel);  // rank among same-bit elements
+            const uint32_t s01 = __byte_perm(sel, 0, 0x1100), s23 = __byte_perm(sel, 0, 0x3322);
+            const uint32_t I01 = ((b1 & s01) | (b0 & ~s01)) + __byte_perm(off, 0, 0x4140);
+            const uint32_t I23 = ((b1 & s23) | (b0 & ~s23)) + __byte_perm(off, 0, 0x4342);
+            if (FULL || jw + 0 < count) sts_elem(out + (I01 & 0xFFFFu), (T)w);
+            if (FULL || jw + 1 < count) sts_elem(out + (I01 >> 16), (T)(w >> 8));
+            if (FULL || jw + 2 < count) sts_elem(out + (I23 & 0xFFFFu), (T)(w >> 16));
+            if (FULL || jw + 3 < count) sts_elem(out + (I23 >> 16), (T)(w >> 24));
+        } else if (W == 2) {
+            const uint32_t bb = (m >> (2 * i)) & 3u;
+            const uint32_t sel = (bb & 1u ? 0x0000FFFFu : 0u) | (bb & 2u ? 0xFFFF0000u : 0u);
+            // second element: ones before it if it is a one, zeros before it otherwise
+            const uint32_t off = ((bb ^ (bb >> 1)) & 1u) ? 0u : 0x00010000u;
+            const uint32_t I = ((b1 & sel) | (b0 & ~sel)) + off;
+            if (FULL || jw + 0 < count) sts_elem(out + 2 * (I & 0xFFFFu), (T)w);
+            if (FULL || jw + 1 < count) sts_elem(out + 2 * (I >> 16), (T)(w >> 16));
+        } else {
+            const uint32_t bit = (m >> i) & 1u;
+            if (FULL || jw < count) sts_elem(out + 4 * ((bit ? b1 : b0) & 0xFFFFu), (T)w);
+        }
+    }
+}
+
+template <typename T, bool ENCODE>
+__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM) level_pass_kernel(const __grid_constant__ LevelPassArgs a) {
+    constexpr int W = sizeof(T);
+    constexpr int VEPL = 16 / W;                // elements per lane per group (one uint4 per lane)
+    constexpr int EPW = 4 / W;                  // elements per 32-bit word
     constexpr int TE = kTileBytes / W;          // elements per tile
-    constexpr int ROUNDS = kTileBytes / 128;    // one round = one 128-byte row = 32 lanes x 4 bytes
+    constexpr int NG = kTileBytes / 512;        // groups per tile: one group = 32 lanes x 16 bytes
     constexpr int NWARP = kLpThreads / 32;
-    constexpr int RPW = ROUNDS / NWARP;
-    constexpr int EPR = 32 * EPL;               // elements per round
+    constexpr int GPW = NG / NWARP;             // groups per warp in phase 1
+    constexpr int GE = 512 / W;                 // elements (= bits) per group
+    constexpr int GBYTES = GE / 8;              // bytes of level bits per group
     constexpr int TPL1 = 65536 / TE;            // tiles per L1 block
-    constexpr int RPL2 = 512 / EPR;             // rounds per L2 block
-    constexpr int WORDS = TE / 64;
-    constexpr int VE = 16 / W;                  // elements per 16 bytes
+    constexpr int GPL2 = W;                     // groups per 512-bit L2 block
     constexpr uint32_t EMASK = (W == 4) ? 0xFFFFFFFFu : ((1u << (8 * W)) - 1u);
+    constexpr uint32_t LOWB = (W == 1) ? 0x01010101u : (W == 2 ? 0x00010001u : 1u);  // bit 0 of every element
+    static_assert(NG % NWARP == 0 && NG <= 64, "tile shape");
 
     extern __shared__ __align__(128) uint8_t smem[];
-    uint32_t* in32 = reinterpret_cast<uint32_t*>(smem);
+    uint4* in4 = reinterpret_cast<uint4*>(smem);
     uint8_t* outb = smem + kTileBytes;
-    uint64_t* words = reinterpret_cast<uint64_t*>(smem + 2 * kTileBytes + 64);
-    uint32_t* bal = reinterpret_cast<uint32_t*>(words + WORDS);
-    uint32_t* rpre = bal + ROUNDS * EPL;  // ROUNDS + 1
+    uint8_t* wbytes = smem + 2 * kTileBytes + 64;                               // level bits of the tile
+    uint32_t* rpre = reinterpret_cast<uint32_t*>(wbytes + kTileBytes / 8 / W);  // NG + 1
+    T* ctab = reinterpret_cast<T*>(rpre + 64 + 1);                              // code table (ENCODE, small sigma)
 
     __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint64_t s_tile, s_E, s_EL1, s_ones, s_p;
+    __shared__ uint64_t s_tile, s_E, s_EL1, s_p;
     __shared__ uint32_t s_single;
+    __shared__ uint32_t s_gcnt[64];
+    __shared__ uint32_t s_gnext;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
     if (tid == 0) {
         s_tile = atomicAdd(a.counter, 1u);
         mbar_init(&mbar, 1);
         mbar_fence_init();
+    }
+    if (ENCODE && a.ctab_n) {
+        for (uint32_t s = tid; s < a.ctab_n; s += kLpThreads) {
+            uint32_t code, len;
+            encode(a.cp, s, code, len);
+            ctab[s] = (T)code;
+        }
     }
     __syncthreads();
     const uint64_t tile = s_tile;
     if (tile >= a.ntiles) return;
     const uint64_t t0 = tile * TE;
     const uint32_t count = (uint32_t)umin64((uint64_t)TE, a.size - t0);
+    const bool full = count == (uint32_t)TE;
     const uint32_t bytes = count * W;
     const uint32_t b16 = bytes & ~15u;
     const uint8_t* srcb = reinterpret_cast<const uint8_t*>(a.src) + t0 * W;
@@ -399,80 +476,107 @@ __global__ void __launch_bounds__(kLpThreads, 2) level_pass_kernel(const __grid_
     }
     __syncthreads();
 
-    // ---- phase 1: level bits per round (ballots), round counts ----
+    // ---- phase 1: level bits of every lane's 16 bytes -> shared memory ----
     const uint32_t shift = a.shift_bit;
-    for (int rr = 0; rr < RPW; rr++) {
-        const int r = warp * RPW + rr;
-        uint32_t v = in32[r * 32 + lane];
-        const uint32_t j0 = r * EPR + lane * EPL;
+#pragma unroll 1
+    for (int gg = 0; gg < GPW; gg++) {
+        const int g = warp * GPW + gg;
+        uint4 V = in4[g * 32 + lane];
+        const uint32_t j0 = g * GE + lane * VEPL;
+        uint32_t wv[4] = {V.x, V.y, V.z, V.w};
         if (ENCODE) {
-            uint32_t nv = 0;
 #pragma unroll
-            for (int k = 0; k < EPL; k++) {
-                uint32_t e = (v >> (8 * W * k)) & EMASK;
-                uint32_t code = 0, len;
-                if (j0 + k < count) encode(a.cp, e, code, len);
-                nv |= (code & EMASK) << (8 * W * k);
-            }
-            v = nv;
-            in32[r * 32 + lane] = v;
-        }
-        uint32_t bl[EPL];
-        uint32_t cnt = 0;
+            for (int i = 0; i < 4; i++) {
+                uint32_t nv = 0;
 #pragma unroll
-        for (int k = 0; k < EPL; k++) {
-            uint32_t e = (v >> (8 * W * k)) & EMASK;
-            bool bit = (j0 + k < count) && ((e >> shift) & 1u);
-            bl[k] = __ballot_sync(0xffffffffu, bit);
-            cnt += __popc(bl[k]);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < EPL; k++) bal[r * EPL + k] = bl[k];
-            rpre[r] = cnt;
-            if (EPL == 1) {
-                reinterpret_cast<uint32_t*>(words)[r] = bl[0];
-            } else if (EPL == 2) {
-                words[r] = spread2(bl[0]) | (spread2(bl[EPL > 1 ? 1 : 0]) << 1);
-            } else {
-                uint64_t w0 = 0, w1 = 0;
-#pragma unroll
-                for (int k = 0; k < EPL; k++) {
-                    w0 |= spread4(bl[k]) << k;
-                    w1 |= spread4(bl[k] >> 16) << k;
+                for (int k = 0; k < EPW; k++) {
+                    const uint32_t e = (wv[i] >> (8 * W * k)) & EMASK;
+                    uint32_t code = 0;
+                    if (j0 + i * EPW + k < count) {
+                        if (a.ctab_n) {
+                            code = ctab[e < a.ctab_n ? e : 0];
+                        } else {
+                            uint32_t len;
+                            encode(a.cp, e, code, len);
+                        }
+                    }
+                    nv |= (code & EMASK) << (8 * W * k);
                 }
-                words[2 * r] = w0;
-                words[2 * r + 1] = w1;
+                wv[i] = nv;
             }
+            in4[g * 32 + lane] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+        uint32_t m = 0;  // bit k = level bit of the lane's element k
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint32_t y = (wv[i] >> shift) & LOWB;
+            uint32_t b;
+            if (W == 1) b = (y * 0x10204080u) >> 28;
+            else if (W == 2) b = (y | (y >> 15)) & 3u;
+            else b = y;
+            m |= b << (i * EPW);
+        }
+        if (!full) {
+            const uint32_t act = j0 < count ? min(count - j0, (uint32_t)VEPL) : 0u;
+            m &= act >= 32 ? 0xFFFFFFFFu : ((1u << act) - 1u);
+        }
+        if (W == 1) {
+            reinterpret_cast<uint16_t*>(wbytes + g * GBYTES)[lane] = (uint16_t)m;
+        } else if (W == 2) {
+            wbytes[g * GBYTES + lane] = (uint8_t)m;
+        } else {
+            const uint32_t x = m | (__shfl_down_sync(0xffffffffu, m, 1) << 4);
+            if ((lane & 1) == 0) wbytes[g * GBYTES + lane / 2] = (uint8_t)x;
+        }
+        const uint32_t gc = __reduce_add_sync(0xffffffffu, __popc(m));
+        if (lane == 0) s_gcnt[g] = gc;
+    }
+    if (tid == kLpThreads - 32) {
+        s_gnext = 0;
+        // does the tile lie inside one node of this level?
+        if (a.level == 0) {
+            s_single = 1;
+            s_p = 0;
+        } else {
+            const T* te = reinterpret_cast<const T*>(smem);
+            const uint64_t p0 = (uint64_t)te[0] >> a.pshift;
+            const uint64_t p1 = (uint64_t)te[count - 1] >> a.pshift;
+            s_single = p0 == p1;
+            s_p = p0;
         }
     }
     __syncthreads();
 
-    // ---- phase 2: tile scan + look-back (warp 0) || word stores (other warps) ----
-    if (warp == 0) {
-        constexpr int PER = ROUNDS / 32;
-        uint32_t loc[PER];
-        uint32_t s = 0;
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            loc[k] = rpre[lane * PER + k];
-            s += loc[k];
-        }
-        uint32_t inc = s;
+    // ---- phase 2 (every warp, no barrier): exclusive scan of the 64 group counts ----
+    // lane l holds the prefixes of groups 2l and 2l+1
+    uint32_t rp0, rp1, ones32;
+    {
+        const uint32_t c0 = 2 * lane < NG ? s_gcnt[2 * lane] : 0u, c1 = 2 * lane + 1 < NG ? s_gcnt[2 * lane + 1] : 0u;
+        const uint32_t sum = c0 + c1;
+        uint32_t inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += t;
         }
-        uint32_t run = inc - s;
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            rpre[lane * PER + k] = run;
-            run += loc[k];
+        rp0 = inc - sum;
+        rp1 = rp0 + c0;
+        ones32 = __shfl_sync(0xffffffffu, inc, 31);
+        if (warp == 1) {
+            if (2 * lane < NG) rpre[2 * lane] = rp0;
+            if (2 * lane + 1 < NG) rpre[2 * lane + 1] = rp1;
+            if (lane == 0) rpre[NG] = ones32;
         }
-        const uint64_t ones = __shfl_sync(0xffffffffu, inc, 31);
-        if (lane == 0) rpre[ROUNDS] = (uint32_t)ones;
-        // publish the aggregate, then look back for the exclusive prefix
+    }
+    const uint32_t Z = count - ones32;  // zeros of the tile
+
+    // ---- phase 3: look-back (warp 0) || level bits to global + partition into shared memory ----
+    // The shared-memory image holds the tile's zeros at out[0, Z) and its ones at
+    // out[Z, count), each in input order; it does not depend on the look-back.
+    T* out = reinterpret_cast<T*>(outb);
+    const uint32_t out_s = smem_addr(outb);
+    if (warp == 0) {
+        const uint64_t ones = ones32;
         if (lane == 0) st_relaxed_u64(a.state + tile, tile == 0 ? lb_pack(kFlagIncl, ones, ones) : lb_pack(kFlagAgg, ones, 0));
         uint64_t excl = 0;
         if (tile > 0) {
@@ -510,41 +614,57 @@ __global__ void __launch_bounds__(kLpThreads, 2) level_pass_kernel(const __grid_
         if (lane == 0) {
             s_E = excl;
             s_EL1 = excl - sub;
-            s_ones = ones;
         }
     } else {
+        const uint32_t tw = tid - 32;
         const uint32_t nw = (count + 63) / 64;
-        for (uint32_t i = tid - 32; i < nw; i += kLpThreads - 32) a.words[tile * WORDS + i] = words[i];
-        if (warp == 1 && lane == 0) {
-            // does the tile lie inside one node of this level?
-            if (a.level == 0) {
-                s_single = 1;
-                s_p = 0;
-            } else {
-                const T* te = reinterpret_cast<const T*>(smem);
-                uint64_t p0 = (uint64_t)te[0] >> a.pshift;
-                uint64_t p1 = (uint64_t)te[count - 1] >> a.pshift;
-                s_single = p0 == p1;
-                s_p = p0;
-            }
-        }
+        const uint64_t* wsrc = reinterpret_cast<const uint64_t*>(wbytes);
+        uint64_t* wdst = a.words + tile * (TE / 64);
+        for (uint32_t i = tw; i < nw; i += kLpThreads - 32) wdst[i] = wsrc[i];
         if (tile == a.ntiles - 1) {
-            // zero the padding words after the level's last word
             const uint64_t first_pad = (a.size + 63) / 64;
-            for (uint64_t i = first_pad + (tid - 32); i < a.words_alloc; i += kLpThreads - 32) a.words[i] = 0;
+            for (uint64_t i = first_pad + tw; i < a.words_alloc; i += kLpThreads - 32) a.words[i] = 0;
+        }
+    }
+    if (a.dst != nullptr) {
+        // groups are handed out dynamically; warp 0 joins once its look-back is done
+#pragma unroll 1
+        while (true) {
+            uint32_t g = 0;
+            if (lane == 0) g = atomicAdd(&s_gnext, 1u);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= (uint32_t)NG) break;
+            const uint4 V = in4[g * 32 + lane];
+            const uint32_t j0 = g * GE + lane * VEPL;
+            uint32_t m;
+            if (W == 1) m = reinterpret_cast<const uint16_t*>(wbytes + g * GBYTES)[lane];
+            else if (W == 2) m = wbytes[g * GBYTES + lane];
+            else m = (wbytes[g * GBYTES + lane / 2] >> ((lane & 1) * 4)) & 0xFu;
+            // ones before this lane's elements: group prefix + warp exclusive scan
+            const uint32_t c = __popc(m);
+            uint32_t inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const uint32_t gpre = __shfl_sync(0xffffffffu, (g & 1u) ? rp1 : rp0, g >> 1);
+            const uint32_t ob = gpre + inc - c;
+            if (full) scatter_group<T, true>(out_s, V, m, j0 - ob, Z + ob, j0, count, shift);
+            else scatter_group<T, false>(out_s, V, m, j0 - ob, Z + ob, j0, count, shift);
         }
     }
     __syncthreads();
 
-    const uint64_t E = s_E, EL1 = s_EL1, ones = s_ones;
-    const uint64_t zeros = count - ones;
+    const uint64_t E = s_E, EL1 = s_EL1, ones = ones32;
+    const uint64_t zeros = Z;
     const uint64_t R0 = t0 - E;  // zeros before the tile
 
-    // ---- phase 3: L1/L2 counters and select samples ----
+    // ---- phase 4: L1/L2 counters and select samples ----
     {
         const uint32_t nl2 = (count + 511) / 512;
         for (uint32_t b = tid; b < nl2; b += kLpThreads)
-            a.l2[(t0 >> 9) + b] = (uint16_t)(E - EL1 + rpre[b * RPL2]);
+            a.l2[(t0 >> 9) + b] = (uint16_t)(E - EL1 + rpre[b * GPL2]);
         if (tid == 0) {
             if (tile % TPL1 == 0) a.l1[t0 >> 16] = E;
             if (tile == a.ntiles - 1) {
@@ -571,97 +691,73 @@ __global__ void __launch_bounds__(kLpThreads, 2) level_pass_kernel(const __grid_
             const uint32_t b = idx < ns1;
             const uint64_t m = b ? m1lo + idx : m0lo + (idx - ns1);
             const uint32_t t = (uint32_t)((m << kl) - (b ? E : R0));  // 1-based rank within the tile
-            int lo = 0, hi = ROUNDS - 1;
+            int lo = 0, hi = NG - 1;  // last group with fewer than t b-bits before it
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                uint32_t c = b ? rpre[mid] : (uint32_t)(mid * EPR) - rpre[mid];
+                uint32_t c = b ? rpre[mid] : (uint32_t)(mid * GE) - rpre[mid];
                 if (c < t) lo = mid;
                 else hi = mid - 1;
             }
-            const uint32_t before = b ? rpre[lo] : (uint32_t)(lo * EPR) - rpre[lo];
-            const uint32_t tt = t - before;
-            uint64_t w0, w1 = 0;
-            if (EPL == 4) {
-                w0 = words[2 * lo];
-                w1 = words[2 * lo + 1];
-            } else if (EPL == 2) {
-                w0 = words[lo];
-            } else {
-                w0 = reinterpret_cast<const uint32_t*>(words)[lo];
+            uint32_t tt = t - (b ? rpre[lo] : (uint32_t)(lo * GE) - rpre[lo]);
+            const uint64_t* gw = reinterpret_cast<const uint64_t*>(wbytes + lo * GBYTES);
+            uint32_t pin = 0;
+#pragma unroll 1
+            for (int k = 0; k < GE / 64; k++) {
+                uint64_t x = gw[k];
+                if (!b) x = ~x;
+                const uint32_t c = __popcll(x);
+                if (c >= tt) {
+                    pin = k * 64 + select_in_word(x, tt);
+                    break;
+                }
+                tt -= c;
             }
-            if (!b) {
-                w0 = ~w0;
-                w1 = ~w1;
-                if (EPL == 1) w0 &= 0xFFFFFFFFull;
-                if (EPL <= 2) w1 = 0;
-            }
-            const uint32_t c0 = __popcll(w0);
-            const uint32_t pin = c0 >= tt ? select_in_word(w0, tt) : 64 + select_in_word(w1, tt - c0);
-            if (m < (b ? a.n_s1 : a.n_s0)) (b ? a.s1 : a.s0)[m] = t0 + (uint64_t)lo * EPR + pin;
+            if (m < (b ? a.n_s1 : a.n_s0)) (b ? a.s1 : a.s0)[m] = t0 + (uint64_t)lo * GE + pin;
         }
     }
 
     if (a.dst == nullptr) return;
 
-    // ---- phase 4: stable partition of the tile by the level bit (shared memory) ----
-    const bool single = s_single != 0;
-    uint64_t D0 = 0, D1 = 0;
-    uint32_t pad0 = 0, OB = (uint32_t)zeros;
-    if (single) {
-        const NodeEntry* ne = a.nodes + s_p;
-        D0 = __ldg(&ne->off0) + R0;
-        D1 = __ldg(&ne->off1) + E;
-        pad0 = (uint32_t)(D0 % VE);
-        OB = ((pad0 + (uint32_t)zeros + VE - 1) / VE) * VE + (uint32_t)(D1 % VE);
-    }
-    T* out = reinterpret_cast<T*>(outb);
-    const uint32_t ltmask = (1u << lane) - 1u;
-    for (int rr = 0; rr < RPW; rr++) {
-        const int r = warp * RPW + rr;
-        const uint32_t v = in32[r * 32 + lane];
-        const uint32_t j0 = r * EPR + lane * EPL;
-        uint32_t ob = rpre[r];
-        uint32_t bl[EPL];
-#pragma unroll
-        for (int k = 0; k < EPL; k++) {
-            bl[k] = bal[r * EPL + k];
-            ob += __popc(bl[k] & ltmask);
-        }
-#pragma unroll
-        for (int k = 0; k < EPL; k++) {
-            const uint32_t j = j0 + k;
-            if (j < count) {
-                const uint32_t bit = (bl[k] >> lane) & 1u;
-                const uint32_t idx = bit ? OB + ob : pad0 + j - ob;
-                out[idx] = (T)((v >> (8 * W * k)) & EMASK);
-                ob += bit;
-            }
-        }
-    }
-    __syncthreads();
-
+    // ---- phase 5: shared-memory image -> T_{l+1} ----
     T* dst = reinterpret_cast<T*>(a.dst);
     const uint64_t lim = a.size_next;
-    if (single) {
-        // two runs with the same alignment in shared and global memory: 16-byte copies
+    if (s_single != 0) {
+        // two contiguous runs: zeros to off0 + R0, ones to off1 + E.  Global 4-byte
+        // words are assembled from two shared words with a funnel shift.
+        const NodeEntry* ne = a.nodes + s_p;
+        const uint64_t D0 = __ldg(&ne->off0) + R0;
+        const uint64_t D1 = __ldg(&ne->off1) + E;
 #pragma unroll
         for (int run = 0; run < 2; run++) {
-            uint64_t D = run ? D1 : D0;
-            uint64_t len = run ? ones : zeros;
-            const uint32_t so = run ? OB : pad0;  // element offset in shared memory
-            if (D >= lim || len == 0) continue;
-            len = umin64(len, lim - D);
-            const uint64_t gb = D * W, ge = (D + len) * W;
-            const uint64_t hb = umin64((gb + 15) & ~(uint64_t)15, ge);
-            const uint64_t be = umax64(hb, ge & ~(uint64_t)15);
-            uint8_t* db = reinterpret_cast<uint8_t*>(dst);
-            const uint64_t sbase = (uint64_t)so * W;  // shared byte of global byte g: sbase + (g - gb)
-            for (uint64_t g = gb + (uint64_t)tid * W; g < hb; g += (uint64_t)kLpThreads * W)
-                *reinterpret_cast<T*>(db + g) = *reinterpret_cast<const T*>(outb + sbase + (g - gb));
-            for (uint64_t g = hb + (uint64_t)tid * 16; g < be; g += (uint64_t)kLpThreads * 16)
-                *reinterpret_cast<uint4*>(db + g) = *reinterpret_cast<const uint4*>(outb + sbase + (g - gb));
-            for (uint64_t g = be + (uint64_t)tid * W; g < ge; g += (uint64_t)kLpThreads * W)
-                *reinterpret_cast<T*>(db + g) = *reinterpret_cast<const T*>(outb + sbase + (g - gb));
+            const uint64_t D = run ? D1 : D0;
+            uint64_t len64 = run ? ones : zeros;
+            const uint32_t so = run ? Z : 0u;
+            if (D >= lim || len64 == 0) continue;
+            const uint32_t len = (uint32_t)umin64(len64, lim - D);
+            T* dr = dst + D;
+            if (W == 4) {
+                for (uint32_t i = tid; i < len; i += kLpThreads) dr[i] = out[so + i];
+                continue;
+            }
+            // element counts of the unaligned head, the 4-byte body and the tail
+            const uint32_t mis = (uint32_t)(D * W) & 3u;
+            const uint32_t head = min(len, mis ? (4u - mis) / W : 0u);
+            const uint32_t nbody = (len - head) * W / 4;
+            const uint32_t tail0 = head + nbody * (4 / W);
+            if (tid < head) dr[tid] = out[so + tid];
+            uint32_t* db = reinterpret_cast<uint32_t*>(dr + head);
+            const uint32_t sb0 = (so + head) * W;  // shared byte of the first body byte
+            // the shared/global byte shift is the same for the whole run; each lane
+            // reads one shared word and takes the next one from its neighbour lane
+            const uint32_t fs = (sb0 & 3u) * 8u, w0 = sb0 >> 2;
+            const uint32_t nb32 = (nbody + 31u) & ~31u;
+            for (uint32_t i = tid; i < nb32; i += kLpThreads) {
+                const uint32_t lo = lds_u32(out_s + 4 * (w0 + i));
+                uint32_t hi = __shfl_down_sync(0xffffffffu, lo, 1);
+                if (lane == 31) hi = lds_u32(out_s + 4 * (w0 + i + 1));
+                if (i < nbody) db[i] = __funnelshift_r(lo, hi, fs);
+            }
+            for (uint32_t i = tail0 + tid; i < len; i += kLpThreads) dr[i] = out[so + i];
         }
     } else {
         // several nodes: every element finds its node's offsets from its own code
@@ -672,19 +768,19 @@ __global__ void __launch_bounds__(kLpThreads, 2) level_pass_kernel(const __grid_
             if (Dx < lim) dst[Dx] = x;
         }
         for (uint32_t i = tid; i < ones; i += kLpThreads) {
-            const T x = out[OB + i];
+            const T x = out[Z + i];
             const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off1) + E + i;
             if (Dx < lim) dst[Dx] = x;
         }
     }
 }
 
+constexpr uint32_t kCodeTableBytes = 8192;
+
 template <typename T, bool ENC>
 static size_t level_pass_smem() {
     constexpr int W = sizeof(T);
-    constexpr int TE = kTileBytes / W;
-    constexpr int ROUNDS = kTileBytes / 128;
-    return 2 * kTileBytes + 64 + (TE / 64) * 8 + ROUNDS * (4 / W) * 4 + (ROUNDS + 1) * 4;
+    return 2 * kTileBytes + 64 + kTileBytes / 8 / W + (64 + 1) * 4 + (ENC ? kCodeTableBytes : 0);
 }
 
 template <typename T, bool ENC>
@@ -900,6 +996,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.pshift = L - l;
             a.k_log2 = k_log2;
             a.cp = cp;
+            a.ctab_n = ((uint64_t)sigma * w <= kCodeTableBytes) ? sigma : 0;
             WT_CUDA_TRY(cudaMemsetAsync(state, 0, a.ntiles * 8, s));
             const bool enc = (l == 0) && !cp.pow2;
             cudaError_t e;
