@@ -184,6 +184,47 @@ enum {
 };
 wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, uint64_t* count);
 
+/*
+ * wt_bitvector_support_static — rank/select support of a caller-owned
+ * bitvector, computed without allocating any device memory.  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot allocate
+ * while they run: code that executes inside an allocator or memory-pool
+ * callback, latency-critical loops that must not take the driver's allocation
+ * path, or host frameworks that own all device memory and pass in fixed
+ * buffers.  Everything the caller passes is an input or an output; the only
+ * other memory used is a scratch array compiled into libwt (a 64-bit word per
+ * 65536-bit tile plus a counter, 512 KiB), which every GPU that loads the
+ * library keeps until the process exits.
+ *
+ * It writes the same counters and samples wt_build stores for a level
+ * (wt_export's WT_EXPORT_L1, L2, S0 and S1 contents) for the bitvector
+ * d_words[0 .. ceil(nbits/64)) (LSB-first; bits at or past nbits are ignored):
+ *  d_l1   floor(nbits/65536) + 1 uint64: ones in B[0, 65536 k)
+ *  d_l2   floor(nbits/512) + 1 uint16: ones from the start of the enclosing
+ *         65536-bit block to position 512 m
+ *  d_s0, d_s1  sample_capacity uint64 each; [0] = 0 and [m] = position of the
+ *         (m * sample_k)-th zero / one; entries past the last sample are not written
+ *  sample_capacity  at least floor(nbits / sample_k) + 2
+ *  d_status  optional device word; WT_ETIMEOUT's bit (1 << WT_ETIMEOUT) is OR-ed
+ *         into it if a bounded device wait gave up.
+ * Limits: 1 <= nbits <= 2^32 (the size of the static scratch); larger or
+ * empty inputs, a sample_k that is not a power of two in [256, 2^20], a too
+ * small sample_capacity or a pointer that is not device memory return
+ * WT_EINVAL before any work is enqueued.  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ * The first call on a device looks up the device address of the static
+ * scratch (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call on a device shares the scratch,
+ * which keeps the last call's contents; each call clears what must start at
+ * zero.  Calls whose work overlaps on the GPU (different streams, or a call
+ * issued while another is still running) race on the scratch and give wrong
+ * results: serialise them.  Work is enqueued on `stream`; the call returns
+ * before it finishes.
+ */
+wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64_t nbits, uint32_t sample_k, uint64_t* d_l1,
+                                      uint16_t* d_l2, uint64_t* d_s0, uint64_t* d_s1, uint64_t sample_capacity,
+                                      uint32_t* d_status, wt_stream stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* wt_status_str(wt_status s);
 

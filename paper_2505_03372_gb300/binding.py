@@ -24,7 +24,7 @@ MAX_LEVELS = 26
 EXPORTED = (
     "wt_build", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync",
     "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
-    "wt_profile_report",
+    "wt_profile_report", "wt_bitvector_support_static",
 )
 
 
@@ -82,6 +82,8 @@ def lib():
         L.wt_profile_launches.restype = u64
         L.wt_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.wt_profile_report.restype = ctypes.c_size_t
+        L.wt_bitvector_support_static.argtypes = [vp, u64, u32, vp, vp, vp, vp, u64, vp, vp]
+        L.wt_bitvector_support_static.restype = ctypes.c_int
         for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync", "wt_info",
                   "wt_export"):
             getattr(L, f).restype = ctypes.c_int
