@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="text")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's n (small profiling cases)")
+    ap.add_argument("--query-scale", type=float, default=1.0, help="scale the query counts (small profiling cases)")
     return ap.parse_args()
 
 
@@ -218,6 +220,10 @@ def run_ours(args):
     from paper_2505_03372_gb300 import workloads
 
     wl = workloads.WORKLOADS[args.workload]
+    if args.n is not None or args.query_scale != 1.0:
+        qs = {k: max(1, int(v * args.query_scale)) for k, v in wl.queries.items()}
+        wl = workloads.Workload(wl.name, wl.index, args.n or wl.n, wl.sigma, wl.symbol_bytes, wl.dist, wl.zipf_s, qs,
+                                wl.sample_k)
     sym = workloads.make_symbols(wl.n, wl.sigma, wl.symbol_bytes, wl.dist, wl.zipf_s,
                                  seed=workloads.SEED_BASE + wl.index, device="cuda")
     counts = workloads.symbol_counts(sym, wl.sigma)
@@ -321,10 +327,11 @@ def run_ours(args):
         achieved = per_launch_bytes * nlaunch / (dom_ms * 1e-3) / 1e9
     for k in list(kern):
         kern[k]["share"] = kern[k]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)
+    traffic = _measured_traffic(dom, sum(sizes) / max(len(sizes), 1)) if dom == lp_name else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback 6.8 TB/s",
-            "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": dom_ms / nlaunch, "traffic": None}
+            "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": dom_ms / nlaunch, "traffic": traffic}
     if lp_name in kern:
         roof["level_pass_frac"] = (sum(lp_bytes) * args.steps / (kern[lp_name]["ms"] * 1e-3) / 1e9) / peak
 
@@ -352,6 +359,24 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _measured_traffic(kernel, symbols_per_launch):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
+    scaled by the symbols one launch processes; None if the kernel source changed
+    since the counters were taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["file"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except Exception:
+        return None
+    if sha != rec["source_sha256_16"]:
+        return None
+    return rec["dram_bytes_per_symbol"] * symbols_per_launch
 
 
 def _mean_code_len(wl, q, counts):
