@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--workload", default="text")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-sampled select comparison")
     ap.add_argument("--n", type=int, default=None, help="override the workload's n (small profiling cases)")
     ap.add_argument("--query-scale", type=float, default=1.0, help="scale the query counts (small profiling cases)")
     return ap.parse_args()
@@ -345,6 +346,10 @@ def run_ours(args):
         "phases": phases, "roofline": roof, "kernels": kern, "gpu_launches": launches, "clocks": clk,
     }
 
+    # ---- learned vs sampled select on the same tree (outside the timed step) ----
+    if ("select_j" in q or "mixed_arg" in q) and not args.no_learned:
+        line["learned_select"] = _learned_compare(wl, sym, q, outs)
+
     # ---- end to end: host buffers, copies inside the timed region ----
     if not args.no_e2e:
         line["e2e"] = _e2e(args, wl, sym, q, outs, step, barrier, dist, world, Q)
@@ -359,6 +364,59 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _learned_compare(wl, sym, q, outs, reps=3):
+    """Sampled select vs learned select (PLA, then the trained MLP) on the select
+    queries of the step, same tree and GPU; results must agree exactly."""
+    import numpy as np
+    import torch
+    from paper_2505_03372_gb300 import binding as wt
+
+    if "select_j" in q:
+        c, j = q["select_c"], q["select_j"]
+    else:
+        m = q["mixed_kind"] == 2
+        c, j = q["mixed_c"][m].contiguous(), q["mixed_arg"][m].contiguous()
+    out = torch.empty(j.numel(), dtype=torch.int64, device="cuda")
+    ref = torch.empty_like(out)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {"queries": int(j.numel())}
+    with wt.build(sym, wl.sigma, sample_k=wl.sample_k) as t:
+        ms = timed(lambda: t.select(c, j, out=ref))
+        res["sampled"] = {"ms": ms, "Mqps": j.numel() / (ms * 1e-3) / 1e6}
+        inf = t.info()
+        sample_bytes = sum(((inf.level_size[l] - inf.level_ones[l]) // wl.sample_k + 1
+                            + inf.level_ones[l] // wl.sample_k + 1) * 8 for l in range(inf.levels))
+        res["sample_bytes"] = sample_bytes
+        for name, mode in (("pla", wt.LEARN_PLA), ("mlp", wt.LEARN_MLP)):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t.train_select(mode)
+            e1.record()
+            torch.cuda.synchronize()
+            train_ms = e0.elapsed_time(e1)
+            ms = timed(lambda: t.select_learned(c, j, out=out))
+            li = t.learned_info()
+            same = bool(torch.equal(out, ref))
+            epsm = [li.eps_mean[l][b] for l in range(inf.levels) for b in (0, 1)]
+            res[name] = {"ms": ms, "Mqps": j.numel() / (ms * 1e-3) / 1e6, "train_ms": train_ms,
+                         "identical_to_sampled": same, "fallbacks": int(li.fallbacks),
+                         "mean_window_bits": 2 * float(np.mean(epsm)) + 1,
+                         "model_bytes": int(li.model_bytes)}
+    return res
 
 
 def _measured_traffic(kernel, symbols_per_launch):

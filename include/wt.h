@@ -180,9 +180,67 @@ enum {
     WT_EXPORT_C = 5,
     WT_EXPORT_CODES = 6,
     WT_EXPORT_LENS = 7,
-    WT_EXPORT_NODES = 8
+    WT_EXPORT_NODES = 8,
+    WT_EXPORT_EPS0 = 9,  /* learned select: per-segment bound for zeros, floor(zeros/K)+1 uint32 */
+    WT_EXPORT_EPS1 = 10, /* learned select: per-segment bound for ones, floor(ones/K)+1 uint32 */
+    WT_EXPORT_MLP = 11   /* learned select: 2 x 97 float MLP parameters of the level (b = 0, then b = 1) */
 };
 wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, uint64_t* count);
+
+/*
+ * Learned select (not in the paper; the workload's "learned select").  For
+ * every level and bit value b a model predicts the position of the k-th b-bit
+ * from the select samples around k, which serve as knots: the sample positions
+ * S_b[m] of the (m K)-th b-bits (Section 4.2), with the virtual (count_b + 1)-th
+ * b-bit at the end of the level.
+ *   mode 1 (PLA): linear interpolation between the knots.
+ *   mode 2 (MLP): the fraction u = (k - mK) / (segment length) is mapped to
+ *          u + g(u), g a 1 -> 32 -> 1 ReLU network in FP32 per (level, b), trained
+ *          on the GPU with Adam on (u, position fraction) pairs drawn from the
+ *          built levels (opt->pairs per model, opt->steps steps, learning rate
+ *          opt->lr); g starts at 0, i.e. at mode 1.
+ * wt_train_select then evaluates the model at the rank of every b-bit of every
+ * level and stores per segment the largest distance between prediction and
+ * position (WT_EXPORT_EPS0/1).  wt_select_learned answers the same queries as
+ * wt_select: per level it searches only the window prediction +- bound; if the
+ * counters show the bit is outside the window the level falls back to the
+ * sampled select and a counter records it (wt_learned_info).  Results are
+ * identical to wt_select.  mode 0 removes the model.  Returns WT_EUNSUPPORTED
+ * from wt_select_learned if no model was trained.  wt_train_select allocates
+ * (stream-ordered on `stream`) and enqueues its work.
+ */
+typedef struct {
+    uint32_t steps;  /* Adam steps (default 300) */
+    uint32_t pairs;  /* training pairs per model, <= 16384 (default 8192) */
+    float lr;        /* learning rate (default 0.01) */
+    uint32_t reserved[5];
+} wt_train_options;
+
+wt_status wt_train_select(wt_tree tree, uint32_t mode, const wt_train_options* opt, wt_stream stream);
+wt_status wt_select_learned(wt_tree tree, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out, uint64_t q,
+                            wt_stream stream);
+
+typedef struct {
+    uint32_t mode;
+    uint32_t pad;
+    uint64_t fallbacks;                     /* level searches that left their window, since training */
+    uint64_t model_bytes;                   /* device bytes of bounds + parameters */
+    double eps_mean[WT_MAX_LEVELS][2];      /* mean per-segment bound, per level and b */
+    uint32_t eps_max[WT_MAX_LEVELS][2];
+} wt_learned_info_t;
+
+/* Synchronises the tree's stream; copies bound statistics to the host. */
+wt_status wt_learned_info(wt_tree tree, wt_learned_info_t* out);
+
+/*
+ * wt_mlp_gradient — one evaluation of the MLP's loss and gradient on the GPU,
+ * with the same device code the training kernel runs (for checking the
+ * backward pass).  Host arrays: h_params 97 floats {w1[32], b1[32], w2[32], b2},
+ * h_u / h_t n inputs and targets (n <= 16384); h_grad receives 97 floats,
+ * *h_loss the loss mean_i (u_i + g(u_i) - t_i)^2.  Synchronous.
+ */
+wt_status wt_mlp_gradient(const float* h_params, const float* h_u, const float* h_t, uint32_t n, float* h_grad,
+                          float* h_loss);
 
 /*
  * wt_bitvector_support_static — rank/select support of a caller-owned

@@ -18,13 +18,17 @@ LIB_PATH = os.path.join(_HERE, "libwt.so")
 
 WT_OK, WT_EINVAL, WT_ESYMBOL, WT_ENOMEM, WT_ECUDA, WT_EQUERY, WT_ETIMEOUT, WT_EUNSUPPORTED = range(8)
 EXPORT_BITS, EXPORT_L1, EXPORT_L2, EXPORT_S0, EXPORT_S1, EXPORT_C, EXPORT_CODES, EXPORT_LENS, EXPORT_NODES = range(9)
+EXPORT_EPS0, EXPORT_EPS1, EXPORT_MLP = 9, 10, 11
+LEARN_NONE, LEARN_PLA, LEARN_MLP = 0, 1, 2
+MLP_PARAMS = 97
 MAX_LEVELS = 26
 
 # every symbol include/wt.h declares (checked by the ABI test)
 EXPORTED = (
     "wt_build", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync",
     "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
-    "wt_profile_report", "wt_bitvector_support_static",
+    "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
+    "wt_mlp_gradient",
 )
 
 
@@ -48,6 +52,22 @@ class Info(ctypes.Structure):
         ("level_size", ctypes.c_uint64 * MAX_LEVELS),
         ("level_ones", ctypes.c_uint64 * MAX_LEVELS),
         ("tree_bytes", ctypes.c_uint64),
+    ]
+
+
+class TrainOptions(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("pairs", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("reserved", ctypes.c_uint32 * 5)]
+
+
+class LearnedInfo(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_uint32),
+        ("pad", ctypes.c_uint32),
+        ("fallbacks", ctypes.c_uint64),
+        ("model_bytes", ctypes.c_uint64),
+        ("eps_mean", (ctypes.c_double * 2) * MAX_LEVELS),
+        ("eps_max", (ctypes.c_uint32 * 2) * MAX_LEVELS),
     ]
 
 
@@ -84,8 +104,13 @@ def lib():
         L.wt_profile_report.restype = ctypes.c_size_t
         L.wt_bitvector_support_static.argtypes = [vp, u64, u32, vp, vp, vp, vp, u64, vp, vp]
         L.wt_bitvector_support_static.restype = ctypes.c_int
+        L.wt_train_select.argtypes = [vp, u32, ctypes.POINTER(TrainOptions), vp]
+        L.wt_select_learned.argtypes = [vp, vp, vp, vp, u64, vp]
+        L.wt_learned_info.argtypes = [vp, ctypes.POINTER(LearnedInfo)]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.wt_mlp_gradient.argtypes = [fp, fp, fp, u32, fp, fp]
         for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync", "wt_info",
-                  "wt_export"):
+                  "wt_export", "wt_train_select", "wt_select_learned", "wt_learned_info", "wt_mlp_gradient"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -230,6 +255,29 @@ class Tree:
                                         _dptr(out, "out"), q, _stream(stream)), "wt_query_mixed")
         return out
 
+    # ---- learned select ----
+    def train_select(self, mode: int = LEARN_PLA, steps: int = 0, pairs: int = 0, lr: float = 0.0, stream=None):
+        opt = TrainOptions(steps=steps, pairs=pairs, lr=lr)
+        _check(lib().wt_train_select(self._h, mode, ctypes.byref(opt), _stream(stream)), "wt_train_select")
+
+    def select_learned(self, c, j, out=None, stream=None):
+        import torch
+
+        q = j.numel()
+        if c.numel() != q:
+            raise ValueError("c and j must have the same length")
+        if out is None:
+            out = torch.empty(q, dtype=torch.int64, device=j.device)
+        if q:
+            _check(lib().wt_select_learned(self._h, _as_u32(c, "c"), _as_u64(j, "j"), _dptr(out, "out"), q,
+                                           _stream(stream)), "wt_select_learned")
+        return out
+
+    def learned_info(self) -> LearnedInfo:
+        inf = LearnedInfo()
+        _check(lib().wt_learned_info(self._h, ctypes.byref(inf)), "wt_learned_info")
+        return inf
+
     # ---- status / metadata ----
     def status_sync(self, stream=None) -> int:
         """Synchronise the stream; return and clear the sticky device status."""
@@ -243,7 +291,8 @@ class Tree:
     def export(self, what: int, level: int = 0) -> np.ndarray:
         cnt = ctypes.c_uint64()
         _check(lib().wt_export(self._h, level, what, None, ctypes.byref(cnt)), "wt_export")
-        dt = {EXPORT_L2: np.uint16, EXPORT_LENS: np.uint8}.get(what, np.uint64)
+        dt = {EXPORT_L2: np.uint16, EXPORT_LENS: np.uint8, EXPORT_EPS0: np.uint32, EXPORT_EPS1: np.uint32,
+              EXPORT_MLP: np.float32}.get(what, np.uint64)
         width = 4 if what == EXPORT_NODES else 1
         out = np.zeros(cnt.value * width, dt)
         if cnt.value:
@@ -254,6 +303,19 @@ class Tree:
 def build(symbols, sigma: int, sample_k: int = 4096, stream=None) -> Tree:
     """wt_build: construct the tree of a 1-D CUDA tensor of symbols in [0, sigma)."""
     return Tree(symbols, sigma, sample_k=sample_k, stream=stream)
+
+
+def mlp_gradient(params, u, t):
+    """Loss and gradient of the learned-select MLP on the GPU (the training kernel's code)."""
+    fp = ctypes.POINTER(ctypes.c_float)
+    P = np.ascontiguousarray(params, np.float32)
+    U = np.ascontiguousarray(u, np.float32)
+    T = np.ascontiguousarray(t, np.float32)
+    g = np.zeros(MLP_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(lib().wt_mlp_gradient(P.ctypes.data_as(fp), U.ctypes.data_as(fp), T.ctypes.data_as(fp), U.size,
+                                 g.ctypes.data_as(fp), ctypes.byref(loss)), "wt_mlp_gradient")
+    return g, float(loss.value)
 
 
 # ---- launch accounting / kernel timing ----

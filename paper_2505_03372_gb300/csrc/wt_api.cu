@@ -183,6 +183,7 @@ wt_status wt_build(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t s
 
 void wt_destroy(wt_tree tree) {
     if (!tree_ok(tree)) return;
+    free_learned(tree, tree->stream);
     dev_free(tree->hdr_mem, tree->stream);
     dev_free(tree->lvl_mem, tree->stream);
     tree->magic = 0;
@@ -296,6 +297,19 @@ wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, ui
             }
         }
         return WT_OK;
+    } else if (what == WT_EXPORT_EPS0 || what == WT_EXPORT_EPS1 || what == WT_EXPORT_MLP) {
+        if (level >= L || tree->learned.mode == kLearnNone) return WT_EUNSUPPORTED;
+        if (what == WT_EXPORT_MLP) {
+            cnt = 2 * kMlpParams;
+            src = tree->learned.mlp + 2 * level * kMlpParams;
+            esz = 4;
+        } else {
+            const uint32_t b = what == WT_EXPORT_EPS1;
+            const uint64_t c = b ? tree->level_ones[level] : tree->level_size[level] - tree->level_ones[level];
+            cnt = (c >> d.k_log2) + 1;
+            src = tree->learned.eps[level][b];
+            esz = 4;
+        }
     } else {
         if (level >= L) return WT_EINVAL;
         const LevelDesc& v = d.lv[level];

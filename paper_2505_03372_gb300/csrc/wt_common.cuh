@@ -187,6 +187,21 @@ struct TreeDesc {
     LevelDesc lv[kMaxLevels];
 };
 
+// Learned select (wt_train_select): per level and bit value b, the position of
+// the k-th b-bit is predicted between the select samples around k (the knots)
+// and the true position lies within eps[b][k >> k_log2] of the prediction.
+constexpr uint32_t kMlpHidden = 32;
+constexpr uint32_t kMlpParams = 3 * kMlpHidden + 1;  // w1[32], b1[32], w2[32], b2
+constexpr uint32_t kLearnNone = 0, kLearnPla = 1, kLearnMlp = 2;
+
+struct LearnedDesc {
+    uint32_t mode;                     // kLearnNone / kLearnPla / kLearnMlp
+    uint32_t pad;
+    const uint32_t* eps[kMaxLevels][2];  // per-segment error bounds, (count_b >> k_log2) + 1 entries
+    const float* mlp;                  // [level][b][kMlpParams], mode kLearnMlp only
+    unsigned long long* fallbacks;     // queries whose window check failed (answered by sampled select)
+};
+
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------

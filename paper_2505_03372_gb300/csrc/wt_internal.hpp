@@ -19,6 +19,10 @@ struct wt_tree_s {
     size_t hdr_bytes;
     void* lvl_mem;            // bit arrays, L1, L2, samples of every level
     size_t lvl_bytes;
+    // learned select (wt_train_select): per-segment error bounds, MLP parameters, counters
+    wt::LearnedDesc learned;
+    void* learned_mem;
+    size_t learned_bytes;
     uint64_t magic;
 };
 
@@ -44,6 +48,12 @@ void dev_free(void* p, cudaStream_t s);
 // ---- build (wt_build.cu) ----
 wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t w, uint32_t sample_k,
                      cudaStream_t s, wt_tree_s* t);
+
+// ---- learned select (wt_learned.cu) ----
+wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, uint32_t pairs, cudaStream_t s);
+wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out,
+                                uint64_t q, cudaStream_t s);
+void free_learned(wt_tree_s* t, cudaStream_t s);
 
 // ---- queries (wt_query.cu) ----
 wt_status launch_access(const wt_tree_s* t, const uint64_t* d_i, uint32_t* d_out, uint64_t q, cudaStream_t s);

@@ -309,3 +309,35 @@ def test_space_overheads_from_paper():
         samples = t.export(oracle.EXPORT_S0, 0).size + t.export(oracle.EXPORT_S1, 0).size
         pct = 100.0 * (l1 * 64 + l2 * 16 + samples * 64) / n
         assert round(pct, 1) == row["percent"]
+
+
+# --------------------------------------------------------------------------
+# learned-select network (FP64 reference) against central differences
+# --------------------------------------------------------------------------
+
+def test_mlp_backward_matches_finite_differences():
+    from oracle import mlp
+
+    rng = np.random.default_rng(11)
+    for trial in range(4):
+        P = rng.normal(size=mlp.NPARAM)
+        u = rng.random(300)
+        t = u + 0.1 * rng.normal(size=300)
+        loss, g = mlp.loss_and_grad(P, u, t)
+        fd = mlp.finite_difference_grad(P, u, t)
+        assert np.allclose(g, fd, rtol=1e-6, atol=1e-7), trial
+        # the loss is the mean squared error of u + g(u) against t, recomputed directly
+        y, _, _ = mlp.forward(P, u)
+        assert abs(loss - float(np.mean((u + y - t) ** 2))) < 1e-12
+
+
+def test_pla_predictor_hits_its_knots():
+    from oracle import mlp
+
+    samples = np.array([0, 7000, 15000, 21000], np.uint64)
+    K, total, size = 4096, 3 * 4096 + 100, 22000
+    for m in range(4):
+        kn = mlp.knots(samples, total, size, m, K)
+        assert mlp.predict_pla(kn, kn[0]) == kn[2]
+        if m < 3:
+            assert mlp.predict_pla(kn, kn[1]) == kn[3]
