@@ -40,6 +40,7 @@ extern "C" {
 
 typedef struct CUstream_st* wt_stream; /* identical to cudaStream_t */
 typedef struct wt_tree_s* wt_tree;     /* opaque, owned by libwt, immutable after build */
+typedef struct wt_batch_s* wt_batch;   /* opaque: many trees built and queried by one graph launch */
 
 typedef enum {
     WT_OK = 0,
@@ -231,6 +232,46 @@ typedef struct {
 
 /* Synchronises the tree's stream; copies bound statistics to the host. */
 wt_status wt_learned_info(wt_tree tree, wt_learned_info_t* out);
+
+/*
+ * Batches of independent trees (not in the paper; the workload of thousands of
+ * small trees).  wt_batch_create lays out ntrees trees in one device
+ * allocation — sizes are worst cases from n and sigma, so nothing is read back
+ * — and captures into one CUDA graph the whole construction of every tree
+ * (the same steps as wt_build, each a kernel over all trees at once: one
+ * persistent level-pass kernel per level walks the tiles of every tree) plus
+ * the query batch registered with wt_batch_set_queries.  wt_batch_run launches
+ * that graph on `stream` (no host synchronisation inside); it may be run again
+ * after the caller rewrites the symbol or query buffers in place.
+ *
+ *  h_symbols  host array of ntrees device pointers (16-byte aligned) to each
+ *             tree's symbols; the buffers must stay valid while the batch runs.
+ *  h_n, h_sigma  host arrays of sizes and alphabet sizes (limits as wt_build).
+ *  opt        sample_k as in wt_options; query_threads 128, 256 or 512 threads
+ *             per CTA of the query kernel (default 256); NULL for defaults.
+ * Queries: d_tree[k] < ntrees selects the tree, then d_kind / d_c / d_arg /
+ * d_out as in wt_query_mixed.  A tree index >= ntrees yields UINT64_MAX.
+ * wt_batch_status_sync reports the OR of every tree's sticky status.
+ * wt_batch_tree returns a handle on one tree of the batch (after a run) for
+ * wt_info / wt_export / wt_access / ... ; it shares the batch's memory, must
+ * be released with wt_destroy before wt_batch_destroy, and reflects the
+ * contents of the last completed run.
+ */
+typedef struct {
+    uint32_t sample_k;
+    uint32_t query_threads;
+    uint32_t reserved[6];
+} wt_batch_options;
+
+wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const uint64_t* h_n, const uint32_t* h_sigma,
+                          uint32_t symbol_bytes, const wt_batch_options* opt, wt_batch* out);
+wt_status wt_batch_set_queries(wt_batch batch, const uint32_t* d_tree, const uint8_t* d_kind, const uint32_t* d_c,
+                               const uint64_t* d_arg, uint64_t* d_out, uint64_t q);
+wt_status wt_batch_run(wt_batch batch, wt_stream stream);
+wt_status wt_batch_status_sync(wt_batch batch, wt_stream stream);
+wt_status wt_batch_tree(wt_batch batch, uint32_t index, wt_tree* out);
+uint64_t wt_batch_bytes(wt_batch batch);
+void wt_batch_destroy(wt_batch batch);
 
 /*
  * wt_mlp_gradient — one evaluation of the MLP's loss and gradient on the GPU,

@@ -8,6 +8,6 @@ sources (``csrc/``), their in-tree build (``_build.py``), the ctypes binding
 """
 from .binding import (  # noqa: F401
     EXPORT_BITS, EXPORT_C, EXPORT_CODES, EXPORT_L1, EXPORT_L2, EXPORT_LENS, EXPORT_NODES, EXPORT_S0, EXPORT_S1,
-    WT_EINVAL, WT_EQUERY, WT_ESYMBOL, WT_ETIMEOUT, WT_OK, Tree, WTError, build, profile_enable, profile_launches,
+    WT_EINVAL, WT_EQUERY, WT_ESYMBOL, WT_ETIMEOUT, WT_OK, Batch, Tree, WTError, build, profile_enable, profile_launches,
     profile_report, profile_reset, status_str,
 )

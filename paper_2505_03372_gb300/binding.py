@@ -28,7 +28,8 @@ EXPORTED = (
     "wt_build", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync",
     "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
     "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
-    "wt_mlp_gradient",
+    "wt_mlp_gradient", "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync",
+    "wt_batch_tree", "wt_batch_bytes", "wt_batch_destroy",
 )
 
 
@@ -71,6 +72,10 @@ class LearnedInfo(ctypes.Structure):
     ]
 
 
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("sample_k", ctypes.c_uint32), ("query_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+
+
 _lib = None
 
 
@@ -109,8 +114,19 @@ def lib():
         L.wt_learned_info.argtypes = [vp, ctypes.POINTER(LearnedInfo)]
         fp = ctypes.POINTER(ctypes.c_float)
         L.wt_mlp_gradient.argtypes = [fp, fp, fp, u32, fp, fp]
+        L.wt_batch_create.argtypes = [u32, ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(u32), u32,
+                                      ctypes.POINTER(BatchOptions), ctypes.POINTER(vp)]
+        L.wt_batch_set_queries.argtypes = [vp, vp, vp, vp, vp, vp, u64]
+        L.wt_batch_run.argtypes = [vp, vp]
+        L.wt_batch_status_sync.argtypes = [vp, vp]
+        L.wt_batch_tree.argtypes = [vp, u32, ctypes.POINTER(vp)]
+        L.wt_batch_bytes.argtypes = [vp]
+        L.wt_batch_bytes.restype = u64
+        L.wt_batch_destroy.argtypes = [vp]
+        L.wt_batch_destroy.restype = None
         for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync", "wt_info",
-                  "wt_export", "wt_train_select", "wt_select_learned", "wt_learned_info", "wt_mlp_gradient"):
+                  "wt_export", "wt_train_select", "wt_select_learned", "wt_learned_info", "wt_mlp_gradient",
+                  "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync", "wt_batch_tree"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -161,6 +177,15 @@ def _as_u32(t, name):
 
 class Tree:
     """Handle of a wavelet tree built on the GPU (wt_build)."""
+
+    @classmethod
+    def _view(cls, handle, n: int, sigma: int, symbol_bytes: int):
+        t = cls.__new__(cls)
+        t._h = handle
+        t.n, t.sigma, t.symbol_bytes = n, sigma, symbol_bytes
+        t._stream = None
+        t.levels = t.info().levels
+        return t
 
     def __init__(self, symbols, sigma: int, sample_k: int = 4096, stream=None):
         import torch
@@ -303,6 +328,72 @@ class Tree:
 def build(symbols, sigma: int, sample_k: int = 4096, stream=None) -> Tree:
     """wt_build: construct the tree of a 1-D CUDA tensor of symbols in [0, sigma)."""
     return Tree(symbols, sigma, sample_k=sample_k, stream=stream)
+
+
+class Batch:
+    """Many independent trees built and queried by one CUDA graph launch (wt_batch_*).
+
+    symbols: list of 1-D CUDA tensors (16-byte aligned, same element size); they
+    must stay alive and unchanged in size while the batch exists."""
+
+    def __init__(self, symbols, sigmas, sample_k: int = 4096, query_threads: int = 256):
+        self._syms = list(symbols)
+        nt = len(self._syms)
+        w = self._syms[0].element_size()
+        ptrs = (ctypes.c_void_p * nt)(*[t.data_ptr() if t.numel() else None for t in self._syms])
+        ns = (ctypes.c_uint64 * nt)(*[t.numel() for t in self._syms])
+        sg = (ctypes.c_uint32 * nt)(*[int(x) for x in sigmas])
+        self.n = [t.numel() for t in self._syms]
+        self.sigma = [int(x) for x in sigmas]
+        self.symbol_bytes = w
+        opt = BatchOptions(sample_k=sample_k, query_threads=query_threads)
+        h = ctypes.c_void_p()
+        _check(lib().wt_batch_create(nt, ptrs, ns, sg, w, ctypes.byref(opt), ctypes.byref(h)), "wt_batch_create")
+        self._h = h
+        self._q = None
+
+    def set_queries(self, tree, kind, c, arg, out=None):
+        import torch
+
+        q = arg.numel()
+        if out is None:
+            out = torch.empty(q, dtype=torch.int64, device=arg.device)
+        self._q = (tree, kind, c, arg, out)  # keep the buffers alive
+        _check(lib().wt_batch_set_queries(self._h, _as_u32(tree, "tree"), _dptr(kind, "kind"), _as_u32(c, "c"),
+                                          _as_u64(arg, "arg"), _dptr(out, "out"), q), "wt_batch_set_queries")
+        return out
+
+    def run(self, stream=None):
+        _check(lib().wt_batch_run(self._h, _stream(stream)), "wt_batch_run")
+
+    def status_sync(self, stream=None) -> int:
+        return lib().wt_batch_status_sync(self._h, _stream(stream))
+
+    def tree(self, i: int) -> "Tree":
+        h = ctypes.c_void_p()
+        _check(lib().wt_batch_tree(self._h, i, ctypes.byref(h)), "wt_batch_tree")
+        return Tree._view(h, self.n[i], self.sigma[i], self.symbol_bytes)
+
+    def nbytes(self) -> int:
+        return int(lib().wt_batch_bytes(self._h))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().wt_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def mlp_gradient(params, u, t):

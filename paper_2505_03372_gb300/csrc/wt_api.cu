@@ -92,6 +92,12 @@ void prof_before(const char* name, cudaStream_t s) {
     }
 }
 
+void prof_count(const char* name, uint64_t n) {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stats[name].launches += n;
+}
+
 void prof_after(const char* name, cudaStream_t s) {
     if (!g_timing.load() || !tl_start) return;
     std::lock_guard<std::mutex> lk(g_mu);

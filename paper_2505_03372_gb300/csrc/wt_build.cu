@@ -317,30 +317,6 @@ __device__ __forceinline__ uint64_t lb_flag(uint64_t s) { return s & 3u; }
 __device__ __forceinline__ uint64_t lb_agg(uint64_t s) { return (s >> 2) & ((1u << 19) - 1); }
 __device__ __forceinline__ uint64_t lb_incl(uint64_t s) { return s >> 21; }
 
-struct LevelPassArgs {
-    const void* src;   // T_l
-    void* dst;         // T_{l+1}, or null at the last level
-    uint64_t size;     // size_l
-    uint64_t size_next;
-    uint64_t ntiles;
-    uint64_t words_alloc;
-    uint64_t* words;
-    uint64_t* l1;
-    uint16_t* l2;
-    uint64_t* s0;
-    uint64_t* s1;
-    uint64_t n_s0, n_s1;     // allocated sample entries (writes beyond are dropped)
-    const NodeEntry* nodes;  // level-l slice of the node table
-    uint64_t* state;         // ntiles look-back words, zeroed
-    uint32_t* counter;       // tile counter, zeroed
-    uint32_t* status;
-    uint32_t level;
-    uint32_t shift_bit;  // L - 1 - l
-    uint32_t pshift;     // L - l (prefix = code >> pshift), unused at level 0
-    uint32_t k_log2;
-    uint32_t ctab_n;     // level 0 re-encoding: table size (0 = compute codes arithmetically)
-    CodeParams cp;       // used when re-encoding at level 0
-};
 
 // 32-bit shared-memory addressing for the byte / half / word scatter stores
 __device__ __forceinline__ void sts_elem(uint32_t addr, uint8_t v) {
@@ -406,8 +382,11 @@ __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V,
     }
 }
 
+// One tile of one level pass (the phases below).  Called by every thread of the
+// CTA; returns whether the tile's load used the mbarrier (its parity flips).
 template <typename T, bool ENCODE>
-__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM) level_pass_kernel(const __grid_constant__ LevelPassArgs a) {
+__device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const uint64_t tile, uint8_t* smem,
+                                                uint64_t* mbar_p, uint32_t mphase) {
     constexpr int W = sizeof(T);
     constexpr int VEPL = 16 / W;                // elements per lane per group (one uint4 per lane)
     constexpr int EPW = 4 / W;                  // elements per 32-bit word
@@ -423,51 +402,35 @@ __global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpB
     constexpr uint32_t LOWB = (W == 1) ? 0x01010101u : (W == 2 ? 0x00010001u : 1u);  // bit 0 of every element
     static_assert(NG % NWARP == 0 && NG <= 64, "tile shape");
 
-    extern __shared__ __align__(128) uint8_t smem[];
     uint4* in4 = reinterpret_cast<uint4*>(smem);
     uint8_t* outb = smem + kTileBytes;
     uint8_t* wbytes = smem + 2 * kTileBytes + 64;                               // level bits of the tile
     uint32_t* rpre = reinterpret_cast<uint32_t*>(wbytes + kTileBytes / 8 / W);  // NG + 1
     T* ctab = reinterpret_cast<T*>(rpre + 64 + 1);                              // code table (ENCODE, small sigma)
 
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint64_t s_tile, s_E, s_EL1, s_p;
+    __shared__ uint64_t s_E, s_EL1, s_p;
     __shared__ uint32_t s_single;
     __shared__ uint32_t s_gcnt[64];
     __shared__ uint32_t s_gnext;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_tile = atomicAdd(a.counter, 1u);
-        mbar_init(&mbar, 1);
-        mbar_fence_init();
-    }
-    if (ENCODE && a.ctab_n) {
-        for (uint32_t s = tid; s < a.ctab_n; s += kLpThreads) {
-            uint32_t code, len;
-            encode(a.cp, s, code, len);
-            ctab[s] = (T)code;
-        }
-    }
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    if (tile >= a.ntiles) return;
     const uint64_t t0 = tile * TE;
     const uint32_t count = (uint32_t)umin64((uint64_t)TE, a.size - t0);
     const bool full = count == (uint32_t)TE;
     const uint32_t bytes = count * W;
     const uint32_t b16 = bytes & ~15u;
     const uint8_t* srcb = reinterpret_cast<const uint8_t*>(a.src) + t0 * W;
+    const bool used_mbar = b16 != 0;
 
     // ---- phase 0: tile -> shared memory (TMA bulk copy + ragged tail) ----
     if (tid == 0 && b16) {
-        mbar_expect_tx(&mbar, b16);
-        bulk_g2s(smem, srcb, b16, &mbar);
+        mbar_expect_tx(mbar_p, b16);
+        bulk_g2s(smem, srcb, b16, mbar_p);
     }
     for (uint32_t i = b16 + tid; i < bytes; i += kLpThreads) smem[i] = srcb[i];
     if (b16) {
         uint32_t spins = 0;
-        while (!mbar_try_wait(&mbar, 0)) {
+        while (!mbar_try_wait(mbar_p, mphase)) {
             if (++spins > kSpinCap) {
                 if (lane == 0) set_status(a.status, kStTimeout);
                 break;
@@ -716,7 +679,7 @@ __global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpB
         }
     }
 
-    if (a.dst == nullptr) return;
+    if (a.dst == nullptr) return used_mbar;
 
     // ---- phase 5: shared-memory image -> T_{l+1} ----
     T* dst = reinterpret_cast<T*>(a.dst);
@@ -772,6 +735,77 @@ __global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpB
             const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off1) + E + i;
             if (Dx < lim) dst[Dx] = x;
         }
+    }
+    return used_mbar;
+}
+
+// Single tree: one CTA per tile, tiles taken in order from a counter.
+template <typename T, bool ENCODE>
+__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM)
+    level_pass_kernel(const __grid_constant__ LevelPassArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint64_t s_tile;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_tile = atomicAdd(a.counter, 1u);
+        mbar_init(&mbar, 1);
+        mbar_fence_init();
+    }
+    if (ENCODE && a.ctab_n) {
+        constexpr int W = sizeof(T);
+        T* ctab = reinterpret_cast<T*>(smem + 2 * kTileBytes + 64 + kTileBytes / 8 / W + (64 + 1) * 4);
+        for (uint32_t s = tid; s < a.ctab_n; s += kLpThreads) {
+            uint32_t code, len;
+            encode(a.cp, s, code, len);
+            ctab[s] = (T)code;
+        }
+    }
+    __syncthreads();
+    if (s_tile >= a.ntiles) return;
+    level_pass_tile<T, ENCODE>(a, s_tile, smem, &mbar, 0);
+}
+
+// Many trees: a persistent grid walks the concatenation of every tree's tiles
+// (tile_prefix[i] = tiles of trees before i), so each tree's tiles are taken in
+// order and its look-back only waits on running CTAs.  Codes are computed
+// arithmetically (no shared code table).
+template <typename T, bool ENCODE>
+__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM)
+    level_pass_batched_kernel(const LevelPassArgs* __restrict__ args, const uint64_t* __restrict__ tile_prefix,
+                              uint32_t ntrees, unsigned long long* __restrict__ counter) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint64_t s_g;
+    __shared__ uint32_t s_tree;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const uint64_t total = tile_prefix[ntrees];
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) {
+            const uint64_t g = atomicAdd(counter, 1ull);
+            s_g = g;
+            if (g < total) {
+                uint32_t lo = 0, hi = ntrees - 1;  // last tree whose first tile is <= g
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (tile_prefix[mid] <= g) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_tree = lo;
+            }
+        }
+        __syncthreads();
+        const uint64_t g = s_g;
+        if (g >= total) break;
+        const uint32_t tr = s_tree;
+        if (level_pass_tile<T, ENCODE>(args[tr], g - tile_prefix[tr], smem, &mbar, phase)) phase ^= 1u;
+        __syncthreads();
     }
 }
 
@@ -1021,6 +1055,225 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         }
     }
     dev_free(scratch, s);
+    return WT_OK;
+}
+
+// ===========================================================================
+// batches of trees: the same pipeline for many trees, with no host round trip
+// (every size the host would read back is computed on the device), so the
+// whole sequence can be captured in one CUDA graph
+// ===========================================================================
+
+uint64_t batch_tile_elems(uint32_t w) { return (uint64_t)kTileBytes / w; }
+
+__device__ __forceinline__ uint32_t find_tree(const uint64_t* prefix, uint32_t ntrees, uint64_t g) {
+    uint32_t lo = 0, hi = ntrees - 1;  // last tree whose first item is <= g
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr uint32_t kBatchSmemBins = 4096;
+
+// one CTA per chunk of kBatchChunk symbols of one tree
+template <typename T>
+__global__ void __launch_bounds__(512) batch_hist_kernel(const BatchTreeInfo* __restrict__ info,
+                                                         const uint64_t* __restrict__ chunk_prefix, uint32_t ntrees) {
+    __shared__ uint32_t sh[kBatchSmemBins];
+    __shared__ uint32_t s_tree;
+    const uint64_t g = blockIdx.x;
+    if (threadIdx.x == 0) s_tree = find_tree(chunk_prefix, ntrees, g);
+    __syncthreads();
+    const BatchTreeInfo& ti = info[s_tree];
+    const uint64_t c0 = (g - chunk_prefix[s_tree]) * kBatchChunk;
+    const uint64_t c1 = umin64(ti.n, c0 + kBatchChunk);
+    const uint32_t sigma = ti.sigma;
+    const bool small = sigma <= kBatchSmemBins;
+    if (small)
+        for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const T* S = reinterpret_cast<const T*>(ti.sym);
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(ti.hist);
+    bool bad = false;
+    for (uint64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+        const uint32_t v = (uint32_t)S[j];
+        if (v >= sigma) bad = true;
+        else if (small) atomicAdd(sh + v, 1u);
+        else atomicAdd(hist + v, 1ull);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(ti.status, kStSymbol);
+    if (small)
+        for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x)
+            if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
+}
+
+// one CTA per tree: C = exclusive scan of the histogram
+__global__ void __launch_bounds__(kScanThreads) batch_C_kernel(const BatchTreeInfo* __restrict__ info) {
+    const BatchTreeInfo& ti = info[blockIdx.x];
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < ti.sigma; base += kScanChunk) {
+        const uint64_t c = umin64((uint64_t)kScanChunk, ti.sigma - base);
+        carry += block_scan_chunk(ti.hist + base, ti.C + base, c, carry);
+    }
+    if (threadIdx.x == 0) ti.C[ti.sigma] = carry;
+}
+
+// one thread per node slot of every tree
+__global__ void batch_node_start_kernel(const BatchTreeInfo* __restrict__ info, const TreeDesc* __restrict__ desc,
+                                        const uint64_t* __restrict__ slot_prefix, uint32_t ntrees, uint64_t total) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const uint32_t tr = find_tree(slot_prefix, ntrees, g);
+    const BatchTreeInfo& ti = info[tr];
+    const uint64_t slot = g - slot_prefix[tr];
+    const uint32_t l = 63u - (uint32_t)__clzll((long long)(slot + 1));
+    const uint64_t p = slot + 1 - (1ull << l);
+    uint64_t a = 0;
+    const uint64_t wd = node_info(desc[tr].cp, l, p, a);
+    NodeEntry e = {0, 0, 0, 0};
+    uint64_t lf = 0;
+    if (wd >= 2) {
+        e.start = ti.C[a];
+        lf = ti.C[node_mid(a, wd)] - e.start;
+    }
+    ti.nodes[slot] = e;
+    ti.left[slot] = lf;
+}
+
+// one CTA per tree: exclusive scan of the left-child sizes over the tree's slots
+__global__ void __launch_bounds__(kScanThreads) batch_left_scan_kernel(const BatchTreeInfo* __restrict__ info) {
+    const BatchTreeInfo& ti = info[blockIdx.x];
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < ti.nslots; base += kScanChunk) {
+        const uint64_t c = umin64((uint64_t)kScanChunk, ti.nslots - base);
+        carry += block_scan_chunk(ti.left + base, ti.excl + base, c, carry);
+    }
+    if (threadIdx.x == 0) ti.excl[ti.nslots] = carry;
+}
+
+__global__ void batch_node_finish_kernel(const BatchTreeInfo* __restrict__ info,
+                                         const uint64_t* __restrict__ slot_prefix, uint32_t ntrees, uint64_t total) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const uint32_t tr = find_tree(slot_prefix, ntrees, g);
+    const BatchTreeInfo& ti = info[tr];
+    const uint64_t slot = g - slot_prefix[tr];
+    const uint32_t l = 63u - (uint32_t)__clzll((long long)(slot + 1));
+    NodeEntry e = ti.nodes[slot];
+    const uint64_t r0 = ti.excl[slot] - ti.excl[(1ull << l) - 1];
+    e.r0 = r0;
+    e.off0 = e.start - r0;
+    e.off1 = ti.left[slot] + r0;
+    ti.nodes[slot] = e;
+}
+
+// one thread per (tree, level): level sizes and ones into the tree descriptors
+// and the level-pass arguments; tiles per level
+__global__ void batch_meta_kernel(const BatchTreeInfo* __restrict__ info, TreeDesc* __restrict__ desc,
+                                  LevelPassArgs* __restrict__ lpa, uint64_t* __restrict__ tiles, uint32_t ntrees,
+                                  uint32_t maxL, uint64_t te, uint32_t kl) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)ntrees * maxL) return;
+    const uint32_t tr = (uint32_t)(g % ntrees), l = (uint32_t)(g / ntrees);
+    const BatchTreeInfo& ti = info[tr];
+    LevelPassArgs& a = lpa[(uint64_t)l * ntrees + tr];
+    if (l >= ti.L || ti.n == 0) {
+        a.ntiles = 0;
+        tiles[(uint64_t)l * ntrees + tr] = 0;
+        if (l < ti.L) {
+            desc[tr].lv[l].size = 0;
+            desc[tr].lv[l].ones = 0;
+        }
+        return;
+    }
+    const uint64_t size = ti.C[ti.s0[l]];
+    const uint64_t zeros = ti.excl[(2ull << l) - 1] - ti.excl[(1ull << l) - 1];
+    const uint64_t ones = size - zeros;
+    desc[tr].lv[l].size = size;
+    desc[tr].lv[l].ones = ones;
+    a.size = size;
+    a.size_next = (l + 1 < ti.L) ? ti.C[ti.s0[l + 1]] : 0;
+    a.ntiles = (size + te - 1) / te;
+    a.n_s0 = (zeros >> kl) + 1;
+    a.n_s1 = (ones >> kl) + 1;
+    tiles[(uint64_t)l * ntrees + tr] = a.ntiles;
+}
+
+// one CTA per level: exclusive scan of the trees' tile counts
+__global__ void __launch_bounds__(kScanThreads) batch_tile_scan_kernel(const uint64_t* __restrict__ tiles,
+                                                                       uint64_t* __restrict__ prefix,
+                                                                       uint32_t ntrees) {
+    const uint64_t* in = tiles + (uint64_t)blockIdx.x * ntrees;
+    uint64_t* out = prefix + (uint64_t)blockIdx.x * (ntrees + 1);
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < ntrees; base += kScanChunk) {
+        const uint64_t c = umin64((uint64_t)kScanChunk, ntrees - base);
+        carry += block_scan_chunk(in + base, out + base, c, carry);
+    }
+    if (threadIdx.x == 0) out[ntrees] = carry;
+}
+
+template <typename T, bool ENC>
+static cudaError_t launch_level_pass_batched(const BatchDev& b, uint32_t l, cudaStream_t s) {
+    static bool configured = false;
+    const size_t sm = level_pass_smem<T, ENC>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(level_pass_batched_kernel<T, ENC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int grid = sm_count() * (ENC ? kLpBlocksPerSM - 1 : kLpBlocksPerSM);
+    level_pass_batched_kernel<T, ENC><<<grid, kLpThreads, sm, s>>>(b.lpa + (uint64_t)l * b.ntrees,
+                                                                   b.tile_prefix + (uint64_t)l * (b.ntrees + 1),
+                                                                   b.ntrees, b.counters + l);
+    return cudaGetLastError();
+}
+
+wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kernels) {
+    uint32_t nk = 0;
+    WT_CUDA_TRY(cudaMemsetAsync(b.hist_pool, 0, b.hist_bytes, s));
+    WT_CUDA_TRY(cudaMemsetAsync(b.status_pool, 0, (size_t)b.ntrees * 4, s));
+    WT_CUDA_TRY(cudaMemsetAsync(b.counters, 0, (size_t)b.maxL * 8, s));
+    if (b.total_chunks) {
+        nk++;
+        if (b.w == 1) batch_hist_kernel<uint8_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
+        else if (b.w == 2) batch_hist_kernel<uint16_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
+        else batch_hist_kernel<uint32_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
+    }
+    batch_C_kernel<<<b.ntrees, kScanThreads, 0, s>>>(b.info);
+    nk++;
+    if (b.total_slots) {
+        nk += 3;
+        batch_node_start_kernel<<<(unsigned)((b.total_slots + 255) / 256), 256, 0, s>>>(b.info, b.desc, b.slot_prefix,
+                                                                                       b.ntrees, b.total_slots);
+        batch_left_scan_kernel<<<b.ntrees, kScanThreads, 0, s>>>(b.info);
+        batch_node_finish_kernel<<<(unsigned)((b.total_slots + 255) / 256), 256, 0, s>>>(b.info, b.slot_prefix,
+                                                                                        b.ntrees, b.total_slots);
+    }
+    if (b.maxL) {
+        const uint64_t te = batch_tile_elems(b.w);
+        const uint64_t nm = (uint64_t)b.ntrees * b.maxL;
+        nk += 2;
+        batch_meta_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(b.info, b.desc, b.lpa, b.tiles, b.ntrees, b.maxL,
+                                                                       te, b.k_log2);
+        batch_tile_scan_kernel<<<b.maxL, kScanThreads, 0, s>>>(b.tiles, b.tile_prefix, b.ntrees);
+    }
+    WT_CUDA_TRY(cudaGetLastError());
+    for (uint32_t l = 0; l < b.maxL; l++) {
+        WT_CUDA_TRY(cudaMemsetAsync(b.state_pool, 0, b.state_bytes, s));
+        cudaError_t e;
+        const bool enc = l == 0;
+        if (b.w == 1) e = enc ? launch_level_pass_batched<uint8_t, true>(b, l, s) : launch_level_pass_batched<uint8_t, false>(b, l, s);
+        else if (b.w == 2) e = enc ? launch_level_pass_batched<uint16_t, true>(b, l, s) : launch_level_pass_batched<uint16_t, false>(b, l, s);
+        else e = enc ? launch_level_pass_batched<uint32_t, true>(b, l, s) : launch_level_pass_batched<uint32_t, false>(b, l, s);
+        if (e != cudaSuccess) return WT_ECUDA;
+        nk++;
+    }
+    if (kernels) *kernels = nk;
     return WT_OK;
 }
 

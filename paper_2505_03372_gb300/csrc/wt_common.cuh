@@ -187,6 +187,32 @@ struct TreeDesc {
     LevelDesc lv[kMaxLevels];
 };
 
+// Arguments of one level pass over one tree (see wt_build.cu).
+struct LevelPassArgs {
+    const void* src;   // T_l
+    void* dst;         // T_{l+1}, or null at the last level
+    uint64_t size;     // size_l
+    uint64_t size_next;
+    uint64_t ntiles;
+    uint64_t words_alloc;
+    uint64_t* words;
+    uint64_t* l1;
+    uint16_t* l2;
+    uint64_t* s0;
+    uint64_t* s1;
+    uint64_t n_s0, n_s1;     // allocated sample entries (writes beyond are dropped)
+    const NodeEntry* nodes;  // level-l slice of the node table
+    uint64_t* state;         // ntiles look-back words, zeroed
+    uint32_t* counter;       // tile counter, zeroed
+    uint32_t* status;
+    uint32_t level;
+    uint32_t shift_bit;  // L - 1 - l
+    uint32_t pshift;     // L - l (prefix = code >> pshift), unused at level 0
+    uint32_t k_log2;
+    uint32_t ctab_n;     // level 0 re-encoding: table size (0 = compute codes arithmetically)
+    CodeParams cp;       // used when re-encoding at level 0
+};
+
 // Learned select (wt_train_select): per level and bit value b, the position of
 // the k-th b-bit is predicted between the select samples around k (the knots)
 // and the true position lies within eps[b][k >> k_log2] of the prediction.

@@ -23,6 +23,7 @@ struct wt_tree_s {
     wt::LearnedDesc learned;
     void* learned_mem;
     size_t learned_bytes;
+    uint32_t is_view;         // a tree of a batch (wt_batch_tree): memory belongs to the batch
     uint64_t magic;
 };
 
@@ -33,6 +34,7 @@ namespace wt {
 // ---- launch accounting / timing (wt_profile.cu) ----
 void prof_before(const char* name, cudaStream_t s);
 void prof_after(const char* name, cudaStream_t s);
+void prof_count(const char* name, uint64_t n);  // count launches without timing them (graph runs)
 
 struct ProfScope {
     const char* n;
@@ -54,6 +56,45 @@ wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, ui
 wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out,
                                 uint64_t q, cudaStream_t s);
 void free_learned(wt_tree_s* t, cudaStream_t s);
+
+// ---- batches of trees (wt_batch.cu, built by wt_build.cu) ----
+struct BatchTreeInfo {
+    const void* sym;
+    uint64_t n;
+    uint32_t sigma;
+    uint32_t L;
+    uint64_t nslots;           // 2^L - 1
+    uint64_t* hist;            // sigma
+    uint64_t* C;               // sigma + 1
+    NodeEntry* nodes;          // nslots (at least 1)
+    uint64_t* left;            // nslots
+    uint64_t* excl;            // nslots + 1
+    uint32_t* status;
+    uint64_t s0[kMaxLevels];   // first symbol whose code has length <= l (sigma if none)
+};
+
+struct BatchDev {
+    uint32_t ntrees, w, maxL, k_log2;
+    uint64_t total_chunks, total_slots;
+    BatchTreeInfo* info;
+    TreeDesc* desc;
+    LevelPassArgs* lpa;              // [maxL][ntrees]
+    uint64_t* tiles;                 // [maxL][ntrees]
+    uint64_t* tile_prefix;           // [maxL][ntrees + 1]
+    unsigned long long* counters;    // [maxL]
+    uint64_t* chunk_prefix;          // [ntrees + 1] histogram chunks per tree
+    uint64_t* slot_prefix;           // [ntrees + 1] node slots per tree
+    uint64_t* hist_pool;
+    size_t hist_bytes;
+    uint64_t* state_pool;
+    size_t state_bytes;
+    uint32_t* status_pool;           // [ntrees]
+};
+
+constexpr uint64_t kBatchChunk = 65536;  // symbols per histogram work item
+
+wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kernels);
+uint64_t batch_tile_elems(uint32_t w);
 
 // ---- queries (wt_query.cu) ----
 wt_status launch_access(const wt_tree_s* t, const uint64_t* d_i, uint32_t* d_out, uint64_t q, cudaStream_t s);

@@ -12,89 +12,9 @@
 #include <stdint.h>
 
 #include "wt_internal.hpp"
+#include "wt_walk.cuh"
 
 namespace wt {
-
-__device__ __forceinline__ ulonglong2 node_sr(const TreeDesc& t, uint32_t l, uint64_t p) {
-    // {start, r0} of node (l, p); slots are 32-byte aligned
-    return ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + ((1ull << l) - 1 + p)));
-}
-
-// Algorithm 5 with the early stop at nodes of at most two symbols.
-__device__ __forceinline__ uint32_t do_access(const TreeDesc& t, uint64_t i) {
-    const CodeParams& cp = t.cp;
-    if (cp.L == 0) return 0;
-    uint64_t p = 0;
-    for (uint32_t l = 0; l < cp.L; l++) {
-        uint64_t a, width;
-        if (cp.pow2) {
-            width = 1ull << (cp.L - l);
-            a = p << (cp.L - l);
-        } else {
-            width = node_info(cp, l, p, a);
-        }
-        if (width == 1) return (uint32_t)a;
-        const ulonglong2 ne = node_sr(t, l, p);
-        const uint64_t pos = ne.x + i;
-        if (width == 2) return (uint32_t)(a + bit_at(t.lv[l], pos));
-        uint32_t b;
-        const uint64_t r1 = rank1_bit(t.lv[l], pos, b);
-        const uint64_t zb = (pos - r1) - ne.y;  // zeros of the node before i
-        i = b ? i - zb : zb;
-        p = 2 * p + b;
-    }
-    return UINT32_MAX;  // not reached: every root-to-leaf path ends at a leaf
-}
-
-// Algorithm 6: the code of c gives the direction at every level.
-__device__ __forceinline__ uint64_t do_rank(const TreeDesc& t, uint32_t c, uint64_t i) {
-    const CodeParams& cp = t.cp;
-    uint32_t code, len;
-    encode(cp, c, code, len);
-    ulonglong2 ne = node_sr(t, 0, 0);
-    for (uint32_t l = 0; l < len; l++) {
-        if (i == 0) return 0;
-        const uint32_t b = (code >> (cp.L - 1 - l)) & 1u;
-        const uint64_t pos = ne.x + i;
-        const uint64_t r0n = ne.y;
-        if (l + 1 < len) ne = node_sr(t, l + 1, code >> (cp.L - 1 - l));  // next node, issued early
-        const uint64_t r1 = rank1(t.lv[l], pos);
-        const uint64_t zb = (pos - r1) - r0n;
-        i = b ? i - zb : zb;
-    }
-    return i;
-}
-
-// Algorithms 7 and 8: leaf to root; the node of c at level l is the prefix of
-// its code, so getNodeStart becomes a table index.
-__device__ __forceinline__ uint64_t do_select(const TreeDesc& t, uint32_t c, uint64_t j) {
-    const CodeParams& cp = t.cp;
-    uint32_t code, len;
-    encode(cp, c, code, len);
-    if (len == 0) return j - 1;
-    int l = (int)len - 1;
-    ulonglong2 ne = node_sr(t, (uint32_t)l, (uint64_t)code >> (cp.L - (uint32_t)l));
-    for (; l >= 0; l--) {
-        const uint32_t b = (code >> (cp.L - 1 - (uint32_t)l)) & 1u;
-        const uint64_t start = ne.x;
-        const uint64_t kb = b ? (start - ne.y) : ne.y;  // b-bits before the node
-        if (l > 0) ne = node_sr(t, (uint32_t)l - 1, (uint64_t)code >> (cp.L - (uint32_t)l + 1));
-        const uint64_t pos = select_b(t.lv[l], b, kb + j, t.k_log2);
-        j = pos + 1 - start;
-    }
-    return j - 1;
-}
-
-__device__ __forceinline__ bool select_valid(const TreeDesc& t, uint32_t c, uint64_t j) {
-    if (c >= t.cp.sigma || j == 0) return false;
-    return j <= __ldg(t.C + c + 1) - __ldg(t.C + c);
-}
-
-__device__ __forceinline__ void flag_query_error(const TreeDesc& t, bool bad) {
-    if (__any_sync(__activemask(), bad)) {
-        if (bad) atomicOr(t.status, kStQuery);
-    }
-}
 
 constexpr int kQThreads = 256;
 

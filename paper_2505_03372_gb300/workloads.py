@@ -176,3 +176,62 @@ def make_workload(name: str, device="cuda", n: int = None, scale_queries: float 
     counts = symbol_counts(sym, w.sigma)
     q = make_queries(w, sym, counts=counts, scale=scale_queries)
     return w, sym, q, counts
+
+
+# --------------------------------------------------------------------------
+# batched workload: thousands of independent trees
+# --------------------------------------------------------------------------
+
+BATCH_SIGMAS = (4, 256, 65536)
+
+
+def make_batch(ntrees: int = 4096, seed: int = SEED_BASE + 3, device="cuda", log_n=(10, 24), log_q=(4, 16),
+               sigmas=BATCH_SIGMAS, symbol_bytes: int = 2):
+    """Symbols and mixed queries of a batch of independent trees.
+
+    Tree i has n_i = floor(2^U(log_n)) symbols drawn uniformly from [0, sigma_i),
+    sigma_i drawn uniformly from `sigmas`, and floor(2^U(log_q)) queries, each
+    access, rank or select with probability 1/3 (arguments as in make_queries;
+    select's symbol is drawn uniformly among the symbols that occur in the tree).
+    All symbols live in one buffer; each tree starts on a 16-byte boundary.
+    Returns (buffer, per-tree views, sigmas, queries dict with tree/kind/c/arg).
+    """
+    g = generator(seed, device)
+    gh = torch.Generator()
+    gh.manual_seed(seed)
+    u = torch.rand(ntrees, generator=gh, dtype=torch.float64)
+    ns = torch.floor(2.0 ** (log_n[0] + u * (log_n[1] - log_n[0]))).to(torch.int64).tolist()
+    sg = [sigmas[i] for i in torch.randint(0, len(sigmas), (ntrees,), generator=gh).tolist()]
+    uq = torch.rand(ntrees, generator=gh, dtype=torch.float64)
+    qs = torch.floor(2.0 ** (log_q[0] + uq * (log_q[1] - log_q[0]))).to(torch.int64).tolist()
+    align = 16 // symbol_bytes
+    offs, tot = [], 0
+    for n in ns:
+        offs.append(tot)
+        tot += (n + align - 1) // align * align
+    dtype = {1: torch.uint8, 2: torch.int16, 4: torch.int32}[symbol_bytes]
+    buf = torch.zeros(max(tot, 1), dtype=dtype, device=device)
+    views = []
+    qt, qk, qc, qa = [], [], [], []
+    for i, (n, s, q, o) in enumerate(zip(ns, sg, qs, offs)):
+        v = torch.randint(0, s, (n,), generator=g, device=device, dtype=torch.int64)
+        cnt = torch.bincount(v, minlength=s)
+        if symbol_bytes == 2:
+            v = torch.where(v >= 32768, v - 65536, v)
+        buf[o:o + n] = v.to(dtype)
+        views.append(buf[o:o + n])
+        kind = torch.randint(0, 3, (q,), generator=g, device=device, dtype=torch.int64)
+        pos = torch.randint(0, max(n, 1), (q,), generator=g, device=device, dtype=torch.int64)
+        c_r = torch.randint(0, s, (q,), generator=g, device=device, dtype=torch.int64)
+        present = torch.nonzero(cnt).flatten()
+        c_s = present[torch.randint(0, max(present.numel(), 1), (q,), generator=g, device=device)] if present.numel() \
+            else torch.zeros(q, dtype=torch.int64, device=device)
+        cs_cnt = cnt[c_s] if present.numel() else torch.ones(q, dtype=torch.int64, device=device)
+        j = (torch.rand(q, generator=g, device=device, dtype=torch.float64) * cs_cnt).to(torch.int64) + 1
+        j = torch.minimum(j, cs_cnt)
+        qt.append(torch.full((q,), i, dtype=torch.int32, device=device))
+        qk.append(kind.to(torch.uint8))
+        qc.append(torch.where(kind == 1, c_r, torch.where(kind == 2, c_s, torch.zeros_like(c_r))).to(torch.int32))
+        qa.append(torch.where(kind == 2, j, pos))
+    queries = {"tree": torch.cat(qt), "kind": torch.cat(qk), "c": torch.cat(qc), "arg": torch.cat(qa)}
+    return buf, views, sg, queries
