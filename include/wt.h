@@ -324,6 +324,16 @@ wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64_t nbits, u
                                       uint16_t* d_l2, uint64_t* d_s0, uint64_t* d_s1, uint64_t sample_capacity,
                                       uint32_t* d_status, wt_stream stream);
 
+/*
+ * wt_selftest_lookback_timeout — diagnostic for the bounded device waits.
+ * Runs the build's decoupled look-back for a tile whose predecessor never
+ * publishes its count, with at most spin_cap polls (1 <= spin_cap <= 2^22;
+ * the build uses 2^22).  The wait gives up, the kernel records WT_ETIMEOUT in
+ * a status word and returns normally, so the context stays usable.  Returns
+ * WT_ETIMEOUT when that path works (the expected result).  Synchronous.
+ */
+wt_status wt_selftest_lookback_timeout(uint32_t spin_cap, wt_stream stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* wt_status_str(wt_status s);
 

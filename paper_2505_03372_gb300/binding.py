@@ -29,7 +29,7 @@ EXPORTED = (
     "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
     "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
     "wt_mlp_gradient", "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync",
-    "wt_batch_tree", "wt_batch_bytes", "wt_batch_destroy",
+    "wt_batch_tree", "wt_batch_bytes", "wt_batch_destroy", "wt_selftest_lookback_timeout",
 )
 
 
@@ -124,6 +124,8 @@ def lib():
         L.wt_batch_bytes.restype = u64
         L.wt_batch_destroy.argtypes = [vp]
         L.wt_batch_destroy.restype = None
+        L.wt_selftest_lookback_timeout.argtypes = [u32, vp]
+        L.wt_selftest_lookback_timeout.restype = ctypes.c_int
         for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync", "wt_info",
                   "wt_export", "wt_train_select", "wt_select_learned", "wt_learned_info", "wt_mlp_gradient",
                   "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync", "wt_batch_tree"):

@@ -382,6 +382,56 @@ __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V,
     }
 }
 
+// Decoupled look-back over tiles, run by one full warp: publish this tile's
+// count of ones (as its inclusive prefix if it is tile 0), walk back over the
+// earlier tiles 32 at a time summing aggregates until an inclusive prefix is
+// found, then publish this tile's inclusive prefix.  Returns the ones before
+// the tile.  Every wait is bounded: after spin_cap polls the warp sets
+// kStTimeout in *status, counts the missing predecessor as zero and returns.
+__device__ __forceinline__ uint64_t lookback_warp(uint64_t* state, uint64_t tile, uint64_t ones, uint32_t* status,
+                                               uint32_t spin_cap) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) st_relaxed_u64(state + tile, tile == 0 ? lb_pack(kFlagIncl, ones, ones) : lb_pack(kFlagAgg, ones, 0));
+    uint64_t excl = 0;
+    if (tile == 0) return 0;
+    int64_t base = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    bool timed_out = false;
+    while (true) {
+        const int64_t idx = base - lane;
+        uint64_t st = idx >= 0 ? ld_relaxed_u64(state + idx) : lb_pack(kFlagIncl, 0, 0);
+        while (__any_sync(0xffffffffu, lb_flag(st) == 0)) {
+            if (++spins > spin_cap) {
+                timed_out = true;
+                if (lb_flag(st) == 0) st = lb_pack(kFlagIncl, 0, 0);
+                break;
+            }
+            __nanosleep(20);
+            if (lb_flag(st) == 0) st = ld_relaxed_u64(state + idx);
+        }
+        const uint32_t im = __ballot_sync(0xffffffffu, lb_flag(st) == kFlagIncl);
+        if (im) {
+            const int first = __ffs(im) - 1;
+            const uint64_t v = lane < first ? lb_agg(st) : (lane == first ? lb_incl(st) : 0);
+            excl += warp_sum_u64(v);
+            break;
+        }
+        excl += warp_sum_u64(lb_agg(st));
+        base -= 32;
+    }
+    if (lane == 0) {
+        if (timed_out) set_status(status, kStTimeout);
+        st_relaxed_u64(state + tile, lb_pack(kFlagIncl, ones, excl + ones));
+    }
+    return excl;
+}
+
+// Diagnostic: tile 1 looks back at a tile 0 that never publishes anything.
+__global__ void lookback_timeout_kernel(uint64_t* state, uint32_t* status, uint32_t spin_cap, uint64_t* out) {
+    const uint64_t excl = lookback_warp(state, 1, 5, status, spin_cap);
+    if (threadIdx.x == 0) *out = excl;
+}
+
 // One tile of one level pass (the phases below).  Called by every thread of the
 // CTA; returns whether the tile's load used the mbarrier (its parity flips).
 template <typename T, bool ENCODE>
@@ -540,35 +590,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
     const uint32_t out_s = smem_addr(outb);
     if (warp == 0) {
         const uint64_t ones = ones32;
-        if (lane == 0) st_relaxed_u64(a.state + tile, tile == 0 ? lb_pack(kFlagIncl, ones, ones) : lb_pack(kFlagAgg, ones, 0));
-        uint64_t excl = 0;
-        if (tile > 0) {
-            int64_t base = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            while (true) {
-                const int64_t idx = base - lane;
-                uint64_t st = idx >= 0 ? ld_relaxed_u64(a.state + idx) : lb_pack(kFlagIncl, 0, 0);
-                while (__any_sync(0xffffffffu, lb_flag(st) == 0)) {
-                    if (++spins > kSpinCap) {
-                        if (lane == 0) set_status(a.status, kStTimeout);
-                        if (lb_flag(st) == 0) st = lb_pack(kFlagIncl, 0, 0);
-                        break;
-                    }
-                    __nanosleep(20);
-                    if (lb_flag(st) == 0) st = ld_relaxed_u64(a.state + idx);
-                }
-                const uint32_t im = __ballot_sync(0xffffffffu, lb_flag(st) == kFlagIncl);
-                if (im) {
-                    const int first = __ffs(im) - 1;
-                    uint64_t v = lane < first ? lb_agg(st) : (lane == first ? lb_incl(st) : 0);
-                    excl += warp_sum_u64(v);
-                    break;
-                }
-                excl += warp_sum_u64(lb_agg(st));
-                base -= 32;
-            }
-            if (lane == 0) st_relaxed_u64(a.state + tile, lb_pack(kFlagIncl, ones, excl + ones));
-        }
+        const uint64_t excl = lookback_warp(a.state, tile, ones, a.status, kSpinCap);
         // ones before the enclosing L1 block
         const uint32_t q = (uint32_t)(tile % TPL1);
         uint64_t sub = 0;
@@ -1278,3 +1300,23 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
 }
 
 }  // namespace wt
+
+extern "C" wt_status wt_selftest_lookback_timeout(uint32_t spin_cap, wt_stream stream) {
+    using namespace wt;
+    if (spin_cap == 0 || spin_cap > kSpinCap) return WT_EINVAL;
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, 256) != cudaSuccess) return WT_ENOMEM;
+    uint64_t* state = static_cast<uint64_t*>(mem);
+    uint32_t* status = reinterpret_cast<uint32_t*>(state + 4);
+    uint64_t* out = state + 8;
+    wt_status r = WT_ECUDA;
+    if (cudaMemsetAsync(mem, 0, 256, stream) == cudaSuccess) {
+        lookback_timeout_kernel<<<1, 32, 0, stream>>>(state, status, spin_cap, out);
+        uint32_t st = 0;
+        if (cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess &&
+            cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost) == cudaSuccess)
+            r = (st & kStTimeout) ? WT_ETIMEOUT : WT_OK;
+    }
+    cudaFree(mem);
+    return r;
+}

@@ -324,3 +324,22 @@ def test_full_size_workloads_sampled(name):
         _check_mixed(t, q["mixed_kind"], q["mixed_c"], q["mixed_arg"], o1)
     assert t.status_sync() == wt.WT_OK
     t.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A look-back whose predecessor never publishes gives up after its poll
+    limit, reports WT_ETIMEOUT through the status word, and the GPU keeps
+    working (a build right after it is still exact)."""
+    from paper_2505_03372_gb300.binding import lib
+
+    import time
+
+    t0 = time.perf_counter()
+    assert lib().wt_selftest_lookback_timeout(1 << 16, None) == wt.WT_ETIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    sym = workloads.make_symbols(50000, 96, 1, "zipf", 1.0, seed=1, device="cuda")
+    S = _host(sym, 1)
+    with wt.build(sym, 96) as t:
+        i = np.arange(0, 50000, 7, dtype=np.uint64)
+        assert np.array_equal(_u32(t.access(_dev(i, np.int64))), S[i.astype(np.int64)].astype(np.uint32))
+        assert t.status_sync() == wt.WT_OK
