@@ -88,3 +88,38 @@ def predict_mlp_f32(kn, k, P):
     span = x1 - x0
     off = int(f(f(span) * hh))
     return x0 + min(off, span)
+
+
+def segment_knots_all(samples, total, size, K):
+    """Knots (k0, k1, x0, x1) of every rank k = 1..total, as int64 arrays (as in ``knots``)."""
+    k = np.arange(1, total + 1, dtype=np.int64)
+    m = k // K
+    samples = np.asarray(samples, np.int64)
+    k0 = m * K
+    x0 = samples[m]
+    has_next = (m + 1) * K <= total
+    k1 = np.where(has_next, (m + 1) * K, total + 1)
+    x1 = np.where(has_next, samples[np.minimum(m + 1, samples.size - 1)], size)
+    return k, m, k0, k1, x0, x1
+
+
+def predict_pla_all(k, k0, k1, x0, x1):
+    """``predict_pla`` for arrays of ranks."""
+    return x0 + ((k - k0) * (x1 - x0)) // (k1 - k0)
+
+
+def predict_mlp_f32_all(k, k0, k1, x0, x1, P):
+    """``predict_mlp_f32`` for arrays of ranks (same rounding steps, elementwise)."""
+    f = np.float32
+    P = np.asarray(P, np.float32)
+    u = (f(1) * (k - k0).astype(np.float32)) / (k1 - k0).astype(np.float32)
+    u = u.astype(np.float32)
+    u64 = u.astype(np.float64)
+    y = np.full(u.shape, P[3 * H], np.float32)
+    for j in range(H):
+        a = (np.float64(P[j]) * u64 + np.float64(P[H + j])).astype(np.float32)
+        y = (np.float64(P[2 * H + j]) * np.maximum(a, f(0)).astype(np.float64) + y.astype(np.float64)).astype(np.float32)
+    hh = np.clip((u + y).astype(np.float32), f(0), f(1)).astype(np.float32)
+    span = x1 - x0
+    off = (span.astype(np.float32) * hh).astype(np.float32).astype(np.int64)
+    return x0 + np.minimum(off, span)

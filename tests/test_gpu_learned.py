@@ -82,8 +82,9 @@ def test_learned_select_is_exact(mode, n, sigma, w, dist, s, K):
 
 
 @pytest.mark.parametrize("mode", [wt.LEARN_PLA, wt.LEARN_MLP])
-def test_bounds_cover_every_error_the_cpu_recomputes(mode):
-    n, sigma, K = 150001, 300, 256
+@pytest.mark.parametrize("n,sigma,K", [(150001, 300, 256), (1 << 22, 65536, 4096)])
+def test_bounds_cover_every_error_the_cpu_recomputes(mode, n, sigma, K):
+    """Every stored segment bound covers the error the CPU recomputes at every rank k of every level and bit."""
     sym = workloads.make_symbols(n, sigma, 2, "zipf", 1.2, seed=99, device="cuda")
     S = sym.cpu().numpy().view(np.uint16)
     o2 = oracle.O2Tree(S, sigma, K=K)
@@ -91,26 +92,32 @@ def test_bounds_cover_every_error_the_cpu_recomputes(mode):
         t.train_select(mode, steps=200)
         for l in range(o2.L):
             size, ones = o2.level_size(l), o2.level_ones(l)
+            bits = o2.bits(l)
             P = t.export(wt.EXPORT_MLP, l)
             for b in (0, 1):
                 total = ones if b else size - ones
                 if total == 0:
                     continue
+                pos = np.flatnonzero(bits == b).astype(np.int64)  # pos[k - 1] = select_b(l, k)
+                assert pos.size == total
                 samples = o2.export(oracle.EXPORT_S1 if b else oracle.EXPORT_S0, l)
-                eps = t.export(wt.EXPORT_EPS1 if b else wt.EXPORT_EPS0, l)
+                eps = t.export(wt.EXPORT_EPS1 if b else wt.EXPORT_EPS0, l).astype(np.int64)
                 assert eps.size == total // K + 1
-                stride = max(1, total // 3000)
-                for k in range(1, total + 1, stride):
-                    pos = o2.select_b(l, b, k)
-                    m = k // K
-                    kn = omlp.knots(samples, total, size, m, K)
-                    if mode == wt.LEARN_PLA:
-                        pred = omlp.predict_pla(kn, k)
-                        slack = 0
-                    else:
-                        pred = omlp.predict_mlp_f32(kn, k, P[b * 97:(b + 1) * 97])
-                        slack = 2  # FP32 emulation on the CPU may round one step differently
-                    assert abs(pred - pos) <= int(eps[m]) + slack, (l, b, k, pred, pos, int(eps[m]))
+                k, m, k0, k1, x0, x1 = omlp.segment_knots_all(samples, total, size, K)
+                if mode == wt.LEARN_PLA:
+                    pred = omlp.predict_pla_all(k, k0, k1, x0, x1)
+                    slack = 0
+                else:
+                    pred = omlp.predict_mlp_f32_all(k, k0, k1, x0, x1, P[b * 97:(b + 1) * 97])
+                    slack = 2  # the CPU emulates FP32 fma as an FP64 product-sum rounded once to FP32
+                err = np.abs(pred - pos)
+                bad = np.flatnonzero(err > eps[m] + slack)
+                assert bad.size == 0, (l, b, int(k[bad[0]]), int(pred[bad[0]]), int(pos[bad[0]]), int(eps[m[bad[0]]]))
+                # the bound is tight for PLA: some rank of every segment attains it
+                if mode == wt.LEARN_PLA:
+                    worst = np.zeros(eps.size, np.int64)
+                    np.maximum.at(worst, m, err)
+                    assert np.array_equal(worst, eps), (l, b)
 
 
 def test_training_reduces_the_fitted_error():

@@ -341,3 +341,21 @@ def test_pla_predictor_hits_its_knots():
         assert mlp.predict_pla(kn, kn[0]) == kn[2]
         if m < 3:
             assert mlp.predict_pla(kn, kn[1]) == kn[3]
+
+
+def test_vectorised_predictors_equal_the_scalar_ones():
+    """The array forms used for all-rank bound checks give the scalar forms' values."""
+    from oracle import mlp
+
+    rng = np.random.default_rng(5)
+    K, total, size = 256, 256 * 7 + 40, 5000
+    samples = np.concatenate([[0], np.sort(rng.choice(np.arange(1, size), 7, replace=False))]).astype(np.uint64)
+    k, m, k0, k1, x0, x1 = mlp.segment_knots_all(samples, total, size, K)
+    P = (0.3 * rng.normal(size=mlp.NPARAM)).astype(np.float32)
+    pla = mlp.predict_pla_all(k, k0, k1, x0, x1)
+    net = mlp.predict_mlp_f32_all(k, k0, k1, x0, x1, P)
+    for idx in list(range(0, total, 37)) + [total - 1]:
+        kn = mlp.knots(samples, total, size, int(m[idx]), K)
+        assert (int(k0[idx]), int(k1[idx]), int(x0[idx]), int(x1[idx])) == kn
+        assert int(pla[idx]) == mlp.predict_pla(kn, int(k[idx]))
+        assert int(net[idx]) == mlp.predict_mlp_f32(kn, int(k[idx]), P)
