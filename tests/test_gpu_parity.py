@@ -284,7 +284,9 @@ def test_repeated_builds_and_profile_counts():
             t.access(torch.zeros(10, dtype=torch.int64, device="cuda"))
     rep = wt.profile_report()
     assert rep["access"]["launches"] == 3
-    assert rep["level_pass_u8"]["launches"] == 3 * 7
+    assert rep["transpose"]["launches"] == 3
+    assert rep["rank_pass"]["launches"] == 3 * 7
+    assert rep["move_pass"]["launches"] == 3 * 6
     assert wt.profile_launches() >= 3 * 8
 
 
