@@ -322,7 +322,7 @@ def run_ours(args):
             ms = kern[kind]["ms"] / kern[kind]["launches"]
             phases[f"{kind}_ms"] = ms
             phases[f"{kind}_Mqps"] = q[qk].numel() / (ms * 1e-3) / 1e6
-    lp_kernels = [k for k in ("transpose", "rank_pass", "move_pass") if k in kern]
+    lp_kernels = [k for k in ("transpose", "count_scan", "level") if k in kern]
     lp_ms = sum(kern[k]["ms"] for k in lp_kernels)
     lp_name = "level passes (" + " + ".join(lp_kernels) + ")"
     cands = []

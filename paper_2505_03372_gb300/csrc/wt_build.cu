@@ -397,11 +397,11 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         d.ones = t->level_ones[l];
     }
 
-    // ---- level passes over bit planes (wt_level.cu) ----
+    // ---- level kernels over bit planes (wt_level.cu) ----
     if (L && n) {
         const uint64_t ps = plane_stride(n);
         const uint64_t set_words = (uint64_t)(L - 1) * ps;  // planes 1..L-1 of T_0, the most any level has
-        const uint64_t nrank = rank_tiles(n), nmove = move_tiles(n);
+        const uint64_t ntile = level_tiles(n);
         const uint64_t w0 = 2 * lay[0].walloc;               // 32-bit words of B_0
         const uint64_t nchunks = transpose_chunks(w0);
         size_t o = 0;
@@ -412,13 +412,12 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         };
         const size_t o_set0 = take(set_words * 4);
         const size_t o_set1 = take(L > 2 ? set_words * 4 : 0);
-        const size_t o_prefix = take(nmove * 8);
-        const size_t o_first = take(nmove * 4);
-        const size_t o_state = take(nrank * 8);
+        const size_t o_count = take(ntile * 4);
+        const size_t o_prefix = take(ntile * 8);
         const size_t o_la = take(L * sizeof(LevelArgs));
         const size_t o_ta = take(sizeof(TransposeArgs));
-        const size_t o_tp = take((2 * L + 1) * 2 * 8);  // tile prefixes {0, tiles} per pass + transpose
-        const size_t o_cnt = take(2 * L * 8);
+        const size_t o_tp = take((L + 1) * 2 * 8);  // tile prefixes {0, tiles} per level + transpose
+        const size_t o_cnt = take(L * 8);
         void* work = nullptr;
         if (dev_alloc(&work, o, s) != cudaSuccess) {
             dev_free(scratch, s);
@@ -426,14 +425,14 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         }
         uint8_t* Wm = reinterpret_cast<uint8_t*>(work);
         uint32_t* set[2] = {reinterpret_cast<uint32_t*>(Wm + o_set0), reinterpret_cast<uint32_t*>(Wm + o_set1)};
+        uint32_t* count = reinterpret_cast<uint32_t*>(Wm + o_count);
         LevelArgs* d_la = reinterpret_cast<LevelArgs*>(Wm + o_la);
         TransposeArgs* d_ta = reinterpret_cast<TransposeArgs*>(Wm + o_ta);
         uint64_t* d_tp = reinterpret_cast<uint64_t*>(Wm + o_tp);
         unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(Wm + o_cnt);
-        uint64_t* state = reinterpret_cast<uint64_t*>(Wm + o_state);
 
         std::vector<LevelArgs> la(L);
-        std::vector<uint64_t> tp(2 * (2 * L + 1), 0);  // pairs {0, tiles}
+        std::vector<uint64_t> tp(2 * (L + 1), 0);  // pairs {0, tiles}
         for (uint32_t l = 0; l < L; l++) {
             LevelArgs& a = la[l];
             memset(&a, 0, sizeof(a));
@@ -445,7 +444,6 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.pstride = ps;
             a.size = t->level_size[l];
             a.size_next = last ? 0 : t->level_size[l + 1];
-            a.out0_words = last ? 0 : 2 * lay[l + 1].walloc;
             a.l1 = reinterpret_cast<uint64_t*>(M + lay[l].l1);
             a.l2 = reinterpret_cast<uint16_t*>(M + lay[l].l2);
             a.s0 = reinterpret_cast<uint64_t*>(M + lay[l].s0);
@@ -454,16 +452,15 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.n_s1 = (t->level_ones[l] >> k_log2) + 1;
             a.nodes = nodes + ((1ull << l) - 1);
             a.nnodes = internal_nodes(cp, l);
+            a.count = count;
             a.prefix = reinterpret_cast<uint64_t*>(Wm + o_prefix);
-            a.first_node = reinterpret_cast<uint32_t*>(Wm + o_first);
-            a.state = state;
+            a.next_count = count;
             a.status = t->desc.status;
             a.R = L - l;
             a.k_log2 = k_log2;
-            tp[2 * (2 * l) + 1] = rank_tiles(a.size);
-            tp[2 * (2 * l + 1) + 1] = (last || a.size_next == 0) ? 0 : move_tiles(a.size);
+            tp[2 * l + 1] = level_tiles(a.size);
         }
-        tp[2 * (2 * L) + 1] = nchunks;
+        tp[2 * L + 1] = nchunks;
         TransposeArgs ta;
         memset(&ta, 0, sizeof(ta));
         ta.sym = d_symbols;
@@ -472,20 +469,24 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         ta.bits0_words = w0;
         ta.planes = set[0];
         ta.pstride = ps;
+        ta.count = count;
         ta.sigma = sigma;
         ta.L = L;
         ta.pow2 = cp.pow2;
         WT_CUDA_TRY(cudaMemcpyAsync(d_la, la.data(), L * sizeof(LevelArgs), cudaMemcpyHostToDevice, s));
         WT_CUDA_TRY(cudaMemcpyAsync(d_ta, &ta, sizeof(ta), cudaMemcpyHostToDevice, s));
         WT_CUDA_TRY(cudaMemcpyAsync(d_tp, tp.data(), tp.size() * 8, cudaMemcpyHostToDevice, s));
-        WT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 2 * L * 8, s));
-        wt_status st = launch_transpose(d_ta, d_tp + 2 * (2 * L), 1, nchunks, w, s);
+        WT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, L * 8, s));
+        // outputs are ORed into where two runs share a word: they start at zero
+        WT_CUDA_TRY(cudaMemsetAsync(t->lvl_mem, 0, t->lvl_bytes, s));
+        if (L > 2) WT_CUDA_TRY(cudaMemsetAsync(set[1], 0, set_words * 4, s));
+        WT_CUDA_TRY(cudaMemsetAsync(count, 0, ntile * 4, s));
+        wt_status st = launch_transpose(d_ta, d_tp + 2 * L, 1, nchunks, w, s);
         for (uint32_t l = 0; l < L && st == WT_OK; l++) {
             if (t->level_size[l] == 0) continue;
-            const uint64_t nr = tp[2 * (2 * l) + 1], nm = tp[2 * (2 * l + 1) + 1];
-            if (cudaMemsetAsync(state, 0, nr * 8, s) != cudaSuccess) st = WT_ECUDA;
-            if (st == WT_OK) st = launch_rank_pass(d_la + l, d_tp + 2 * (2 * l), 1, d_cnt + 2 * l, nr, s);
-            if (st == WT_OK && nm) st = launch_move_pass(d_la + l, d_tp + 2 * (2 * l + 1), 1, d_cnt + 2 * l + 1, nm, s);
+            st = launch_count_scan(d_la + l, 1, s);
+            if (st == WT_OK && l + 1 < L && cudaMemsetAsync(count, 0, ntile * 4, s) != cudaSuccess) st = WT_ECUDA;
+            if (st == WT_OK) st = launch_level(d_la + l, d_tp + 2 * l, 1, d_cnt + l, tp[2 * l + 1], s);
         }
         dev_free(work, s);
         if (st != WT_OK) {
@@ -608,7 +609,7 @@ __global__ void batch_node_finish_kernel(const BatchTreeInfo* __restrict__ info,
 }
 
 // one thread per (tree, level): level sizes and ones into the tree descriptors
-// and the level arguments; rank and move tiles per level
+// and the level arguments; tiles per level
 __global__ void batch_meta_kernel(const BatchTreeInfo* __restrict__ info, TreeDesc* __restrict__ desc,
                                   LevelArgs* __restrict__ la, uint64_t* __restrict__ tiles, uint32_t ntrees,
                                   uint32_t maxL, uint32_t kl) {
@@ -617,10 +618,8 @@ __global__ void batch_meta_kernel(const BatchTreeInfo* __restrict__ info, TreeDe
     const uint32_t tr = (uint32_t)(g % ntrees), l = (uint32_t)(g / ntrees);
     const BatchTreeInfo& ti = info[tr];
     uint64_t* rt = tiles + (uint64_t)l * ntrees + tr;
-    uint64_t* mt = tiles + ((uint64_t)maxL + l) * ntrees + tr;
     if (l >= ti.L || ti.n == 0) {
         *rt = 0;
-        *mt = 0;
         if (l < ti.L) {
             desc[tr].lv[l].size = 0;
             desc[tr].lv[l].ones = 0;
@@ -637,8 +636,7 @@ __global__ void batch_meta_kernel(const BatchTreeInfo* __restrict__ info, TreeDe
     a.size_next = (l + 1 < ti.L) ? ti.C[ti.s0[l + 1]] : 0;
     a.n_s0 = (zeros >> kl) + 1;
     a.n_s1 = (ones >> kl) + 1;
-    *rt = rank_tiles(size);
-    *mt = (l + 1 < ti.L && a.size_next > 0) ? move_tiles(size) : 0;
+    *rt = level_tiles(size);
 }
 
 // one CTA per level: exclusive scan of the trees' tile counts
@@ -659,7 +657,10 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
     uint32_t nk = 0;
     WT_CUDA_TRY(cudaMemsetAsync(b.hist_pool, 0, b.hist_bytes, s));
     WT_CUDA_TRY(cudaMemsetAsync(b.status_pool, 0, (size_t)b.ntrees * 4, s));
-    WT_CUDA_TRY(cudaMemsetAsync(b.counters, 0, (size_t)2 * b.maxL * 8, s));
+    WT_CUDA_TRY(cudaMemsetAsync(b.counters, 0, (size_t)(b.maxL ? b.maxL : 1) * 8, s));
+    // level outputs are ORed into where two runs share a word: they start at zero
+    WT_CUDA_TRY(cudaMemsetAsync(b.words_pool, 0, b.words_bytes, s));
+    WT_CUDA_TRY(cudaMemsetAsync(b.count_pool, 0, b.count_bytes, s));
     if (b.total_chunks) {
         nk++;
         if (b.w == 1) batch_hist_kernel<uint8_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
@@ -681,7 +682,7 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
         nk += 2;
         batch_meta_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(b.info, b.desc, b.la, b.tiles, b.ntrees, b.maxL,
                                                                        b.k_log2);
-        batch_tile_scan_kernel<<<2 * b.maxL, kScanThreads, 0, s>>>(b.tiles, b.tile_prefix, b.ntrees);
+        batch_tile_scan_kernel<<<b.maxL, kScanThreads, 0, s>>>(b.tiles, b.tile_prefix, b.ntrees);
     }
     WT_CUDA_TRY(cudaGetLastError());
     if (b.maxL && b.total_tr_chunks) {
@@ -689,18 +690,13 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
         nk++;
     }
     for (uint32_t l = 0; l < b.maxL; l++) {
-        WT_CUDA_TRY(cudaMemsetAsync(b.state_pool, 0, b.state_bytes, s));
         const LevelArgs* la = b.la + (uint64_t)l * b.ntrees;
-        if (launch_rank_pass(la, b.tile_prefix + (uint64_t)l * (b.ntrees + 1), b.ntrees, b.counters + 2 * l,
-                             b.max_rank_tiles, s) != WT_OK)
+        if (launch_count_scan(la, b.ntrees, s) != WT_OK) return WT_ECUDA;
+        WT_CUDA_TRY(cudaMemsetAsync(b.count_pool, 0, b.count_bytes, s));
+        if (launch_level(la, b.tile_prefix + (uint64_t)l * (b.ntrees + 1), b.ntrees, b.counters + l, b.max_tiles, s) !=
+            WT_OK)
             return WT_ECUDA;
-        nk++;
-        if (l + 1 < b.maxL) {
-            if (launch_move_pass(la, b.tile_prefix + ((uint64_t)b.maxL + l) * (b.ntrees + 1), b.ntrees,
-                                 b.counters + 2 * l + 1, b.max_move_tiles, s) != WT_OK)
-                return WT_ECUDA;
-            nk++;
-        }
+        nk += 2;
     }
     if (kernels) *kernels = nk;
     return WT_OK;

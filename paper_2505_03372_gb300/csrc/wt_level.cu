@@ -18,17 +18,18 @@
 // reads R bits and writes R - 1 bits per element, and 32 elements move per
 // instruction.
 //
-// Per level:
-//  * rank pass (B_l only; tiles of 65,536 bits = one L1 block): popcounts, a
-//    decoupled look-back for the ones before the tile, the L1/L2 counters
-//    (Section 4.1) and select samples (Section 4.2), the ones before every
-//    move tile and its first node, and a zero in every output word that two
-//    runs share (the move pass ORs into those and stores all others);
-//  * move pass (tiles of 16,384 elements, independent of each other):
-//    planes 1..R-1 of T_l -> B_{l+1} and planes 1..R-2 of T_{l+1}.
-// Level 0's planes come from S by a 32x32 bit-matrix transpose of the codes.
-// Every kernel walks the work items of one or many trees (a batch), so a
-// single tree is a batch of one.
+// Per level one kernel walks tiles of 16,384 positions.  A tile reads B_l's
+// words, writes the level's L1/L2 counters (Section 4.1) and select samples
+// (Section 4.2) from the ones before it (an exclusive scan of per-tile counts),
+// and moves planes 1..R-1.  Output words covered by one run are stored;
+// words shared by two runs are ORed into, so the output planes must start at
+// zero: each kernel clears the input planes it consumes, and those buffers hold
+// the next level's output.  While it writes B_{l+1} the kernel counts its ones
+// per tile of level l+1; a scan of those counts gives the next level's prefixes.
+// Tiles are independent of each other: no look-back, no waiting on other CTAs.
+// Level 0's planes come from S by a transpose of the codes.  Every kernel walks
+// the work items of one or many trees (a batch), so a single tree is a batch
+// of one.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,18 +38,20 @@
 
 namespace wt {
 
-constexpr uint32_t kRankThreads = 512;  // four 32-bit words per thread
-constexpr uint32_t kRankWords = kRankTile / 32;
-constexpr uint32_t kMoveThreads = 512;  // one 32-bit word of every plane per thread
-constexpr uint32_t kMoveWords = kMoveTile / 32;
-constexpr uint32_t kMovesPerRank = kRankTile / kMoveTile;
+static_assert(sizeof(LevelArgs) % 8 == 0, "level arguments are copied as 64-bit words");
+
+constexpr uint32_t kTileThreads = 512;  // one 32-bit word of every plane per thread
+constexpr uint32_t kTileWords = kTile / 32;
+constexpr uint32_t kTilesPerL1 = kL1Bits / kTile;
+constexpr uint32_t kScanPerThread = 8;
 constexpr uint32_t kSlots = 8;          // plane ring of the move pass
-constexpr uint32_t kImgWords = 520;     // one run image: 512 words + read-ahead
+constexpr uint32_t kImgWords = 520;     // one run image: 512 words + alignment and read-ahead
+constexpr uint32_t kSets = 4;           // run-image sets in rotation
 constexpr uint32_t kTrThreads = 256;    // transpose: 32 symbols per thread
 constexpr uint32_t kTrTable = 1024;     // codes tabulated in shared memory up to this sigma
 
 uint64_t transpose_chunks(uint64_t words32) { return (words32 + kTrThreads - 1) / kTrThreads; }
-uint64_t plane_stride(uint64_t n) { return (n + kMoveTile - 1) / kMoveTile * kMoveWords; }
+uint64_t plane_stride(uint64_t n) { return level_tiles(n) * kTileWords; }
 
 // Internal nodes (two or more symbols) of level l.  In prefix order they come
 // first: a prefix whose node is a leaf or absent belongs to a code that ended
@@ -89,32 +92,33 @@ __device__ __forceinline__ void transpose32(uint32_t (&A)[32]) {
     tr_stage<1, 0x55555555u>(A);
 }
 
-// Shift masks of compress(., m): stage i moves the selected bits right by 2^i.
-// A bit of m moves right by the number of zeros of m below it; stage i takes
-// the bits whose remaining distance has bit i set, found as the parity of the
-// zeros below them (a prefix XOR).
+// Shift masks of compress_left(., m): stage i moves the selected bits left by
+// 2^i.  A bit of m moves left by the number of zeros of m above it; stage i
+// takes the bits whose remaining distance has bit i set, found as the parity
+// of the zeros above them (a suffix XOR).  Moving bits never land on occupied
+// positions, so the move is an add: m + v * (2^(2^i) - 1).
 __device__ __forceinline__ void compress_masks(uint32_t m, uint32_t (&mv)[5]) {
-    uint32_t mk = ~m << 1;  // zeros of m, seen from the bit above
+    uint32_t mk = ~m >> 1;  // zeros of m, seen from the bit below
 #pragma unroll
     for (int i = 0; i < 5; i++) {
-        uint32_t mp = mk ^ (mk << 1);  // prefix XOR: parity of the marked bits at or below
-        mp ^= mp << 2;
-        mp ^= mp << 4;
-        mp ^= mp << 8;
-        mp ^= mp << 16;
+        uint32_t mp = mk ^ (mk >> 1);  // suffix XOR: parity of the marked bits at or above
+        mp ^= mp >> 2;
+        mp ^= mp >> 4;
+        mp ^= mp >> 8;
+        mp ^= mp >> 16;
         const uint32_t v = mp & m;
         mv[i] = v;
-        m = (m ^ v) | (v >> (1 << i));
+        m += v * ((1u << (1 << i)) - 1u);
         mk &= ~mp;
     }
 }
-// The bits of x under m, packed towards bit 0 in order.
-__device__ __forceinline__ uint32_t compress(uint32_t x, uint32_t m, const uint32_t (&mv)[5]) {
-    x &= m;
+// The bits of x under m (x already masked by m), packed towards bit 31 in
+// order: one AND and one multiply-add per stage.
+__device__ __forceinline__ uint32_t compress_left(uint32_t x, const uint32_t (&mv)[5]) {
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         const uint32_t t = x & mv[i];
-        x = (x ^ t) | (t >> (1 << i));
+        x += t * ((1u << (1 << i)) - 1u);
     }
     return x;
 }
@@ -140,40 +144,14 @@ __device__ __forceinline__ uint64_t warp_find_node(const NodeEntry* nodes, uint6
 // level 0: symbols -> bit planes
 // ===========================================================================
 
-// One CTA per 256 words of 32 symbols of one tree.  A thread reads its 32
-// symbols, encodes them, transposes the 32 codes and writes one word of every
-// plane (plane 0 into B_0).  Words of B_0 past n are written as zeros.
+// Encode and transpose the 32 symbols of one word of B_0: plane j gets code bit
+// L-1-j of each.  Returns the ones of B_0's word.
 template <typename T>
-__global__ void __launch_bounds__(kTrThreads) transpose_kernel(const TransposeArgs* __restrict__ args,
-                                                               const uint64_t* __restrict__ chunk_prefix,
-                                                               uint32_t ntrees) {
-    __shared__ uint32_t s_code[kTrTable];
-    __shared__ uint32_t s_tree;
-    if (threadIdx.x == 0) s_tree = ntrees > 1 ? find_tree(chunk_prefix, ntrees, blockIdx.x) : 0u;
-    __syncthreads();
-    const TransposeArgs& a = args[s_tree];
+__device__ __forceinline__ uint32_t transpose_word(const TransposeArgs& a, const CodeParams& cp, bool table,
+                                                   const uint32_t* s_code, uint64_t word) {
     const uint64_t n = a.n;
-    const uint32_t sigma = a.sigma, L = a.L;
-    CodeParams cp;  // encode() reads sigma, L and pow2 only
-    cp.sigma = sigma;
-    cp.L = L;
-    cp.pow2 = a.pow2;
-    const bool table = !cp.pow2 && sigma <= kTrTable;
-    if (table) {
-        for (uint32_t s = threadIdx.x; s < sigma; s += kTrThreads) {
-            uint32_t code, len;
-            encode(cp, s, code, len);
-            s_code[s] = code;
-        }
-        __syncthreads();
-    }
-    const uint64_t word = (blockIdx.x - chunk_prefix[s_tree]) * kTrThreads + threadIdx.x;
-    if (word >= a.bits0_words) return;
+    const uint32_t sigma = cp.sigma, L = cp.L;
     const uint64_t e0 = word * 32;
-    if (e0 >= n) {
-        a.bits0[word] = 0;
-        return;
-    }
     constexpr int EPW = 4 / (int)sizeof(T);  // symbols per 32-bit word
     uint32_t A[32];
     const T* S = reinterpret_cast<const T*>(a.sym) + e0;
@@ -213,275 +191,329 @@ __global__ void __launch_bounds__(kTrThreads) transpose_kernel(const TransposeAr
         }
         A[k] = (uint32_t)k < cnt ? code : 0u;
     }
-    transpose32(A);
+    uint32_t b0 = 0;
+    if (sizeof(T) == 1) {
+        // codes of at most 8 bits: four per word; bit b of the four bytes of a
+        // word gathers into a nibble with one multiply (bits 28..31 of the product)
+        uint32_t P[8];
 #pragma unroll
-    for (int b = 0; b < 32; b++) {
-        if ((uint32_t)b < L) {
-            const uint32_t j = L - 1 - b;  // plane j holds code bit L-1-j
-            if (j == 0) a.bits0[word] = A[b];
-            else a.planes[(uint64_t)(j - 1) * a.pstride + word] = A[b];
+        for (int i = 0; i < 8; i++) P[i] = A[4 * i] | (A[4 * i + 1] << 8) | (A[4 * i + 2] << 16) | (A[4 * i + 3] << 24);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            if ((uint32_t)b < L) {
+                uint32_t acc = 0;
+#pragma unroll
+                for (int i = 0; i < 8; i++) acc += (((P[i] & (0x01010101u << b)) * (0x10204080u >> b)) >> 28) << (4 * i);
+                const uint32_t j = L - 1 - b;  // plane j holds code bit L-1-j
+                if (j == 0) b0 = acc;
+                else a.planes[(uint64_t)(j - 1) * a.pstride + word] = acc;
+            }
+        }
+    } else {
+        transpose32(A);
+#pragma unroll
+        for (int b = 0; b < 32; b++) {
+            if ((uint32_t)b < L) {
+                const uint32_t j = L - 1 - b;
+                if (j == 0) b0 = A[b];
+                else a.planes[(uint64_t)(j - 1) * a.pstride + word] = A[b];
+            }
         }
     }
+    a.bits0[word] = b0;
+    return __popc(b0);
 }
 
-// ===========================================================================
-// rank pass
-// ===========================================================================
-
-// Zero the first and the last word of a run of output bits [d, d + nbits)
-// (clipped at lim) when the run covers them only partly; the move pass ORs
-// into exactly those words.
-__device__ __forceinline__ void zero_run_edges(const LevelArgs& a, uint64_t d, uint64_t nbits) {
-    const uint64_t lim = a.size_next;
-    if (nbits == 0 || d >= lim) return;
-    const uint64_t e = umin64(d + nbits, lim);
-    const uint32_t np = a.R - 2;  // output planes besides B_{l+1}
-    if (d & 31) {
-        const uint64_t w = d >> 5;
-        a.out0[w] = 0;
-        for (uint32_t j = 0; j < np; j++) a.out[j * a.pstride + w] = 0;
-    }
-    if (e & 31) {
-        const uint64_t w = (e - 1) >> 5;
-        a.out0[w] = 0;
-        for (uint32_t j = 0; j < np; j++) a.out[j * a.pstride + w] = 0;
-    }
-}
-
-__global__ void __launch_bounds__(kRankThreads) rank_pass_kernel(const LevelArgs* __restrict__ args,
-                                                                 const uint64_t* __restrict__ tile_prefix,
-                                                                 uint32_t ntrees, unsigned long long* __restrict__ counter) {
-    __shared__ uint32_t s_b[kRankWords];    // B_l words of the tile
-    __shared__ uint32_t s_pre[kRankWords];  // ones before each word within the tile
-    __shared__ uint32_t s_wsum[kRankThreads / 32];
-    __shared__ uint64_t s_g, s_E;
+// One CTA per 256 words of 32 symbols of one tree; words of B_0 past n are
+// written as zeros.  The CTA's words lie in one tile, whose count of ones it
+// adds to.
+template <typename T>
+__global__ void __launch_bounds__(kTrThreads) transpose_kernel(const TransposeArgs* __restrict__ args,
+                                                               const uint64_t* __restrict__ chunk_prefix,
+                                                               uint32_t ntrees) {
+    __shared__ uint32_t s_code[kTrTable];
     __shared__ uint32_t s_tree;
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t total = tile_prefix[ntrees];
-    for (;;) {
-        if (tid == 0) {
-            const uint64_t g = atomicAdd(counter, 1ull);
-            s_g = g;
-            if (g < total) s_tree = ntrees > 1 ? find_tree(tile_prefix, ntrees, g) : 0u;
+    __shared__ uint32_t s_ones;
+    if (threadIdx.x == 0) {
+        s_tree = ntrees > 1 ? find_tree(chunk_prefix, ntrees, blockIdx.x) : 0u;
+        s_ones = 0;
+    }
+    __syncthreads();
+    const TransposeArgs& a = args[s_tree];
+    CodeParams cp;  // encode() reads sigma, L and pow2 only
+    cp.sigma = a.sigma;
+    cp.L = a.L;
+    cp.pow2 = a.pow2;
+    const bool table = !cp.pow2 && cp.sigma <= kTrTable;
+    if (table) {
+        for (uint32_t s = threadIdx.x; s < cp.sigma; s += kTrThreads) {
+            uint32_t code, len;
+            encode(cp, s, code, len);
+            s_code[s] = code;
         }
-        __syncthreads();
-        const uint64_t g = s_g;
-        if (g >= total) break;
-        const LevelArgs& a = args[s_tree];
-        const uint64_t tile = g - tile_prefix[s_tree];
-        const uint64_t size = a.size;
-        const uint64_t t0 = tile * kRankTile;
-        const uint32_t count = (uint32_t)umin64(kRankTile, size - t0);
-        const uint32_t nw = (count + 31) / 32;
-
-        // ---- words, popcounts, prefix within the tile ----
-        const uint32_t w0 = tid * 4;
-        uint32_t w[4];
-        const uint32_t* src = a.bits + (t0 >> 5) + w0;
-        if (w0 + 4 <= nw) {
-            const uint4 q = *reinterpret_cast<const uint4*>(src);
-            w[0] = q.x;
-            w[1] = q.y;
-            w[2] = q.z;
-            w[3] = q.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                w[k] = 0u;
-                if (w0 + k < nw) w[k] = src[k];
-            }
-        }
-        if (count & 31) {
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (w0 + k == nw - 1) w[k] &= (1u << (count & 31)) - 1u;
-        }
-        const uint32_t c = __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
-        uint32_t inc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= (uint32_t)o) inc += t;
-        }
-        if (lane == 31) s_wsum[warp] = inc;
-        __syncthreads();
-        uint32_t before = 0, ones = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < kRankThreads / 32; i++) {
-            const uint32_t v = s_wsum[i];
-            before += i < warp ? v : 0u;
-            ones += v;
-        }
-        const uint32_t pre = before + inc - c;  // ones before this thread's first word
-        {
-            uint32_t p = pre;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                s_b[w0 + k] = w[k];
-                s_pre[w0 + k] = p;
-                p += __popc(w[k]);
-            }
-        }
-        if (warp == 0) {
-            const uint64_t E = lookback_warp(a.state, tile, ones, a.status, kSpinCap);
-            if (lane == 0) s_E = E;
-        }
-        __syncthreads();
-        const uint64_t E = s_E;  // ones of B_l before the tile
-
-        // ---- L1 / L2 counters (the tile is one L1 block) ----
-        if (tid == 0) a.l1[t0 >> 16] = E;
-        if ((tid & 3) == 0 && w0 < nw) a.l2[(t0 >> 9) + tid / 4] = (uint16_t)pre;
-        if (tid == 0 && t0 + count == size && (size & 511) == 0) {
-            if ((size & 65535) == 0) {
-                a.l1[size >> 16] = E + ones;
-                a.l2[size >> 9] = 0;
-            } else {
-                a.l2[size >> 9] = (uint16_t)ones;
-            }
-        }
-        // ---- select samples: at most one of each kind per word (K >= 256) ----
-        if (tid == 0 && tile == 0) {
-            a.s0[0] = 0;
-            a.s1[0] = 0;
-        }
-        {
-            const uint32_t kl = a.k_log2;
-            uint32_t p = pre;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t wi = w0 + k;
-                if (wi < nw) {
-                    const uint32_t x = w[k];
-                    const uint32_t valid = (wi == nw - 1 && (count & 31)) ? (1u << (count & 31)) - 1u : 0xffffffffu;
-                    const uint32_t z = ~x & valid;
-                    const uint32_t c1 = __popc(x), c0 = __popc(z);
-                    const uint64_t g1 = E + p;                       // ones before the word
-                    const uint64_t g0 = (t0 - E) + 32ull * wi - p;   // zeros before the word
-                    const uint64_t base = t0 + 32ull * wi;
-                    if (((g1 + c1) >> kl) != (g1 >> kl)) {
-                        const uint64_t m = (g1 + c1) >> kl;
-                        if (m < a.n_s1) a.s1[m] = base + select_in_word(x, (uint32_t)((m << kl) - g1));
-                    }
-                    if (((g0 + c0) >> kl) != (g0 >> kl)) {
-                        const uint64_t m = (g0 + c0) >> kl;
-                        if (m < a.n_s0) a.s0[m] = base + select_in_word(z, (uint32_t)((m << kl) - g0));
-                    }
-                    p += c1;
-                }
-            }
-        }
-
-        // ---- move tiles: ones before each, its first node, shared output words ----
-        if (a.out0 != nullptr && warp < kMovesPerRank) {
-            const uint64_t m0 = t0 + (uint64_t)warp * kMoveTile;
-            if (m0 < size) {
-                const uint64_t mt = tile * kMovesPerRank + warp;
-                const uint64_t mend = umin64(m0 + kMoveTile, size);
-                const uint64_t Pm = E + s_pre[warp * kMoveWords];  // ones before the move tile
-                const uint64_t p0 = a.nnodes > 1 ? warp_find_node(a.nodes, a.nnodes, m0) : 0;
-                if (lane == 0) {
-                    a.prefix[mt] = Pm;
-                    a.first_node[mt] = (uint32_t)p0;
-                }
-                if (a.size_next > 0) {
-                    // ones before position t0 + r of this rank tile, 0 <= r <= count
-                    auto ones_before = [&](uint32_t r) -> uint32_t {
-                        const uint32_t wi = r >> 5;
-                        if (wi >= nw) return ones;
-                        return s_pre[wi] + __popc(s_b[wi] & ((1u << (r & 31)) - 1u));
-                    };
-                    for (uint64_t pb = p0;; pb += 32) {
-                        const uint64_t p = pb + lane;
-                        bool inside = false;
-                        if (p < a.nnodes) {
-                            const NodeEntry ne = a.nodes[p];
-                            const uint64_t st = ne.start;
-                            const uint64_t en = p + 1 < a.nnodes ? __ldg(&a.nodes[p + 1].start) : size;
-                            inside = st < mend;
-                            const uint64_t q0 = umax64(st, m0), q1 = umin64(en, mend);
-                            if (inside && q0 < q1) {
-                                const uint32_t ob0 = ones_before((uint32_t)(q0 - t0));
-                                const uint32_t ob1 = ones_before((uint32_t)(q1 - t0));
-                                const uint64_t r1 = E + ob0, r0 = q0 - r1;
-                                zero_run_edges(a, ne.off0 + r0, (q1 - q0) - (ob1 - ob0));
-                                zero_run_edges(a, ne.off1 + r1, ob1 - ob0);
-                            }
-                        }
-                        if (!__shfl_sync(0xffffffffu, inside, 31)) break;
-                    }
-                }
-            }
-        }
-        // ---- B_{l+1} past size_{l+1} stays zero ----
-        if (a.out0 != nullptr && t0 + count == size)
-            for (uint64_t i = ((a.size_next + 31) >> 5) + tid; i < a.out0_words; i += kRankThreads) a.out0[i] = 0;
         __syncthreads();
     }
+    const uint64_t word = (blockIdx.x - chunk_prefix[s_tree]) * kTrThreads + threadIdx.x;
+    uint32_t ones = 0;
+    if (word < a.bits0_words) {
+        if (word * 32 < a.n) ones = transpose_word<T>(a, cp, table, s_code, word);
+        else a.bits0[word] = 0;
+    }
+    const uint32_t ws = __reduce_add_sync(0xffffffffu, ones);
+    if ((threadIdx.x & 31) == 0 && ws) atomicAdd(&s_ones, ws);
+    __syncthreads();
+    const uint64_t w0 = (blockIdx.x - chunk_prefix[s_tree]) * kTrThreads;
+    if (threadIdx.x == 0 && s_ones) atomicAdd(a.count + (w0 / kTileWords), s_ones);
 }
 
 // ===========================================================================
-// move pass
+// the level kernel
 // ===========================================================================
 
-struct MoveSmem {
-    uint32_t ring[kSlots][kMoveWords];  // planes in flight
-    uint32_t img[3][2][kImgWords];      // zero-run / one-run images, three sets in rotation
-    uint32_t b[kMoveWords];             // B_l words of the tile
-    uint32_t pre[kMoveWords];           // ones before each word within the tile
-    uint64_t mbar[kSlots];
-    uint32_t wsum[kMoveThreads / 32];
+// Single-node tiles: write-out plan of one run (image aligned with its output
+// words: image word wb + i holds output word k0 + i, wb = k0 mod 4).
+struct RunPlan {
+    uint64_t k0;       // first output word
+    uint32_t nw;       // output words (0: nothing to write)
+    uint32_t wb;       // image word of output word 0
+    uint32_t ta, tb;   // output words [ta, tb) leave by one bulk copy
+    uint32_t fmask;    // bits of the first word inside the run
+    uint32_t lmask;    // bits of the last word inside the run
+    uint64_t tile;     // tile of level l+1 holding the run's first bit
 };
 
-// Append a compressed piece of cnt bits at bit offset off of a run image.
-__device__ __forceinline__ void place(uint32_t* img, uint32_t off, uint32_t cnt, uint32_t v) {
+struct TileSmem {
+    uint32_t ring[kSlots][kTileWords];  // planes in flight
+    uint32_t img[kSets][2][kImgWords];  // zero-run / one-run images, in rotation
+    uint32_t zero[kTileWords];          // zeros: source of the bulk clears of consumed planes
+    uint32_t b[kTileWords];             // B_l words of the tile
+    uint32_t pre[kTileWords];           // ones before each word within the tile
+    LevelArgs args;                     // the current tree's level arguments
+    RunPlan run[2];                     // single-node tiles: zero run, one run
+    uint64_t mbar[kSlots];
+    uint64_t p0;                        // node of the tile's first element
+    uint64_t t0, E;                     // tile start, ones of B_l before it
+    uint32_t count, O;                  // tile elements, ones
+    uint32_t ones[4];                   // ones of B_{l+1} per (run, side of a tile boundary)
+    uint32_t wsum[kTileThreads / 32];
+};
+
+// Append a compressed piece (cnt bits at the top of vl) at image bit off.
+__device__ __forceinline__ void place(uint32_t* img, uint32_t off, uint32_t cnt, uint32_t vl) {
     if (cnt == 0) return;
+    const uint32_t v = vl >> (32 - cnt);
     const uint32_t wi = off >> 5, sh = off & 31;
     atomicOr(img + wi, v << sh);
-    if (sh + cnt > 32) atomicOr(img + wi + 1, v >> (32 - sh));
+    if (sh + cnt > 32) atomicOr(img + wi + 1, __funnelshift_l(v, 0u, sh));
 }
 
-// Output word k of a run [d, e) whose bits come from an image starting at
-// image bit a0: a store when the run covers the word, an OR otherwise.
-__device__ __forceinline__ void copy_word(uint32_t* dst, uint64_t k, uint64_t d, uint64_t e, const uint32_t* img,
-                                          uint32_t a0) {
-    const uint64_t gb = k << 5;
-    const uint32_t lo = gb < d ? (uint32_t)(d - gb) : 0u;
-    const uint32_t hi = gb + 32 > e ? (uint32_t)(e - gb) : 32u;
-    const int64_t sp = (int64_t)a0 + (int64_t)(gb - d);  // image bit of output bit gb (>= -31)
-    const int32_t wi = (int32_t)(sp >> 5);
-    const uint32_t sh = (uint32_t)sp & 31u;
-    const uint32_t lw = wi >= 0 ? img[wi] : 0u;
-    const uint32_t v = __funnelshift_r(lw, img[wi + 1], sh);
-    if (lo == 0 && hi == 32) {
-        dst[k] = v;
+// Ones of run bits [x0, x1) inside a piece of c bits (right-aligned in v) at run bit pre.
+__device__ __forceinline__ uint32_t ones_in(uint32_t v, uint32_t pre, uint32_t c, uint32_t x0, uint32_t x1) {
+    const uint32_t lo = x0 > pre ? x0 - pre : 0u;
+    const uint32_t hi = x1 > pre ? umin64(x1 - pre, c) : 0u;
+    if (hi <= lo) return 0;
+    const uint32_t m = (hi >= 32 ? 0xffffffffu : (1u << hi) - 1u) & ~((1u << lo) - 1u);
+    return __popc(v & m);
+}
+
+// Add ones to the tiles of the next level: one atomic per distinct tile of a warp.
+__device__ __forceinline__ void count_key(uint32_t* next_count, bool active, uint64_t key, uint32_t ones) {
+    const uint64_t k = active ? key : ~0ull;
+    const uint32_t grp = __match_any_sync(0xffffffffu, k);
+    const uint32_t sum = __reduce_add_sync(grp, active ? ones : 0u);
+    if (active && sum && (threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1)) atomicAdd(next_count + key, sum);
+}
+
+// A run of output bits [d, e) (multi-node tiles): shifted out of an image whose
+// run bit 0 sits at image bit pos0.
+struct Run {
+    uint64_t k0;       // first output word
+    uint32_t nw;       // output words (0: nothing to write)
+    uint32_t wb;       // image word of output word 0's window
+    uint32_t sh;       // bit offset of the window in the image words
+    uint32_t fmask;    // bits of the first word inside the run
+    uint32_t lmask;    // bits of the last word inside the run
+};
+__device__ __forceinline__ Run make_run(uint64_t d, uint64_t n, uint64_t lim, uint32_t pos0) {
+    Run r;
+    r.nw = 0;
+    r.k0 = 0;
+    r.wb = r.sh = 0;
+    r.fmask = r.lmask = 0;
+    if (n == 0 || d >= lim) return r;
+    const uint64_t e = umin64(d + n, lim);
+    const uint32_t s = (uint32_t)d & 31u;
+    r.k0 = d >> 5;
+    r.nw = (uint32_t)(((e - 1) >> 5) - r.k0 + 1);
+    const uint32_t p = pos0 - s;  // image position of output word 0's bit 0
+    r.wb = p >> 5;
+    r.sh = p & 31u;
+    r.fmask = ~((1u << s) - 1u);
+    r.lmask = (e & 31) ? (1u << (e & 31)) - 1u : 0xffffffffu;
+    if (r.nw == 1) r.fmask &= r.lmask;
+    return r;
+}
+// Output word i of a run: a store when the run covers the word, an OR into a
+// zero-initialised word shared with another run otherwise.  Returns its ones.
+__device__ __forceinline__ uint32_t run_word(const Run& r, uint32_t i, const uint32_t* img, uint32_t* plane) {
+    uint32_t v = r.sh ? __funnelshift_r(img[r.wb + i], img[r.wb + i + 1], r.sh) : img[r.wb + i];
+    const uint32_t mask = i == 0 ? r.fmask : (i + 1 == r.nw ? r.lmask : 0xffffffffu);
+    if (mask == 0xffffffffu) {
+        plane[r.k0 + i] = v;
     } else {
-        const uint32_t mask = (hi == 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-        atomicOr(dst + k, v & mask);
+        v &= mask;
+        atomicOr(plane + r.k0 + i, v);
     }
+    return __popc(v);
+}
+// Plan of a single-node run of n bits at output bit d (image bit d mod 128 of its image).
+__device__ __forceinline__ RunPlan plan_run(uint64_t d, uint64_t n, uint64_t lim) {
+    RunPlan p;
+    const Run r = make_run(d, n, lim, (uint32_t)d & 127u);
+    p.k0 = r.k0;
+    p.nw = r.nw;
+    p.wb = r.wb;
+    p.fmask = r.fmask;
+    p.lmask = r.lmask;
+    // whole words [f, l) and their 16-byte aligned part [ta, tb)
+    const uint32_t f = r.fmask == 0xffffffffu ? 0u : 1u;
+    const uint32_t l = (r.nw > 0 && (r.nw == 1 ? r.fmask : r.lmask) != 0xffffffffu) ? r.nw - 1 : r.nw;
+    uint32_t ta = f + ((4u - (uint32_t)((r.k0 + f) & 3)) & 3u);
+    uint32_t tb = l >= 4 ? l - (uint32_t)((r.k0 + l) & 3) : 0u;
+    if (ta > r.nw) ta = r.nw;
+    if (tb < ta) tb = ta;
+    p.ta = ta;
+    p.tb = tb;
+    p.tile = d / kTile;
+    return p;
+}
+// One of the (at most eight) output words around a run's bulk span, or nothing.
+__device__ __forceinline__ void plan_edge_word(const RunPlan& p, uint32_t q, const uint32_t* img, uint32_t* plane) {
+    const uint32_t i = q < p.ta ? q : p.tb + (q - p.ta);
+    if (i >= p.nw) return;
+    uint32_t v = img[p.wb + i];
+    const uint32_t mask = i == 0 ? p.fmask : (i + 1 == p.nw ? p.lmask : 0xffffffffu);
+    if (mask == 0xffffffffu) plane[p.k0 + i] = v;
+    else atomicOr(plane + p.k0 + i, v & mask);
 }
 
-// A run's output words: first word index and count (0 if clipped away).
-__device__ __forceinline__ uint64_t run_words(uint64_t d, uint64_t n, uint64_t lim, uint64_t& k0, uint64_t& e) {
-    if (n == 0 || d >= lim) return 0;
-    e = umin64(d + n, lim);
-    k0 = d >> 5;
-    return ((e - 1) >> 5) - k0 + 1;
+// One plane of a tile: compress this thread's word under the zeros and the
+// ones of B_l into the image set, then (after the barrier) write the runs.
+template <bool FIRST>
+__device__ __forceinline__ void move_plane(TileSmem& S, const LevelArgs& a, uint32_t j, uint32_t u, uint32_t R,
+                                           uint32_t x, uint32_t m0, uint32_t m1, const uint32_t (&mv0)[5],
+                                           const uint32_t (&mv1)[5], uint32_t qz, uint32_t qo, uint32_t c0,
+                                           uint32_t c1, uint32_t pre0, uint32_t pre1, bool single,
+                                           const uint32_t (&thr)[4]) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t set = j & (kSets - 1);
+    const uint32_t cz = compress_left(x & m0, mv0), co = compress_left(x & m1, mv1);
+    place(S.img[set][0], qz, c0, cz);
+    place(S.img[set][1], qo, c1, co);
+    if (FIRST && single) {
+        // ones of B_{l+1}: per run, before and after the tile boundary of level l+1
+        const uint32_t vz = c0 ? cz >> (32 - c0) : 0u, vo = c1 ? co >> (32 - c1) : 0u;
+        // thr: per run, the run bits before the next tile boundary and below size_{l+1}
+        uint32_t n0 = ones_in(vz, pre0, c0, 0, umin64(thr[0], thr[1]));
+        uint32_t n1 = ones_in(vz, pre0, c0, thr[0], thr[1]);
+        uint32_t n2 = ones_in(vo, pre1, c1, 0, umin64(thr[2], thr[3]));
+        uint32_t n3 = ones_in(vo, pre1, c1, thr[2], thr[3]);
+        n0 = __reduce_add_sync(0xffffffffu, n0);
+        n1 = __reduce_add_sync(0xffffffffu, n1);
+        n2 = __reduce_add_sync(0xffffffffu, n2);
+        n3 = __reduce_add_sync(0xffffffffu, n3);
+        if (lane == 0) {
+            if (n0) atomicAdd(&S.ones[0], n0);
+            if (n1) atomicAdd(&S.ones[1], n1);
+            if (n2) atomicAdd(&S.ones[2], n2);
+            if (n3) atomicAdd(&S.ones[3], n3);
+        }
+    }
+    fence_proxy_async();
+    if (tid == 0 || tid == 8) bulk_wait_read<1>();  // images of plane j - 2 have been read
+    if (warp == 0 && j + 1 < R) mbar_wait(&S.mbar[(u + 1) % kSlots], ((u + 1) / kSlots) & 1u, a.status);
+    __syncthreads();
+    if (tid == 0 && j + kSlots < R) {  // refill plane j's slot
+        const uint32_t slot = u % kSlots;
+        const uint32_t nw = (S.count + 31) / 32, bytes = (nw * 4 + 15) & ~15u;
+        mbar_expect_tx(&S.mbar[slot], bytes);
+        bulk_g2s(S.ring[slot], a.in + (uint64_t)(j + kSlots - 1) * a.pstride + (S.t0 >> 5), bytes, &S.mbar[slot]);
+    }
+    uint32_t* plane = j == 1 ? a.out0 : a.out + (uint64_t)(j - 2) * a.pstride;
+    const uint32_t* img0 = S.img[set][0];
+    const uint32_t* img1 = S.img[set][1];
+    if (single) {
+        if (tid < 16) {
+            const RunPlan& p = S.run[tid >> 3];
+            const uint32_t* img = tid < 8 ? img0 : img1;
+            const uint32_t q = tid & 7;
+            if (q == 0 && p.tb > p.ta) bulk_s2g(plane + p.k0 + p.ta, img + p.wb + p.ta, 4 * (p.tb - p.ta));
+            plan_edge_word(p, q, img, plane);
+            if (FIRST && q == 0) {  // this run's ones of B_{l+1}, per tile of level l+1
+                const uint32_t k = (tid >> 3) * 2;
+                if (S.ones[k]) atomicAdd(a.next_count + p.tile, S.ones[k]);
+                if (S.ones[k + 1]) atomicAdd(a.next_count + p.tile + 1, S.ones[k + 1]);
+            }
+        }
+    } else {
+        // one warp per node of the tile
+        const uint64_t t0 = S.t0, E = S.E, lim = a.size_next;
+        const uint32_t count = S.count, O = S.O, nw = (count + 31) / 32;
+        auto ones_before = [&](uint32_t r) -> uint32_t {
+            const uint32_t wi = r >> 5;
+            if (wi >= nw) return O;
+            return S.pre[wi] + __popc(S.b[wi] & ((1u << (r & 31)) - 1u));
+        };
+        for (uint64_t p = S.p0 + warp; p < a.nnodes; p += kTileThreads / 32) {
+            const uint64_t st = __ldg(&a.nodes[p].start);
+            if (st >= t0 + count) break;
+            const uint64_t en = p + 1 < a.nnodes ? __ldg(&a.nodes[p + 1].start) : a.size;
+            const uint32_t q0 = (uint32_t)(umax64(st, t0) - t0), q1 = (uint32_t)(umin64(en, t0 + count) - t0);
+            const uint32_t ob0 = ones_before(q0), ob1 = ones_before(q1);
+            const uint32_t zs = q0 - ob0, ze = q1 - ob1;
+            const Run rz = make_run(__ldg(&a.nodes[p].off0) + (t0 - E) + zs, ze - zs, lim, 32 + zs);
+            const Run ro = make_run(__ldg(&a.nodes[p].off1) + E + ob0, ob1 - ob0, lim, 32 + ob0);
+            for (uint32_t i0 = 0; i0 < rz.nw + ro.nw; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                const bool act = i < rz.nw + ro.nw;
+                uint32_t ones = 0;
+                uint64_t k = 0;
+                if (act) {
+                    if (i < rz.nw) {
+                        ones = run_word(rz, i, img0, plane);
+                        k = rz.k0 + i;
+                    } else {
+                        ones = run_word(ro, i - rz.nw, img1, plane);
+                        k = ro.k0 + (i - rz.nw);
+                    }
+                }
+                if (FIRST) count_key(a.next_count, act, k / kTileWords, ones);
+            }
+        }
+    }
+    if (tid == 0 || tid == 8) bulk_commit();
+    // the set of plane j - 2 is free: its bulk reads are done (waited before the barrier)
+    if (tid < 2 * kImgWords / 4)
+        reinterpret_cast<uint4*>(&S.img[(j + 2) & (kSets - 1)][0][0])[tid] = make_uint4(0, 0, 0, 0);
 }
 
-__global__ void __launch_bounds__(kMoveThreads, 2) move_pass_kernel(const LevelArgs* __restrict__ args,
-                                                                    const uint64_t* __restrict__ tile_prefix,
-                                                                    uint32_t ntrees, unsigned long long* __restrict__ counter) {
+__global__ void __launch_bounds__(kTileThreads, 2) level_kernel(const LevelArgs* __restrict__ args,
+                                                                const uint64_t* __restrict__ tile_prefix,
+                                                                uint32_t ntrees, unsigned long long* __restrict__ counter) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    MoveSmem& S = *reinterpret_cast<MoveSmem*>(smem_raw);
+    TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
     __shared__ uint64_t s_g;
-    __shared__ uint32_t s_tree;
+    __shared__ uint32_t s_tree, s_have;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         for (uint32_t i = 0; i < kSlots; i++) mbar_init(&S.mbar[i], 1);
         mbar_fence_init();
+        s_have = 0xffffffffu;
     }
-    for (uint32_t i = tid; i < 3 * 2 * kImgWords; i += kMoveThreads) (&S.img[0][0][0])[i] = 0;
+    for (uint32_t i = tid; i < kSets * 2 * kImgWords / 4; i += kTileThreads)
+        reinterpret_cast<uint4*>(&S.img[0][0][0])[i] = make_uint4(0, 0, 0, 0);
+    S.zero[tid] = 0;
+    fence_proxy_async();
     uint32_t seq = 0;  // plane loads issued and consumed so far by this CTA
     const uint64_t total = tile_prefix[ntrees];
     for (;;) {
@@ -490,121 +522,222 @@ __global__ void __launch_bounds__(kMoveThreads, 2) move_pass_kernel(const LevelA
             s_g = g;
             if (g < total) s_tree = ntrees > 1 ? find_tree(tile_prefix, ntrees, g) : 0u;
         }
+        if (tid < 4) S.ones[tid] = 0;
         __syncthreads();
         const uint64_t g = s_g;
         if (g >= total) break;
-        const LevelArgs& a = args[s_tree];
-        const uint64_t tile = g - tile_prefix[s_tree];
-        const uint64_t t0 = tile * kMoveTile;
-        const uint32_t count = (uint32_t)umin64(kMoveTile, a.size - t0);
-        const uint32_t nw = (count + 31) / 32;
-        const uint32_t R = a.R;
-        const uint32_t bytes = (nw * 4 + 15) & ~15u;
-        auto issue = [&](uint32_t j) {
-            const uint32_t slot = (seq + j) % kSlots;
-            const uint32_t* src = j == 0 ? a.bits + (t0 >> 5) : a.in + (uint64_t)(j - 1) * a.pstride + (t0 >> 5);
-            mbar_expect_tx(&S.mbar[slot], bytes);
-            bulk_g2s(S.ring[slot], src, bytes, &S.mbar[slot]);
-        };
-        if (tid == 0)
-            for (uint32_t j = 0; j < R && j < kSlots; j++) issue(j);
-
-        // ---- plane 0 = B_l: masks, counts, offsets within the tile ----
-        mbar_wait(&S.mbar[seq % kSlots], (seq / kSlots) & 1u, a.status);
-        const uint32_t valid = tid < nw ? ((tid == nw - 1 && (count & 31)) ? (1u << (count & 31)) - 1u : 0xffffffffu) : 0u;
-        const uint32_t m1 = S.ring[seq % kSlots][tid] & valid, m0 = ~m1 & valid;
-        const uint32_t c1 = __popc(m1), c0 = __popc(m0);
-        uint32_t inc = c1;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= (uint32_t)o) inc += t;
-        }
-        if (lane == 31) S.wsum[warp] = inc;
-        const uint64_t E = a.prefix[tile];  // ones of B_l before the tile
-        uint32_t mv0[5], mv1[5];
-        compress_masks(m0, mv0);
-        compress_masks(m1, mv1);
-        __syncthreads();
-        if (tid == 0 && R > kSlots) issue(kSlots);  // plane 0's slot is free
-        uint32_t before = 0, O = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < kMoveThreads / 32; i++) {
-            const uint32_t v = S.wsum[i];
-            before += i < warp ? v : 0u;
-            O += v;
-        }
-        const uint32_t pre1 = before + inc - c1;  // ones before this word within the tile
-        const uint32_t pre0 = 32 * tid - pre1;    // zeros before it (earlier words are full)
-        S.b[tid] = m1;
-        S.pre[tid] = pre1;
-
-        // ---- nodes of the tile ----
-        const uint64_t lim = a.size_next;
-        const uint64_t p0 = a.nnodes > 1 ? umin64(a.first_node[tile], a.nnodes - 1) : 0;
-        const bool single = p0 + 1 >= a.nnodes || __ldg(&a.nodes[p0 + 1].start) >= t0 + count;
-        uint64_t d0 = 0, d1 = 0, k00 = 0, k01 = 0, e0 = 0, e1 = 0, nw0 = 0, nw1 = 0;
-        if (single) {
-            const NodeEntry& ne = a.nodes[p0];
-            d0 = __ldg(&ne.off0) + (t0 - E);
-            d1 = __ldg(&ne.off1) + E;
-            nw0 = run_words(d0, count - O, lim, k00, e0);
-            nw1 = run_words(d1, O, lim, k01, e1);
-        }
-
-        // ---- planes 1..R-1 ----
-        for (uint32_t j = 1; j < R; j++) {
-            const uint32_t u = seq + j, slot = u % kSlots;
-            mbar_wait(&S.mbar[slot], (u / kSlots) & 1u, a.status);
-            const uint32_t x = S.ring[slot][tid];
-            const uint32_t set = j % 3;
-            place(S.img[set][0], pre0, c0, compress(x, m0, mv0));
-            place(S.img[set][1], pre1, c1, compress(x, m1, mv1));
+        const uint32_t tree = s_tree;
+        if (tree != s_have) {  // uniform: copy the tree's arguments once
+            if (tid < sizeof(LevelArgs) / 8)
+                reinterpret_cast<uint64_t*>(&S.args)[tid] = reinterpret_cast<const uint64_t*>(args + tree)[tid];
             __syncthreads();
-            if (tid == 0 && j + kSlots < R) issue(j + kSlots);
-            uint32_t* dst = j == 1 ? a.out0 : a.out + (uint64_t)(j - 2) * a.pstride;
-            const uint32_t* img0 = S.img[set][0];
-            const uint32_t* img1 = S.img[set][1];
-            if (single) {
-                for (uint64_t i = tid; i < nw0 + nw1; i += kMoveThreads) {
-                    if (i < nw0) copy_word(dst, k00 + i, d0, e0, img0, 0);
-                    else copy_word(dst, k01 + (i - nw0), d1, e1, img1, 0);
+            if (tid == 0) s_have = tree;
+        }
+        const LevelArgs& a = S.args;
+        const uint32_t R = a.R;
+        uint32_t m0, m1, c0, c1, pre0, pre1, qz = 32, qo = 32;
+        uint32_t mv0[5], mv1[5];
+        uint32_t thr[4] = {0, 0, 0, 0};
+        bool single;
+        {
+            const uint64_t tile = g - tile_prefix[tree];
+            const uint64_t t0 = tile * kTile;
+            const uint64_t size = a.size;
+            const uint32_t count = (uint32_t)umin64(kTile, size - t0);
+            const uint32_t nw = (count + 31) / 32;
+            const uint32_t bytes = (nw * 4 + 15) & ~15u;
+            if (tid == 0) {
+                for (uint32_t j = 0; j < R && j < kSlots; j++) {
+                    const uint32_t slot = (seq + j) % kSlots;
+                    const uint32_t* src = (j == 0 ? a.bits : a.in + (uint64_t)(j - 1) * a.pstride) + (t0 >> 5);
+                    mbar_expect_tx(&S.mbar[slot], bytes);
+                    bulk_g2s(S.ring[slot], src, bytes, &S.mbar[slot]);
                 }
-            } else {
-                // one warp per node of the tile
-                auto ones_before = [&](uint32_t r) -> uint32_t {
-                    const uint32_t wi = r >> 5;
-                    if (wi >= nw) return O;
-                    return S.pre[wi] + __popc(S.b[wi] & ((1u << (r & 31)) - 1u));
-                };
-                for (uint64_t p = p0 + warp; p < a.nnodes; p += kMoveThreads / 32) {
-                    const uint64_t st = __ldg(&a.nodes[p].start);
-                    if (st >= t0 + count) break;
-                    const uint64_t en = p + 1 < a.nnodes ? __ldg(&a.nodes[p + 1].start) : a.size;
-                    const uint32_t r0 = (uint32_t)(umax64(st, t0) - t0), r1 = (uint32_t)(umin64(en, t0 + count) - t0);
-                    const uint32_t ob0 = ones_before(r0), ob1 = ones_before(r1);
-                    const uint32_t zs = r0 - ob0, ze = r1 - ob1;
-                    uint64_t k0, e, kk0, ee;
-                    const uint64_t dz = __ldg(&a.nodes[p].off0) + (t0 - E) + zs;
-                    const uint64_t dn = __ldg(&a.nodes[p].off1) + E + ob0;
-                    const uint64_t nz = run_words(dz, ze - zs, lim, k0, e);
-                    const uint64_t no = run_words(dn, ob1 - ob0, lim, kk0, ee);
-                    for (uint64_t i = lane; i < nz + no; i += 32) {
-                        if (i < nz) copy_word(dst, k0 + i, dz, e, img0, zs);
-                        else copy_word(dst, kk0 + (i - nz), dn, ee, img1, ob0);
+                S.t0 = t0;
+                S.count = count;
+            }
+            const uint64_t E = a.prefix[tile];                                   // ones of B_l before the tile
+            const uint64_t EL1 = a.prefix[tile & ~(uint64_t)(kTilesPerL1 - 1)];  // ... before its L1 block
+            if (warp == 1 && R > 1) {
+                const uint64_t p0 = a.nnodes > 1 ? warp_find_node(a.nodes, a.nnodes, t0) : 0;
+                if (lane == 0) S.p0 = p0;
+            }
+
+            // ---- plane 0 = B_l: counts, offsets within the tile, masks ----
+            // one warp waits for a plane; the barrier after it hands the plane to all
+            if (warp == 0) mbar_wait(&S.mbar[seq % kSlots], (seq / kSlots) & 1u, a.status);
+            __syncthreads();
+            const uint32_t valid = tid < nw ? ((tid == nw - 1 && (count & 31)) ? (1u << (count & 31)) - 1u : 0xffffffffu) : 0u;
+            m1 = S.ring[seq % kSlots][tid] & valid;
+            m0 = ~m1 & valid;
+            c1 = __popc(m1);
+            c0 = __popc(m0);
+            uint32_t inc = c1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= (uint32_t)o) inc += t;
+            }
+            if (lane == 31) S.wsum[warp] = inc;
+            if (R > 1) {
+                compress_masks(m0, mv0);
+                compress_masks(m1, mv1);
+                if (warp == 0) mbar_wait(&S.mbar[(seq + 1) % kSlots], ((seq + 1) / kSlots) & 1u, a.status);
+            }
+            __syncthreads();
+            if (tid == 0 && R > kSlots) {  // plane 0's slot is free
+                const uint32_t slot = seq % kSlots;
+                mbar_expect_tx(&S.mbar[slot], bytes);
+                bulk_g2s(S.ring[slot], a.in + (uint64_t)(kSlots - 1) * a.pstride + (t0 >> 5), bytes, &S.mbar[slot]);
+            }
+            const uint32_t ws = lane < kTileThreads / 32 ? S.wsum[lane] : 0u;
+            const uint32_t before = __reduce_add_sync(0xffffffffu, lane < warp ? ws : 0u);
+            const uint32_t O = __reduce_add_sync(0xffffffffu, ws);  // ones of the tile
+            pre1 = before + inc - c1;  // ones before this word within the tile
+            pre0 = 32 * tid - pre1;    // zeros before it (earlier words are full)
+
+            // ---- level l: L1 / L2 counters and select samples ----
+            if ((tid & 15) == 0 && tid < nw) a.l2[(t0 >> 9) + (tid >> 4)] = (uint16_t)(E - EL1 + pre1);
+            if (tid == 0) {
+                if ((tile & (kTilesPerL1 - 1)) == 0) a.l1[t0 >> 16] = E;
+                if (t0 + count == size && (size & 511) == 0) {
+                    if ((size & 65535) == 0) {
+                        a.l1[size >> 16] = E + O;
+                        a.l2[size >> 9] = 0;
+                    } else {
+                        a.l2[size >> 9] = (uint16_t)(E + O - EL1);
                     }
                 }
+                if (tile == 0) {
+                    a.s0[0] = 0;
+                    a.s1[0] = 0;
+                }
             }
-            // the set used two planes ago is free (everyone passed this plane's barrier)
-            uint32_t* z = &S.img[(j + 2) % 3][0][0];
-            for (uint32_t i = tid; i < 2 * kImgWords; i += kMoveThreads) z[i] = 0;
+            if (tid < nw) {  // at most one sample of each kind per word (K >= 256)
+                const uint32_t kl = a.k_log2;
+                const uint64_t g1 = E + pre1, g0 = (t0 - E) + pre0;  // ones / zeros before the word
+                const uint64_t base = t0 + 32ull * tid;
+                if (((g1 + c1) >> kl) != (g1 >> kl)) {
+                    const uint64_t m = (g1 + c1) >> kl;
+                    if (m < a.n_s1) a.s1[m] = base + select_in_word(m1, (uint32_t)((m << kl) - g1));
+                }
+                if (((g0 + c0) >> kl) != (g0 >> kl)) {
+                    const uint64_t m = (g0 + c0) >> kl;
+                    if (m < a.n_s0) a.s0[m] = base + select_in_word(m0, (uint32_t)((m << kl) - g0));
+                }
+            }
+            if (R == 1) {
+                seq += 1;
+                __syncthreads();
+                continue;
+            }
+
+            // ---- runs of the tile in T_{l+1} ----
+            S.b[tid] = m1;
+            S.pre[tid] = pre1;
+            const uint64_t lim = a.size_next;
+            const uint64_t p0 = S.p0;
+            single = p0 + 1 >= a.nnodes || __ldg(&a.nodes[p0 + 1].start) >= t0 + count;
+            if (single) {
+                // each run's image is aligned with its output words (image word k0 mod 4
+                // holds output word k0), so whole words leave by bulk copy
+                const uint64_t d0 = __ldg(&a.nodes[p0].off0) + (t0 - E);
+                const uint64_t d1 = __ldg(&a.nodes[p0].off1) + E;
+                qz = ((uint32_t)d0 & 127u) + pre0;
+                qo = ((uint32_t)d1 & 127u) + pre1;
+                if (tid == 0) S.run[0] = plan_run(d0, count - O, lim);
+                if (tid == 8) S.run[1] = plan_run(d1, O, lim);
+                thr[0] = (uint32_t)umin64(((d0 / kTile) + 1) * kTile - d0, count - O);
+                thr[1] = d0 >= lim ? 0u : (uint32_t)umin64(count - O, lim - d0);
+                thr[2] = (uint32_t)umin64(((d1 / kTile) + 1) * kTile - d1, O);
+                thr[3] = d1 >= lim ? 0u : (uint32_t)umin64(O, lim - d1);
+            } else {
+                // several nodes: images start at bit 32 and runs are shifted into place
+                qz = 32 + pre0;
+                qo = 32 + pre1;
+                if (tid == 0) {
+                    S.E = E;
+                    S.O = O;
+                }
+            }
+        }
+
+        // ---- planes 1..R-1 (plane j is ready: waited before the last barrier) ----
+        auto clear_input = [&](uint32_t j) {  // consumed: clear for reuse as an output
+            if (tid == 0) {
+                const uint32_t nw = (S.count + 31) / 32, bytes = (nw * 4 + 15) & ~15u;
+                bulk_s2g(a.in + (uint64_t)(j - 1) * a.pstride + (S.t0 >> 5), S.zero, bytes);
+            }
+        };
+        clear_input(1);
+        move_plane<true>(S, a, 1, seq + 1, R, S.ring[(seq + 1) % kSlots][tid], m0, m1, mv0, mv1, qz, qo, c0, c1, pre0,
+                         pre1, single, thr);
+        for (uint32_t j = 2; j < R; j++) {
+            const uint32_t u = seq + j;
+            clear_input(j);
+            move_plane<false>(S, a, j, u, R, S.ring[u % kSlots][tid], m0, m1, mv0, mv1, qz, qo, c0, c1, pre0, pre1,
+                              single, thr);
         }
         seq += R;
+        if (tid == 0 || tid == 8) bulk_wait_read<0>();
         __syncthreads();
-        if (R > 1) {
-            uint32_t* z = &S.img[(R - 1) % 3][0][0];
-            for (uint32_t i = tid; i < 2 * kImgWords; i += kMoveThreads) z[i] = 0;
+        if (tid < 2 * kImgWords / 4) {
+            reinterpret_cast<uint4*>(&S.img[(R - 1) & (kSets - 1)][0][0])[tid] = make_uint4(0, 0, 0, 0);
+            reinterpret_cast<uint4*>(&S.img[(R - 2) & (kSets - 1)][0][0])[tid] = make_uint4(0, 0, 0, 0);
         }
+    }
+    if (tid == 0 || tid == 8) bulk_wait_all();
+}
+
+// ===========================================================================
+// prefixes: exclusive scan of per-tile counts, one CTA per tree
+// ===========================================================================
+
+__global__ void __launch_bounds__(1024) count_scan_kernel(const LevelArgs* __restrict__ args) {
+    __shared__ uint64_t s_w[32];
+    __shared__ uint64_t s_carry;
+    const LevelArgs& a = args[blockIdx.x];
+    const uint64_t n = level_tiles(a.size);
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (uint64_t base = 0; base < n; base += 1024 * kScanPerThread) {
+        uint64_t v[kScanPerThread];
+        uint64_t sum = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kScanPerThread; k++) {
+            const uint64_t i = base + (uint64_t)tid * kScanPerThread + k;
+            v[k] = i < n ? a.count[i] : 0;
+            sum += v[k];
+        }
+        uint64_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (uint32_t)o) inc += t;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t x = s_w[lane], xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t t = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= (uint32_t)o) xi += t;
+            }
+            s_w[lane] = xi - x;
+        }
+        __syncthreads();
+        uint64_t run = s_carry + s_w[warp] + inc - sum;
+#pragma unroll
+        for (uint32_t k = 0; k < kScanPerThread; k++) {
+            const uint64_t i = base + (uint64_t)tid * kScanPerThread + k;
+            if (i < n) a.prefix[i] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == 1023) s_carry = run;
+        __syncthreads();
     }
 }
 
@@ -622,32 +755,26 @@ wt_status launch_transpose(const TransposeArgs* d_args, const uint64_t* d_chunk_
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
-wt_status launch_rank_pass(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
-                           unsigned long long* counter, uint64_t max_tiles, cudaStream_t s) {
+wt_status launch_level(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
+                       unsigned long long* counter, uint64_t max_tiles, cudaStream_t s) {
     static int per_sm = 0;
+    const size_t sm = sizeof(TileSmem);
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_pass_kernel, kRankThreads, 0);
+        if (cudaFuncSetAttribute(level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+            return WT_ECUDA;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_kernel, kTileThreads, sm);
         if (per_sm <= 0) per_sm = 1;
     }
     const uint64_t grid = umin64(max_tiles ? max_tiles : 1, (uint64_t)per_sm * sm_count());
-    ProfScope ps("rank_pass", s);
-    rank_pass_kernel<<<(unsigned)grid, kRankThreads, 0, s>>>(d_args, d_tile_prefix, ntrees, counter);
+    ProfScope ps("level", s);
+    level_kernel<<<(unsigned)grid, kTileThreads, sm, s>>>(d_args, d_tile_prefix, ntrees, counter);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
-wt_status launch_move_pass(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
-                           unsigned long long* counter, uint64_t max_tiles, cudaStream_t s) {
-    static int per_sm = 0;
-    const size_t sm = sizeof(MoveSmem);
-    if (!per_sm) {
-        if (cudaFuncSetAttribute(move_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-            return WT_ECUDA;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, move_pass_kernel, kMoveThreads, sm);
-        if (per_sm <= 0) per_sm = 1;
-    }
-    const uint64_t grid = umin64(max_tiles ? max_tiles : 1, (uint64_t)per_sm * sm_count());
-    ProfScope ps("move_pass", s);
-    move_pass_kernel<<<(unsigned)grid, kMoveThreads, sm, s>>>(d_args, d_tile_prefix, ntrees, counter);
+wt_status launch_count_scan(const LevelArgs* d_args, uint32_t ntrees, cudaStream_t s) {
+    if (!ntrees) return WT_OK;
+    ProfScope ps("count_scan", s);
+    count_scan_kernel<<<ntrees, 1024, 0, s>>>(d_args);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 

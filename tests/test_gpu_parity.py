@@ -285,8 +285,8 @@ def test_repeated_builds_and_profile_counts():
     rep = wt.profile_report()
     assert rep["access"]["launches"] == 3
     assert rep["transpose"]["launches"] == 3
-    assert rep["rank_pass"]["launches"] == 3 * 7
-    assert rep["move_pass"]["launches"] == 3 * 6
+    assert rep["level"]["launches"] == 3 * 7
+    assert rep["count_scan"]["launches"] == 3 * 7
     assert wt.profile_launches() >= 3 * 8
 
 
