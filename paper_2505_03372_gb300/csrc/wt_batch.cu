@@ -213,7 +213,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     const uint64_t o_count = take(count_total);
     const uint64_t o_words = take(words_total);  // every tree's level words, one region (cleared per run)
     struct TreeOff {
-        uint64_t C, nodes, left, excl, planes[2], prefix, count;
+        uint64_t C, nodes, left, excl, planes[2], prefix, count, first;
         std::vector<uint64_t> words, l1, l2, s0, s1, walloc;
     };
     std::vector<TreeOff> to(ntrees);
@@ -231,6 +231,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
         t.planes[0] = take(set_bytes);
         t.planes[1] = take(L > 2 ? set_bytes : 0);
         t.prefix = take(level_tiles(n) * 8);
+        t.first = take(level_tiles(n) * 4);
         t.count = count_off;
         count_off += al(level_tiles(n) * 4);
         for (uint32_t l = 0; l < L; l++) {
@@ -330,6 +331,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
             a.count = count;
             a.prefix = reinterpret_cast<uint64_t*>(M + to[i].prefix);
             a.next_count = count;
+            a.first_node = reinterpret_cast<uint32_t*>(M + to[i].first);
             a.status = ti.status;
             a.R = L - l;
             a.k_log2 = kl;

@@ -414,6 +414,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         const size_t o_set1 = take(L > 2 ? set_words * 4 : 0);
         const size_t o_count = take(ntile * 4);
         const size_t o_prefix = take(ntile * 8);
+        const size_t o_first = take(ntile * 4);
         const size_t o_la = take(L * sizeof(LevelArgs));
         const size_t o_ta = take(sizeof(TransposeArgs));
         const size_t o_tp = take((L + 1) * 2 * 8);  // tile prefixes {0, tiles} per level + transpose
@@ -455,6 +456,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.count = count;
             a.prefix = reinterpret_cast<uint64_t*>(Wm + o_prefix);
             a.next_count = count;
+            a.first_node = reinterpret_cast<uint32_t*>(Wm + o_first);
             a.status = t->desc.status;
             a.R = L - l;
             a.k_log2 = k_log2;
@@ -486,7 +488,9 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             if (t->level_size[l] == 0) continue;
             st = launch_count_scan(d_la + l, 1, s);
             if (st == WT_OK && l + 1 < L && cudaMemsetAsync(count, 0, ntile * 4, s) != cudaSuccess) st = WT_ECUDA;
-            if (st == WT_OK) st = launch_level(d_la + l, d_tp + 2 * l, 1, d_cnt + l, tp[2 * l + 1], s);
+            if (st == WT_OK && l + 1 < L && la[l].nnodes > 1)
+                st = launch_first_node(d_la + l, d_tp + 2 * l, 1, tp[2 * l + 1], s);
+            if (st == WT_OK) st = launch_level(d_la + l, d_tp + 2 * l, 1, tp[2 * l + 1], s);
         }
         dev_free(work, s);
         if (st != WT_OK) {
@@ -693,10 +697,11 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
         const LevelArgs* la = b.la + (uint64_t)l * b.ntrees;
         if (launch_count_scan(la, b.ntrees, s) != WT_OK) return WT_ECUDA;
         WT_CUDA_TRY(cudaMemsetAsync(b.count_pool, 0, b.count_bytes, s));
-        if (launch_level(la, b.tile_prefix + (uint64_t)l * (b.ntrees + 1), b.ntrees, b.counters + l, b.max_tiles, s) !=
-            WT_OK)
+        if (launch_first_node(la, b.tile_prefix + (uint64_t)l * (b.ntrees + 1), b.ntrees, b.max_tiles, s) != WT_OK)
             return WT_ECUDA;
-        nk += 2;
+        if (launch_level(la, b.tile_prefix + (uint64_t)l * (b.ntrees + 1), b.ntrees, b.max_tiles, s) != WT_OK)
+            return WT_ECUDA;
+        nk += 3;
     }
     if (kernels) *kernels = nk;
     return WT_OK;

@@ -212,6 +212,7 @@ struct LevelArgs {
     uint32_t* count;          // per tile: ones of B_l in it
     uint64_t* prefix;         // per tile: ones of B_l before it (exclusive scan of count)
     uint32_t* next_count;     // per tile of level l+1: ones of B_{l+1}, accumulated here (zeroed before)
+    uint32_t* first_node;     // per tile: node holding its first position (levels with several nodes)
     uint32_t* status;
     uint32_t R;               // planes of T_l (L - l)
     uint32_t k_log2;

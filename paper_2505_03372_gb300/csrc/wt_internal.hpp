@@ -109,7 +109,9 @@ uint64_t internal_nodes(const CodeParams& cp, uint32_t l);
 wt_status launch_transpose(const TransposeArgs* d_args, const uint64_t* d_chunk_prefix, uint32_t ntrees,
                            uint64_t chunks, uint32_t w, cudaStream_t s);
 wt_status launch_level(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
-                       unsigned long long* counter, uint64_t max_tiles, cudaStream_t s);
+                       uint64_t max_tiles, cudaStream_t s);
+wt_status launch_first_node(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
+                            uint64_t max_tiles, cudaStream_t s);
 wt_status launch_count_scan(const LevelArgs* d_args, uint32_t ntrees, cudaStream_t s);
 
 // ---- queries (wt_query.cu) ----

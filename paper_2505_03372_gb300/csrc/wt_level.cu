@@ -44,9 +44,9 @@ constexpr uint32_t kTileThreads = 512;  // one 32-bit word of every plane per th
 constexpr uint32_t kTileWords = kTile / 32;
 constexpr uint32_t kTilesPerL1 = kL1Bits / kTile;
 constexpr uint32_t kScanPerThread = 8;
-constexpr uint32_t kSlots = 8;          // plane ring of the move pass
+constexpr uint32_t kSlots = 16;         // plane ring: planes of the current and the next tiles
 constexpr uint32_t kImgWords = 520;     // one run image: 512 words + alignment and read-ahead
-constexpr uint32_t kSets = 4;           // run-image sets in rotation
+constexpr uint32_t kPairs = 3;          // run-image slots in rotation, each for a pair of planes
 constexpr uint32_t kTrThreads = 256;    // transpose: 32 symbols per thread
 constexpr uint32_t kTrTable = 1024;     // codes tabulated in shared memory up to this sigma
 
@@ -66,6 +66,11 @@ uint64_t internal_nodes(const CodeParams& cp, uint32_t l) {
     }
     return lo;
 }
+
+template <bool B>
+struct BoolTag {
+    static constexpr bool value = B;
+};
 
 // ===========================================================================
 // bit tools
@@ -282,19 +287,31 @@ struct RunPlan {
     uint64_t tile;     // tile of level l+1 holding the run's first bit
 };
 
+// Load cursor (thread 0): issues plane loads in (tile, plane) order, tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ..., whenever a ring slot is free.
+struct Cursor {
+    uint64_t g;          // tile being loaded (global index over the trees' tiles)
+    uint32_t tree, j, R, bytes;
+    const uint32_t* bits;
+    const uint32_t* in;
+    uint64_t pstride, w0;  // plane stride, first word of the tile
+    uint64_t size, first;  // the tree's level size and first tile
+    uint32_t issued;
+};
 struct TileSmem {
-    uint32_t ring[kSlots][kTileWords];  // planes in flight
-    uint32_t img[kSets][2][kImgWords];  // zero-run / one-run images, in rotation
-    uint32_t zero[kTileWords];          // zeros: source of the bulk clears of consumed planes
-    uint32_t b[kTileWords];             // B_l words of the tile
-    uint32_t pre[kTileWords];           // ones before each word within the tile
-    LevelArgs args;                     // the current tree's level arguments
-    RunPlan run[2];                     // single-node tiles: zero run, one run
+    uint32_t ring[kSlots][kTileWords];     // planes in flight, in (tile, plane) order
+    uint32_t img[kPairs][2][2][kImgWords]; // [slot][plane of the pair][zero run, one run]
+    uint32_t zero[kTileWords];             // zeros: source of the bulk clears of consumed planes
+    uint32_t b[kTileWords];                // B_l words of the tile
+    uint32_t pre[kTileWords];              // ones before each word within the tile
+    LevelArgs args;                        // the current tile's tree
+    RunPlan run[2];                        // single-node tiles: zero run, one run
     uint64_t mbar[kSlots];
-    uint64_t p0;                        // node of the tile's first element
-    uint64_t t0, E;                     // tile start, ones of B_l before it
-    uint32_t count, O;                  // tile elements, ones
-    uint32_t ones[4];                   // ones of B_{l+1} per (run, side of a tile boundary)
+    uint64_t t0, E, p0;                    // tile start, ones of B_l before it, its first node
+    uint32_t count, O;                     // tile elements, ones
+    uint32_t tree;
+    Cursor cur;                            // load cursor (thread 0)
+    uint32_t ones[4];                      // ones of B_{l+1} per (run, side of a tile boundary)
     uint32_t wsum[kTileThreads / 32];
 };
 
@@ -310,7 +327,7 @@ __device__ __forceinline__ void place(uint32_t* img, uint32_t off, uint32_t cnt,
 // Ones of run bits [x0, x1) inside a piece of c bits (right-aligned in v) at run bit pre.
 __device__ __forceinline__ uint32_t ones_in(uint32_t v, uint32_t pre, uint32_t c, uint32_t x0, uint32_t x1) {
     const uint32_t lo = x0 > pre ? x0 - pre : 0u;
-    const uint32_t hi = x1 > pre ? umin64(x1 - pre, c) : 0u;
+    const uint32_t hi = x1 > pre ? (uint32_t)umin64(x1 - pre, c) : 0u;
     if (hi <= lo) return 0;
     const uint32_t m = (hi >= 32 ? 0xffffffffu : (1u << hi) - 1u) & ~((1u << lo) - 1u);
     return __popc(v & m);
@@ -397,296 +414,348 @@ __device__ __forceinline__ void plan_edge_word(const RunPlan& p, uint32_t q, con
     else atomicOr(plane + p.k0 + i, v & mask);
 }
 
-// One plane of a tile: compress this thread's word under the zeros and the
-// ones of B_l into the image set, then (after the barrier) write the runs.
+// Write plane j's runs from images img0 (zeros) and img1 (ones).  Single-node
+// tiles: 16 threads (base..base+15) write the words around two bulk copies;
+// several nodes: one warp per node.  Returns nothing; j == 1 also counts ones.
 template <bool FIRST>
-__device__ __forceinline__ void move_plane(TileSmem& S, const LevelArgs& a, uint32_t j, uint32_t u, uint32_t R,
-                                           uint32_t x, uint32_t m0, uint32_t m1, const uint32_t (&mv0)[5],
-                                           const uint32_t (&mv1)[5], uint32_t qz, uint32_t qo, uint32_t c0,
-                                           uint32_t c1, uint32_t pre0, uint32_t pre1, bool single,
-                                           const uint32_t (&thr)[4]) {
+__device__ __forceinline__ void write_plane(TileSmem& S, const LevelArgs& a, uint32_t j, const uint32_t* img0,
+                                            const uint32_t* img1, bool single, uint32_t base) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t set = j & (kSets - 1);
-    const uint32_t cz = compress_left(x & m0, mv0), co = compress_left(x & m1, mv1);
-    place(S.img[set][0], qz, c0, cz);
-    place(S.img[set][1], qo, c1, co);
-    if (FIRST && single) {
-        // ones of B_{l+1}: per run, before and after the tile boundary of level l+1
-        const uint32_t vz = c0 ? cz >> (32 - c0) : 0u, vo = c1 ? co >> (32 - c1) : 0u;
-        // thr: per run, the run bits before the next tile boundary and below size_{l+1}
-        uint32_t n0 = ones_in(vz, pre0, c0, 0, umin64(thr[0], thr[1]));
-        uint32_t n1 = ones_in(vz, pre0, c0, thr[0], thr[1]);
-        uint32_t n2 = ones_in(vo, pre1, c1, 0, umin64(thr[2], thr[3]));
-        uint32_t n3 = ones_in(vo, pre1, c1, thr[2], thr[3]);
-        n0 = __reduce_add_sync(0xffffffffu, n0);
-        n1 = __reduce_add_sync(0xffffffffu, n1);
-        n2 = __reduce_add_sync(0xffffffffu, n2);
-        n3 = __reduce_add_sync(0xffffffffu, n3);
-        if (lane == 0) {
-            if (n0) atomicAdd(&S.ones[0], n0);
-            if (n1) atomicAdd(&S.ones[1], n1);
-            if (n2) atomicAdd(&S.ones[2], n2);
-            if (n3) atomicAdd(&S.ones[3], n3);
-        }
-    }
-    fence_proxy_async();
-    if (tid == 0 || tid == 8) bulk_wait_read<1>();  // images of plane j - 2 have been read
-    if (warp == 0 && j + 1 < R) mbar_wait(&S.mbar[(u + 1) % kSlots], ((u + 1) / kSlots) & 1u, a.status);
-    __syncthreads();
-    if (tid == 0 && j + kSlots < R) {  // refill plane j's slot
-        const uint32_t slot = u % kSlots;
-        const uint32_t nw = (S.count + 31) / 32, bytes = (nw * 4 + 15) & ~15u;
-        mbar_expect_tx(&S.mbar[slot], bytes);
-        bulk_g2s(S.ring[slot], a.in + (uint64_t)(j + kSlots - 1) * a.pstride + (S.t0 >> 5), bytes, &S.mbar[slot]);
-    }
     uint32_t* plane = j == 1 ? a.out0 : a.out + (uint64_t)(j - 2) * a.pstride;
-    const uint32_t* img0 = S.img[set][0];
-    const uint32_t* img1 = S.img[set][1];
     if (single) {
-        if (tid < 16) {
-            const RunPlan& p = S.run[tid >> 3];
-            const uint32_t* img = tid < 8 ? img0 : img1;
-            const uint32_t q = tid & 7;
+        if (tid >= base && tid < base + 16) {
+            const uint32_t t = tid - base;
+            const RunPlan& p = S.run[t >> 3];
+            const uint32_t* img = t < 8 ? img0 : img1;
+            const uint32_t q = t & 7;
             if (q == 0 && p.tb > p.ta) bulk_s2g(plane + p.k0 + p.ta, img + p.wb + p.ta, 4 * (p.tb - p.ta));
             plan_edge_word(p, q, img, plane);
             if (FIRST && q == 0) {  // this run's ones of B_{l+1}, per tile of level l+1
-                const uint32_t k = (tid >> 3) * 2;
+                const uint32_t k = (t >> 3) * 2;
                 if (S.ones[k]) atomicAdd(a.next_count + p.tile, S.ones[k]);
                 if (S.ones[k + 1]) atomicAdd(a.next_count + p.tile + 1, S.ones[k + 1]);
             }
         }
-    } else {
-        // one warp per node of the tile
-        const uint64_t t0 = S.t0, E = S.E, lim = a.size_next;
-        const uint32_t count = S.count, O = S.O, nw = (count + 31) / 32;
-        auto ones_before = [&](uint32_t r) -> uint32_t {
-            const uint32_t wi = r >> 5;
-            if (wi >= nw) return O;
-            return S.pre[wi] + __popc(S.b[wi] & ((1u << (r & 31)) - 1u));
-        };
-        for (uint64_t p = S.p0 + warp; p < a.nnodes; p += kTileThreads / 32) {
-            const uint64_t st = __ldg(&a.nodes[p].start);
-            if (st >= t0 + count) break;
-            const uint64_t en = p + 1 < a.nnodes ? __ldg(&a.nodes[p + 1].start) : a.size;
-            const uint32_t q0 = (uint32_t)(umax64(st, t0) - t0), q1 = (uint32_t)(umin64(en, t0 + count) - t0);
-            const uint32_t ob0 = ones_before(q0), ob1 = ones_before(q1);
-            const uint32_t zs = q0 - ob0, ze = q1 - ob1;
-            const Run rz = make_run(__ldg(&a.nodes[p].off0) + (t0 - E) + zs, ze - zs, lim, 32 + zs);
-            const Run ro = make_run(__ldg(&a.nodes[p].off1) + E + ob0, ob1 - ob0, lim, 32 + ob0);
-            for (uint32_t i0 = 0; i0 < rz.nw + ro.nw; i0 += 32) {
-                const uint32_t i = i0 + lane;
-                const bool act = i < rz.nw + ro.nw;
-                uint32_t ones = 0;
-                uint64_t k = 0;
-                if (act) {
-                    if (i < rz.nw) {
-                        ones = run_word(rz, i, img0, plane);
-                        k = rz.k0 + i;
-                    } else {
-                        ones = run_word(ro, i - rz.nw, img1, plane);
-                        k = ro.k0 + (i - rz.nw);
-                    }
+        return;
+    }
+    const uint64_t t0 = S.t0, E = S.E, lim = a.size_next;
+    const uint32_t count = S.count, O = S.O, nw = (count + 31) / 32;
+    auto ones_before = [&](uint32_t r) -> uint32_t {
+        const uint32_t wi = r >> 5;
+        if (wi >= nw) return O;
+        return S.pre[wi] + __popc(S.b[wi] & ((1u << (r & 31)) - 1u));
+    };
+    for (uint64_t p = S.p0 + warp; p < a.nnodes; p += kTileThreads / 32) {
+        const uint64_t st = __ldg(&a.nodes[p].start);
+        if (st >= t0 + count) break;
+        const uint64_t en = p + 1 < a.nnodes ? __ldg(&a.nodes[p + 1].start) : a.size;
+        const uint32_t q0 = (uint32_t)(umax64(st, t0) - t0), q1 = (uint32_t)(umin64(en, t0 + count) - t0);
+        const uint32_t ob0 = ones_before(q0), ob1 = ones_before(q1);
+        const uint32_t zs = q0 - ob0, ze = q1 - ob1;
+        const Run rz = make_run(__ldg(&a.nodes[p].off0) + (t0 - E) + zs, ze - zs, lim, 32 + zs);
+        const Run ro = make_run(__ldg(&a.nodes[p].off1) + E + ob0, ob1 - ob0, lim, 32 + ob0);
+        for (uint32_t i0 = 0; i0 < rz.nw + ro.nw; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool act = i < rz.nw + ro.nw;
+            uint32_t ones = 0;
+            uint64_t k = 0;
+            if (act) {
+                if (i < rz.nw) {
+                    ones = run_word(rz, i, img0, plane);
+                    k = rz.k0 + i;
+                } else {
+                    ones = run_word(ro, i - rz.nw, img1, plane);
+                    k = ro.k0 + (i - rz.nw);
                 }
-                if (FIRST) count_key(a.next_count, act, k / kTileWords, ones);
             }
+            if (FIRST) count_key(a.next_count, act, k / kTileWords, ones);
         }
     }
-    if (tid == 0 || tid == 8) bulk_commit();
-    // the set of plane j - 2 is free: its bulk reads are done (waited before the barrier)
-    if (tid < 2 * kImgWords / 4)
-        reinterpret_cast<uint4*>(&S.img[(j + 2) & (kSets - 1)][0][0])[tid] = make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ void cursor_tile(Cursor& c, const LevelArgs* args, const uint64_t* tile_prefix,
+                                            uint32_t ntrees, uint64_t total) {
+    if (c.g >= total) return;
+    const uint32_t tr0 = c.tree;
+    while (c.tree + 1 < ntrees && tile_prefix[c.tree + 1] <= c.g) c.tree++;
+    if (c.tree != tr0 || c.bits == nullptr) {
+        const LevelArgs& a = args[c.tree];
+        c.R = a.R;
+        c.bits = a.bits;
+        c.in = a.in;
+        c.pstride = a.pstride;
+        c.size = a.size;
+        c.first = tile_prefix[c.tree];
+    }
+    const uint64_t t0 = (c.g - c.first) * kTile;
+    const uint32_t count = (uint32_t)umin64(kTile, c.size - t0);
+    c.w0 = t0 >> 5;
+    c.bytes = (((count + 31) / 32) * 4 + 15) & ~15u;
+    c.j = 0;
+}
+__device__ __forceinline__ void cursor_pump(Cursor& c, TileSmem& S, uint32_t released, const LevelArgs* args,
+                                            const uint64_t* tile_prefix, uint32_t ntrees, uint64_t total) {
+    while (c.g < total && c.issued - released < kSlots) {
+        const uint32_t slot = c.issued % kSlots;
+        const uint32_t* src = (c.j == 0 ? c.bits : c.in + (uint64_t)(c.j - 1) * c.pstride) + c.w0;
+        mbar_expect_tx(&S.mbar[slot], c.bytes);
+        bulk_g2s(S.ring[slot], src, c.bytes, &S.mbar[slot]);
+        c.issued++;
+        if (++c.j == c.R) {
+            c.g += gridDim.x;
+            cursor_tile(c, args, tile_prefix, ntrees, total);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kTileThreads, 2) level_kernel(const LevelArgs* __restrict__ args,
                                                                 const uint64_t* __restrict__ tile_prefix,
-                                                                uint32_t ntrees, unsigned long long* __restrict__ counter) {
+                                                                uint32_t ntrees) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
-    __shared__ uint64_t s_g;
-    __shared__ uint32_t s_tree, s_have;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // threads that issue bulk copies: clears (0) and run write-outs (32, 40, 64, 72)
+    const bool bulk_thread = tid == 0 || tid == 32 || tid == 40 || tid == 64 || tid == 72;
+    const uint64_t total = tile_prefix[ntrees];
+    Cursor& cur = S.cur;
     if (tid == 0) {
         for (uint32_t i = 0; i < kSlots; i++) mbar_init(&S.mbar[i], 1);
         mbar_fence_init();
-        s_have = 0xffffffffu;
+        S.tree = 0xffffffffu;
     }
-    for (uint32_t i = tid; i < kSets * 2 * kImgWords / 4; i += kTileThreads)
-        reinterpret_cast<uint4*>(&S.img[0][0][0])[i] = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = tid; i < kPairs * 2 * 2 * kImgWords / 4; i += kTileThreads)
+        reinterpret_cast<uint4*>(&S.img[0][0][0][0])[i] = make_uint4(0, 0, 0, 0);
     S.zero[tid] = 0;
     fence_proxy_async();
-    uint32_t seq = 0;  // plane loads issued and consumed so far by this CTA
-    const uint64_t total = tile_prefix[ntrees];
-    for (;;) {
-        if (tid == 0) {
-            const uint64_t g = atomicAdd(counter, 1ull);
-            s_g = g;
-            if (g < total) s_tree = ntrees > 1 ? find_tree(tile_prefix, ntrees, g) : 0u;
-        }
-        if (tid < 4) S.ones[tid] = 0;
-        __syncthreads();
-        const uint64_t g = s_g;
-        if (g >= total) break;
-        const uint32_t tree = s_tree;
-        if (tree != s_have) {  // uniform: copy the tree's arguments once
+    __syncthreads();
+    if (tid == 0) {
+        cur.g = blockIdx.x;
+        cur.tree = 0;
+        cur.issued = 0;
+        cur.bits = nullptr;
+        cursor_tile(cur, args, tile_prefix, ntrees, total);
+        cursor_pump(cur, S, 0, args, tile_prefix, ntrees, total);
+    }
+    uint32_t seq = 0;   // planes consumed by this CTA
+    uint32_t pair = 0;  // plane pairs processed by this CTA (image slot rotation)
+    uint32_t tree = 0;  // this thread's view of the current tile's tree
+    for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
+        while (tree + 1 < ntrees && tile_prefix[tree + 1] <= g) tree++;
+        if (tree != S.tree) {  // uniform: copy the tree's arguments (the previous tile is done with them)
+            __syncthreads();
             if (tid < sizeof(LevelArgs) / 8)
                 reinterpret_cast<uint64_t*>(&S.args)[tid] = reinterpret_cast<const uint64_t*>(args + tree)[tid];
             __syncthreads();
-            if (tid == 0) s_have = tree;
+            if (tid == 0) S.tree = tree;
         }
         const LevelArgs& a = S.args;
         const uint32_t R = a.R;
-        uint32_t m0, m1, c0, c1, pre0, pre1, qz = 32, qo = 32;
-        uint32_t mv0[5], mv1[5];
-        uint32_t thr[4] = {0, 0, 0, 0};
-        bool single;
-        {
-            const uint64_t tile = g - tile_prefix[tree];
-            const uint64_t t0 = tile * kTile;
-            const uint64_t size = a.size;
-            const uint32_t count = (uint32_t)umin64(kTile, size - t0);
-            const uint32_t nw = (count + 31) / 32;
-            const uint32_t bytes = (nw * 4 + 15) & ~15u;
-            if (tid == 0) {
-                for (uint32_t j = 0; j < R && j < kSlots; j++) {
-                    const uint32_t slot = (seq + j) % kSlots;
-                    const uint32_t* src = (j == 0 ? a.bits : a.in + (uint64_t)(j - 1) * a.pstride) + (t0 >> 5);
-                    mbar_expect_tx(&S.mbar[slot], bytes);
-                    bulk_g2s(S.ring[slot], src, bytes, &S.mbar[slot]);
-                }
-                S.t0 = t0;
-                S.count = count;
-            }
-            const uint64_t E = a.prefix[tile];                                   // ones of B_l before the tile
-            const uint64_t EL1 = a.prefix[tile & ~(uint64_t)(kTilesPerL1 - 1)];  // ... before its L1 block
-            if (warp == 1 && R > 1) {
-                const uint64_t p0 = a.nnodes > 1 ? warp_find_node(a.nodes, a.nnodes, t0) : 0;
-                if (lane == 0) S.p0 = p0;
-            }
+        const uint64_t tile = g - tile_prefix[tree];
+        const uint64_t t0 = tile * kTile;
+        const uint64_t size = a.size;
+        const uint32_t count = (uint32_t)umin64(kTile, size - t0);
+        const uint32_t nw = (count + 31) / 32;
+        // metadata loads, used after the next barrier
+        const uint64_t E = a.prefix[tile];                                   // ones of B_l before the tile
+        const uint64_t EL1 = a.prefix[tile & ~(uint64_t)(kTilesPerL1 - 1)];  // ... before its L1 block
+        const uint64_t p0 = (R > 1 && a.nnodes > 1) ? umin64(a.first_node[tile], a.nnodes - 1) : 0;
 
-            // ---- plane 0 = B_l: counts, offsets within the tile, masks ----
-            // one warp waits for a plane; the barrier after it hands the plane to all
-            if (warp == 0) mbar_wait(&S.mbar[seq % kSlots], (seq / kSlots) & 1u, a.status);
-            __syncthreads();
-            const uint32_t valid = tid < nw ? ((tid == nw - 1 && (count & 31)) ? (1u << (count & 31)) - 1u : 0xffffffffu) : 0u;
-            m1 = S.ring[seq % kSlots][tid] & valid;
-            m0 = ~m1 & valid;
-            c1 = __popc(m1);
-            c0 = __popc(m0);
-            uint32_t inc = c1;
+        // ---- plane 0 = B_l (waited by warp 0 before the barrier) ----
+        if (warp == 0) mbar_wait(&S.mbar[seq % kSlots], (seq / kSlots) & 1u, a.status);
+        __syncthreads();
+        if (tid < 4) S.ones[tid] = 0;
+        const uint32_t valid = tid < nw ? ((tid == nw - 1 && (count & 31)) ? (1u << (count & 31)) - 1u : 0xffffffffu) : 0u;
+        const uint32_t m1 = S.ring[seq % kSlots][tid] & valid, m0 = ~m1 & valid;
+        const uint32_t c1 = __popc(m1), c0 = __popc(m0);
+        uint32_t inc = c1;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= (uint32_t)o) inc += t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (uint32_t)o) inc += t;
+        }
+        if (lane == 31) S.wsum[warp] = inc;
+        uint32_t mv0[5], mv1[5];
+        if (R > 1) {
+            compress_masks(m0, mv0);
+            compress_masks(m1, mv1);
+            if (warp == 0) {  // planes 1 and 2 (the first pair)
+                mbar_wait(&S.mbar[(seq + 1) % kSlots], ((seq + 1) / kSlots) & 1u, a.status);
+                if (R > 2) mbar_wait(&S.mbar[(seq + 2) % kSlots], ((seq + 2) / kSlots) & 1u, a.status);
             }
-            if (lane == 31) S.wsum[warp] = inc;
-            if (R > 1) {
-                compress_masks(m0, mv0);
-                compress_masks(m1, mv1);
-                if (warp == 0) mbar_wait(&S.mbar[(seq + 1) % kSlots], ((seq + 1) / kSlots) & 1u, a.status);
-            }
-            __syncthreads();
-            if (tid == 0 && R > kSlots) {  // plane 0's slot is free
-                const uint32_t slot = seq % kSlots;
-                mbar_expect_tx(&S.mbar[slot], bytes);
-                bulk_g2s(S.ring[slot], a.in + (uint64_t)(kSlots - 1) * a.pstride + (t0 >> 5), bytes, &S.mbar[slot]);
-            }
-            const uint32_t ws = lane < kTileThreads / 32 ? S.wsum[lane] : 0u;
-            const uint32_t before = __reduce_add_sync(0xffffffffu, lane < warp ? ws : 0u);
-            const uint32_t O = __reduce_add_sync(0xffffffffu, ws);  // ones of the tile
-            pre1 = before + inc - c1;  // ones before this word within the tile
-            pre0 = 32 * tid - pre1;    // zeros before it (earlier words are full)
+        } else if (warp == 0 && g + gridDim.x < total) {  // next tile's plane 0
+            mbar_wait(&S.mbar[(seq + 1) % kSlots], ((seq + 1) / kSlots) & 1u, a.status);
+        }
+        __syncthreads();
+        if (tid == 0) cursor_pump(cur, S, seq + 1, args, tile_prefix, ntrees, total);  // plane 0's slot is free
+        const uint32_t ws = lane < kTileThreads / 32 ? S.wsum[lane] : 0u;
+        const uint32_t before = __reduce_add_sync(0xffffffffu, lane < warp ? ws : 0u);
+        const uint32_t O = __reduce_add_sync(0xffffffffu, ws);  // ones of the tile
+        const uint32_t pre1 = before + inc - c1;  // ones before this word within the tile
+        const uint32_t pre0 = 32 * tid - pre1;    // zeros before it (earlier words are full)
 
-            // ---- level l: L1 / L2 counters and select samples ----
-            if ((tid & 15) == 0 && tid < nw) a.l2[(t0 >> 9) + (tid >> 4)] = (uint16_t)(E - EL1 + pre1);
+        // ---- level l: L1 / L2 counters and select samples ----
+        if ((tid & 15) == 0 && tid < nw) a.l2[(t0 >> 9) + (tid >> 4)] = (uint16_t)(E - EL1 + pre1);
+        if (tid == 0) {
+            if ((tile & (kTilesPerL1 - 1)) == 0) a.l1[t0 >> 16] = E;
+            if (t0 + count == size && (size & 511) == 0) {
+                if ((size & 65535) == 0) {
+                    a.l1[size >> 16] = E + O;
+                    a.l2[size >> 9] = 0;
+                } else {
+                    a.l2[size >> 9] = (uint16_t)(E + O - EL1);
+                }
+            }
+            if (tile == 0) {
+                a.s0[0] = 0;
+                a.s1[0] = 0;
+            }
+        }
+        if (tid < nw) {  // at most one sample of each kind per word (K >= 256)
+            const uint32_t kl = a.k_log2;
+            const uint64_t g1 = E + pre1, g0 = (t0 - E) + pre0;  // ones / zeros before the word
+            const uint64_t base = t0 + 32ull * tid;
+            if (((g1 + c1) >> kl) != (g1 >> kl)) {
+                const uint64_t m = (g1 + c1) >> kl;
+                if (m < a.n_s1) a.s1[m] = base + select_in_word(m1, (uint32_t)((m << kl) - g1));
+            }
+            if (((g0 + c0) >> kl) != (g0 >> kl)) {
+                const uint64_t m = (g0 + c0) >> kl;
+                if (m < a.n_s0) a.s0[m] = base + select_in_word(m0, (uint32_t)((m << kl) - g0));
+            }
+        }
+        if (R == 1) {
+            seq += 1;
+            continue;
+        }
+
+        // ---- runs of the tile in T_{l+1} ----
+        S.b[tid] = m1;
+        S.pre[tid] = pre1;
+        const uint64_t lim = a.size_next;
+        const bool single = p0 + 1 >= a.nnodes || __ldg(&a.nodes[p0 + 1].start) >= t0 + count;
+        uint32_t qz, qo;               // image bits of this thread's zero / one piece
+        uint32_t thr[4] = {0, 0, 0, 0};  // per run: bits before the next tile of level l+1, bits below size_{l+1}
+        if (single) {
+            // each run's image is aligned with its output words (image word k0 mod 4
+            // holds output word k0), so whole words leave by bulk copy
+            const uint64_t d0 = __ldg(&a.nodes[p0].off0) + (t0 - E);
+            const uint64_t d1 = __ldg(&a.nodes[p0].off1) + E;
+            qz = ((uint32_t)d0 & 127u) + pre0;
+            qo = ((uint32_t)d1 & 127u) + pre1;
+            if (tid == 0) S.run[0] = plan_run(d0, count - O, lim);
+            if (tid == 8) S.run[1] = plan_run(d1, O, lim);
+            thr[0] = (uint32_t)umin64(((d0 / kTile) + 1) * kTile - d0, count - O);
+            thr[1] = d0 >= lim ? 0u : (uint32_t)umin64(count - O, lim - d0);
+            thr[2] = (uint32_t)umin64(((d1 / kTile) + 1) * kTile - d1, O);
+            thr[3] = d1 >= lim ? 0u : (uint32_t)umin64(O, lim - d1);
+        } else {
+            // several nodes: images start at bit 32 and runs are shifted into place
+            qz = 32 + pre0;
+            qo = 32 + pre1;
             if (tid == 0) {
-                if ((tile & (kTilesPerL1 - 1)) == 0) a.l1[t0 >> 16] = E;
-                if (t0 + count == size && (size & 511) == 0) {
-                    if ((size & 65535) == 0) {
-                        a.l1[size >> 16] = E + O;
-                        a.l2[size >> 9] = 0;
-                    } else {
-                        a.l2[size >> 9] = (uint16_t)(E + O - EL1);
+                S.t0 = t0;
+                S.E = E;
+                S.p0 = p0;
+                S.count = count;
+                S.O = O;
+            }
+        }
+
+        // ---- planes 1..R-1 in pairs (planes of a pair are ready: waited before the last barrier) ----
+        if (tid == 0) {
+            S.t0 = t0;
+            S.count = count;
+        }
+        auto do_pair = [&](auto first_tag, uint32_t j) {
+            constexpr bool FIRST = decltype(first_tag)::value;
+            const bool two = j + 1 < R;
+            const uint32_t ps = pair % kPairs;
+            if (tid == 0) {  // consumed input planes: clear for reuse as outputs
+                const uint32_t bytes = (((S.count + 31) / 32) * 4 + 15) & ~15u;
+                const uint64_t w0 = S.t0 >> 5;
+                bulk_s2g(a.in + (uint64_t)(j - 1) * a.pstride + w0, S.zero, bytes);
+                if (two) bulk_s2g(a.in + (uint64_t)j * a.pstride + w0, S.zero, bytes);
+            }
+            {
+                const uint32_t x = S.ring[(seq + j) % kSlots][tid];
+                const uint32_t cz = compress_left(x & m0, mv0), co = compress_left(x & m1, mv1);
+                place(S.img[ps][0][0], qz, c0, cz);
+                place(S.img[ps][0][1], qo, c1, co);
+                if (FIRST && single) {
+                    // ones of B_{l+1}: per run, before and after the tile boundary of level l+1
+                    const uint32_t vz = c0 ? cz >> (32 - c0) : 0u, vo = c1 ? co >> (32 - c1) : 0u;
+                    uint32_t n0 = ones_in(vz, pre0, c0, 0, umin64(thr[0], thr[1]));
+                    uint32_t n1 = ones_in(vz, pre0, c0, thr[0], thr[1]);
+                    uint32_t n2 = ones_in(vo, pre1, c1, 0, umin64(thr[2], thr[3]));
+                    uint32_t n3 = ones_in(vo, pre1, c1, thr[2], thr[3]);
+                    n0 = __reduce_add_sync(0xffffffffu, n0);
+                    n1 = __reduce_add_sync(0xffffffffu, n1);
+                    n2 = __reduce_add_sync(0xffffffffu, n2);
+                    n3 = __reduce_add_sync(0xffffffffu, n3);
+                    if (lane == 0) {
+                        if (n0) atomicAdd(&S.ones[0], n0);
+                        if (n1) atomicAdd(&S.ones[1], n1);
+                        if (n2) atomicAdd(&S.ones[2], n2);
+                        if (n3) atomicAdd(&S.ones[3], n3);
                     }
                 }
-                if (tile == 0) {
-                    a.s0[0] = 0;
-                    a.s1[0] = 0;
+            }
+            if (two) {
+                const uint32_t x = S.ring[(seq + j + 1) % kSlots][tid];
+                place(S.img[ps][1][0], qz, c0, compress_left(x & m0, mv0));
+                place(S.img[ps][1][1], qo, c1, compress_left(x & m1, mv1));
+            }
+            fence_proxy_async();
+            if (bulk_thread) bulk_wait_read<0>();  // the previous pair's images have been read
+            if (warp == 0) {  // the next pair, or the next tile's plane 0
+                const uint32_t n0 = j + 2, n1 = j + 3;
+                if (n0 < R) {
+                    mbar_wait(&S.mbar[(seq + n0) % kSlots], ((seq + n0) / kSlots) & 1u, a.status);
+                    if (n1 < R) mbar_wait(&S.mbar[(seq + n1) % kSlots], ((seq + n1) / kSlots) & 1u, a.status);
+                } else if (g + gridDim.x < total) {
+                    mbar_wait(&S.mbar[(seq + R) % kSlots], ((seq + R) / kSlots) & 1u, a.status);
                 }
             }
-            if (tid < nw) {  // at most one sample of each kind per word (K >= 256)
-                const uint32_t kl = a.k_log2;
-                const uint64_t g1 = E + pre1, g0 = (t0 - E) + pre0;  // ones / zeros before the word
-                const uint64_t base = t0 + 32ull * tid;
-                if (((g1 + c1) >> kl) != (g1 >> kl)) {
-                    const uint64_t m = (g1 + c1) >> kl;
-                    if (m < a.n_s1) a.s1[m] = base + select_in_word(m1, (uint32_t)((m << kl) - g1));
-                }
-                if (((g0 + c0) >> kl) != (g0 >> kl)) {
-                    const uint64_t m = (g0 + c0) >> kl;
-                    if (m < a.n_s0) a.s0[m] = base + select_in_word(m0, (uint32_t)((m << kl) - g0));
-                }
-            }
-            if (R == 1) {
-                seq += 1;
-                __syncthreads();
-                continue;
-            }
-
-            // ---- runs of the tile in T_{l+1} ----
-            S.b[tid] = m1;
-            S.pre[tid] = pre1;
-            const uint64_t lim = a.size_next;
-            const uint64_t p0 = S.p0;
-            single = p0 + 1 >= a.nnodes || __ldg(&a.nodes[p0 + 1].start) >= t0 + count;
-            if (single) {
-                // each run's image is aligned with its output words (image word k0 mod 4
-                // holds output word k0), so whole words leave by bulk copy
-                const uint64_t d0 = __ldg(&a.nodes[p0].off0) + (t0 - E);
-                const uint64_t d1 = __ldg(&a.nodes[p0].off1) + E;
-                qz = ((uint32_t)d0 & 127u) + pre0;
-                qo = ((uint32_t)d1 & 127u) + pre1;
-                if (tid == 0) S.run[0] = plan_run(d0, count - O, lim);
-                if (tid == 8) S.run[1] = plan_run(d1, O, lim);
-                thr[0] = (uint32_t)umin64(((d0 / kTile) + 1) * kTile - d0, count - O);
-                thr[1] = d0 >= lim ? 0u : (uint32_t)umin64(count - O, lim - d0);
-                thr[2] = (uint32_t)umin64(((d1 / kTile) + 1) * kTile - d1, O);
-                thr[3] = d1 >= lim ? 0u : (uint32_t)umin64(O, lim - d1);
-            } else {
-                // several nodes: images start at bit 32 and runs are shifted into place
-                qz = 32 + pre0;
-                qo = 32 + pre1;
-                if (tid == 0) {
-                    S.E = E;
-                    S.O = O;
-                }
-            }
-        }
-
-        // ---- planes 1..R-1 (plane j is ready: waited before the last barrier) ----
-        auto clear_input = [&](uint32_t j) {  // consumed: clear for reuse as an output
-            if (tid == 0) {
-                const uint32_t nw = (S.count + 31) / 32, bytes = (nw * 4 + 15) & ~15u;
-                bulk_s2g(a.in + (uint64_t)(j - 1) * a.pstride + (S.t0 >> 5), S.zero, bytes);
-            }
+            __syncthreads();
+            if (tid == 0) cursor_pump(cur, S, seq + j + (two ? 2 : 1), args, tile_prefix, ntrees, total);
+            write_plane<FIRST>(S, a, j, S.img[ps][0][0], S.img[ps][0][1], single, 32);
+            if (two) write_plane<false>(S, a, j + 1, S.img[ps][1][0], S.img[ps][1][1], single, 64);
+            if (bulk_thread) bulk_commit();
+            // the slot of the pair before last is free (its reads were waited before the last barrier)
+            uint4* z = reinterpret_cast<uint4*>(&S.img[(pair + 2) % kPairs][0][0][0]);
+            for (uint32_t i = tid; i < 2 * 2 * kImgWords / 4; i += kTileThreads) z[i] = make_uint4(0, 0, 0, 0);
+            pair++;
         };
-        clear_input(1);
-        move_plane<true>(S, a, 1, seq + 1, R, S.ring[(seq + 1) % kSlots][tid], m0, m1, mv0, mv1, qz, qo, c0, c1, pre0,
-                         pre1, single, thr);
-        for (uint32_t j = 2; j < R; j++) {
-            const uint32_t u = seq + j;
-            clear_input(j);
-            move_plane<false>(S, a, j, u, R, S.ring[u % kSlots][tid], m0, m1, mv0, mv1, qz, qo, c0, c1, pre0, pre1,
-                              single, thr);
-        }
+        do_pair(BoolTag<true>(), 1);
+        for (uint32_t j = 3; j < R; j += 2) do_pair(BoolTag<false>(), j);
         seq += R;
-        if (tid == 0 || tid == 8) bulk_wait_read<0>();
-        __syncthreads();
-        if (tid < 2 * kImgWords / 4) {
-            reinterpret_cast<uint4*>(&S.img[(R - 1) & (kSets - 1)][0][0])[tid] = make_uint4(0, 0, 0, 0);
-            reinterpret_cast<uint4*>(&S.img[(R - 2) & (kSets - 1)][0][0])[tid] = make_uint4(0, 0, 0, 0);
-        }
     }
-    if (tid == 0 || tid == 8) bulk_wait_all();
+    if (bulk_thread) bulk_wait_all();
+}
+
+// ===========================================================================
+// first node of every tile (levels with several nodes)
+// ===========================================================================
+
+// One thread per tile of every tree: the last internal node starting at or
+// before the tile's first position (binary search over the node starts).
+__global__ void __launch_bounds__(256) first_node_kernel(const LevelArgs* __restrict__ args,
+                                                         const uint64_t* __restrict__ tile_prefix, uint32_t ntrees) {
+    const uint64_t total = tile_prefix[ntrees];
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t tree = ntrees > 1 ? find_tree(tile_prefix, ntrees, g) : 0u;
+        const LevelArgs& a = args[tree];
+        if (a.R < 2 || a.nnodes < 2) continue;
+        const uint64_t tile = g - tile_prefix[tree];
+        const uint64_t t0 = tile * kTile;
+        uint64_t lo = 0, hi = a.nnodes - 1;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(&a.nodes[mid].start) <= t0) lo = mid;
+            else hi = mid - 1;
+        }
+        a.first_node[tile] = (uint32_t)lo;
+    }
 }
 
 // ===========================================================================
@@ -756,7 +825,7 @@ wt_status launch_transpose(const TransposeArgs* d_args, const uint64_t* d_chunk_
 }
 
 wt_status launch_level(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
-                       unsigned long long* counter, uint64_t max_tiles, cudaStream_t s) {
+                       uint64_t max_tiles, cudaStream_t s) {
     static int per_sm = 0;
     const size_t sm = sizeof(TileSmem);
     if (!per_sm) {
@@ -767,7 +836,15 @@ wt_status launch_level(const LevelArgs* d_args, const uint64_t* d_tile_prefix, u
     }
     const uint64_t grid = umin64(max_tiles ? max_tiles : 1, (uint64_t)per_sm * sm_count());
     ProfScope ps("level", s);
-    level_kernel<<<(unsigned)grid, kTileThreads, sm, s>>>(d_args, d_tile_prefix, ntrees, counter);
+    level_kernel<<<(unsigned)grid, kTileThreads, sm, s>>>(d_args, d_tile_prefix, ntrees);
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
+}
+
+wt_status launch_first_node(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
+                            uint64_t max_tiles, cudaStream_t s) {
+    const uint64_t grid = umin64((max_tiles + 255) / 256 + 1, (uint64_t)sm_count() * 8);
+    ProfScope ps("first_node", s);
+    first_node_kernel<<<(unsigned)grid, 256, 0, s>>>(d_args, d_tile_prefix, ntrees);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
