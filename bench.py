@@ -124,20 +124,6 @@ def level_pass_bytes(sizes, w, K):
     return out
 
 
-def plane_pass_bytes(n, w, sizes, K):
-    """Bytes this implementation moves per build in its level passes: the
-    transpose reads S and writes L bit planes; the rank pass of level l reads
-    B_l and writes counters, samples and per-tile prefixes; the move pass reads
-    the R = L - l planes of T_l and writes the R - 1 planes of T_{l+1}."""
-    L = len(sizes)
-    b = n * w + L * ((n + 7) // 8)
-    for l, sz in enumerate(sizes):
-        b += (sz + 7) // 8 + (sz // 65536 + 1) * 8 + (sz // 512 + 1) * 2 + (sz // K + 2) * 8 + (sz // 16384 + 1) * 12
-        if l + 1 < L:
-            b += (L - l) * ((sz + 7) // 8) + (L - l - 1) * ((sizes[l + 1] + 7) // 8)
-    return b
-
-
 def build_bytes(n, w, sizes, K):
     """Algorithmic bytes of the level-wise build: histogram read + every level pass."""
     return n * w + sum(level_pass_bytes(sizes, w, K))
@@ -322,23 +308,19 @@ def run_ours(args):
             ms = kern[kind]["ms"] / kern[kind]["launches"]
             phases[f"{kind}_ms"] = ms
             phases[f"{kind}_Mqps"] = q[qk].numel() / (ms * 1e-3) / 1e6
-    lp_kernels = [k for k in ("transpose", "count_scan", "level") if k in kern]
-    lp_ms = sum(kern[k]["ms"] for k in lp_kernels)
-    lp_name = "level passes (" + " + ".join(lp_kernels) + ")"
+    lp_name = {1: "level_pass_u8", 2: "level_pass_u16", 4: "level_pass_u32"}[w]
     cands = []
-    if lp_kernels:
-        cands.append((lp_ms, lp_name))
+    if lp_name in kern:
+        cands.append((kern[lp_name]["ms"], lp_name))
     for kind in ("access", "rank", "select", "mixed"):
         if kind in kern:
             cands.append((kern[kind]["ms"], kind))
     dom_ms, dom = max(cands)
-    own = plane_pass_bytes(wl.n, w, sizes, wl.sample_k)
+    nlaunch = kern[dom]["launches"]
     if dom == lp_name:
-        nlaunch = args.steps  # one set of level passes per build
-        per_launch_bytes = sum(lp_bytes)
+        per_launch_bytes = sum(lp_bytes) / len(lp_bytes)
         achieved = sum(lp_bytes) * args.steps / (dom_ms * 1e-3) / 1e9
     else:
-        nlaunch = kern[dom]["launches"]
         qk = {"access": "access_i", "rank": "rank_i", "select": "select_j", "mixed": "mixed_arg"}[dom]
         nq = q[qk].numel()
         sec = query_sectors(dom, L, code_len) if dom != "mixed" else statistics.mean(
@@ -347,18 +329,13 @@ def run_ours(args):
         achieved = per_launch_bytes * nlaunch / (dom_ms * 1e-3) / 1e9
     for k in list(kern):
         kern[k]["share"] = kern[k]["ms"] / max(sum(v["ms"] for v in kern.values()), 1e-9)
-    traffic = _measured_traffic(lp_kernels, wl.n, w, sizes) if dom == lp_name else None
+    traffic = _measured_traffic(dom, sum(sizes) / max(len(sizes), 1)) if dom == lp_name else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback 6.8 TB/s",
             "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": dom_ms / nlaunch, "traffic": traffic}
-    if lp_kernels:
-        # the level-wise method's bytes (read T_l, write B_l and T_{l+1} per level) are the fixed
-        # denominator; the bit-plane passes move fewer bytes, reported beside it
-        lp_gbs = sum(lp_bytes) * args.steps / (lp_ms * 1e-3) / 1e9
-        roof["level_passes_frac"] = lp_gbs / peak
-        roof["level_passes_own_bytes_per_build"] = own
-        roof["level_passes_own_frac"] = own * args.steps / (lp_ms * 1e-3) / 1e9 / peak
+    if lp_name in kern:
+        roof["level_pass_frac"] = (sum(lp_bytes) * args.steps / (kern[lp_name]["ms"] * 1e-3) / 1e9) / peak
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -443,24 +420,22 @@ def _learned_compare(wl, sym, q, outs, reps=3):
     return res
 
 
-def _measured_traffic(kernels, n, w, sizes):
-    """DRAM bytes of one build's level passes from the committed ncu summary
-    (profiles/traffic.json: bytes per input symbol of the same workload shape,
-    summed over the transpose, rank-pass and move-pass launches of one build),
-    scaled to n symbols; None if the kernels' source changed since the
-    counters were taken."""
+def _measured_traffic(kernel, symbols_per_launch):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
+    scaled by the symbols one launch processes; None if the kernel source changed
+    since the counters were taken."""
     import hashlib
 
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)["level_passes"]
+            rec = json.load(f)[kernel]
         with open(os.path.join(ROOT, rec["file"]), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except Exception:
         return None
-    if sha != rec["source_sha256_16"] or rec.get("symbol_bytes") != w or rec.get("levels") != len(sizes):
+    if sha != rec["source_sha256_16"]:
         return None
-    return rec["dram_bytes_per_symbol"] * n
+    return rec["dram_bytes_per_symbol"] * symbols_per_launch
 
 
 def _mean_code_len(wl, q, counts):

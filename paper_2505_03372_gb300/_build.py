@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwt.so")
-SOURCES = ["wt_build.cu", "wt_level.cu", "wt_query.cu", "wt_api.cu", "wt_learned.cu", "wt_batch.cu", "wt_noalloc.cu"]
-HEADERS = ["wt_common.cuh", "wt_device.cuh", "wt_internal.hpp", "wt_walk.cuh"]
+SOURCES = ["wt_build.cu", "wt_query.cu", "wt_api.cu", "wt_learned.cu", "wt_batch.cu", "wt_noalloc.cu"]
+HEADERS = ["wt_common.cuh", "wt_internal.hpp", "wt_walk.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -168,6 +168,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     uint32_t kl = 0;
     while ((1u << kl) < K) kl++;
     const uint32_t w = symbol_bytes;
+    const uint64_t te = batch_tile_elems(w);
 
     wt_batch_s* b = new wt_batch_s();
     b->magic = kBatchMagic;
@@ -194,30 +195,25 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     };
     const uint64_t o_info = take((uint64_t)ntrees * sizeof(BatchTreeInfo));
     const uint64_t o_desc = take((uint64_t)ntrees * sizeof(TreeDesc));
-    const uint64_t o_la = take((uint64_t)maxL * ntrees * sizeof(LevelArgs));
-    const uint64_t o_ta = take((uint64_t)ntrees * sizeof(TransposeArgs));
+    const uint64_t o_lpa = take((uint64_t)maxL * ntrees * sizeof(LevelPassArgs));
     const uint64_t o_tiles = take((uint64_t)maxL * ntrees * 8);
     const uint64_t o_tpre = take((uint64_t)maxL * (ntrees + 1) * 8);
     const uint64_t o_cnt = take((uint64_t)(maxL ? maxL : 1) * 8);
-    const uint64_t o_trpre = take((uint64_t)(ntrees + 1) * 8);
     const uint64_t o_cpre = take((uint64_t)(ntrees + 1) * 8);
     const uint64_t o_spre = take((uint64_t)(ntrees + 1) * 8);
     const uint64_t o_status = take((uint64_t)ntrees * 4);
-    uint64_t hist_total = 0, count_total = 0, words_total = 0;
+    uint64_t hist_total = 0, state_total = 0;
     for (uint32_t i = 0; i < ntrees; i++) {
         hist_total += al((uint64_t)h_sigma[i] * 8);
-        count_total += al(level_tiles(h_n[i]) * 4);
-        words_total += (uint64_t)cps[i].L * al(al((h_n[i] + 63) / 64 + 16, 16) * 8);
+        state_total += al(((h_n[i] + te - 1) / te) * 8);
     }
     const uint64_t o_hist = take(hist_total);
-    const uint64_t o_count = take(count_total);
-    const uint64_t o_words = take(words_total);  // every tree's level words, one region (cleared per run)
+    const uint64_t o_state = take(state_total);
     struct TreeOff {
-        uint64_t C, nodes, left, excl, planes[2], prefix, count, first;
+        uint64_t C, nodes, left, excl, tbuf[2];
         std::vector<uint64_t> words, l1, l2, s0, s1, walloc;
     };
     std::vector<TreeOff> to(ntrees);
-    uint64_t count_off = o_count, words_off = o_words;
     for (uint32_t i = 0; i < ntrees; i++) {
         const uint64_t n = h_n[i];
         const uint32_t L = cps[i].L;
@@ -227,18 +223,12 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
         t.nodes = take((nslots ? nslots : 1) * sizeof(NodeEntry));
         t.left = take((nslots ? nslots : 1) * 8);
         t.excl = take((nslots + 1) * 8);
-        const uint64_t set_bytes = (L > 1 ? (uint64_t)(L - 1) : 0) * plane_stride(n) * 4;
-        t.planes[0] = take(set_bytes);
-        t.planes[1] = take(L > 2 ? set_bytes : 0);
-        t.prefix = take(level_tiles(n) * 8);
-        t.first = take(level_tiles(n) * 4);
-        t.count = count_off;
-        count_off += al(level_tiles(n) * 4);
+        t.tbuf[0] = take(L > 1 ? n * w : 0);
+        t.tbuf[1] = take(L > 2 ? n * w : 0);
         for (uint32_t l = 0; l < L; l++) {
             const uint64_t wa = al((n + 63) / 64 + 16, 16);
             t.walloc.push_back(wa);
-            t.words.push_back(words_off);
-            words_off += al(wa * 8);
+            t.words.push_back(take(wa * 8));
             t.l1.push_back(take((n / kL1Bits + 1) * 8));
             t.l2.push_back(take((n / kL2Bits + 1) * 2));
             t.s0.push_back(take(((n >> kl) + 2) * 8));
@@ -260,13 +250,10 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     // ---- host-side descriptors ----
     std::vector<BatchTreeInfo> info(ntrees);
     b->h_desc.assign(ntrees, TreeDesc());
-    std::vector<LevelArgs> la((size_t)maxL * ntrees);
-    memset(la.data(), 0, la.size() * sizeof(LevelArgs));
-    std::vector<TransposeArgs> ta(ntrees);
-    memset(ta.data(), 0, ta.size() * sizeof(TransposeArgs));
-    std::vector<uint64_t> cpre(ntrees + 1, 0), spre(ntrees + 1, 0), trpre(ntrees + 1, 0);
-    uint64_t max_tiles = 0;
-    uint64_t hist_off = o_hist;
+    std::vector<LevelPassArgs> lpa((size_t)maxL * ntrees);
+    memset(lpa.data(), 0, lpa.size() * sizeof(LevelPassArgs));
+    std::vector<uint64_t> cpre(ntrees + 1, 0), spre(ntrees + 1, 0);
+    uint64_t hist_off = o_hist, state_off = o_state;
     for (uint32_t i = 0; i < ntrees; i++) {
         const uint64_t n = h_n[i];
         const uint32_t L = cps[i].L;
@@ -304,10 +291,8 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
         d.nodes = ti.nodes;
         d.C = ti.C;
         d.status = ti.status;
-        const uint64_t ps = plane_stride(n);
-        uint32_t* planes[2] = {reinterpret_cast<uint32_t*>(M + to[i].planes[0]), reinterpret_cast<uint32_t*>(M + to[i].planes[1])};
-        max_tiles += level_tiles(n);
-        uint32_t* count = reinterpret_cast<uint32_t*>(M + to[i].count);
+        uint64_t* state = reinterpret_cast<uint64_t*>(M + state_off);
+        state_off += al(((n + te - 1) / te) * 8);
         for (uint32_t l = 0; l < L; l++) {
             LevelDesc& v = d.lv[l];
             v.words = reinterpret_cast<uint64_t*>(M + to[i].words[l]);
@@ -315,41 +300,25 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
             v.l2 = reinterpret_cast<uint16_t*>(M + to[i].l2[l]);
             v.s0 = reinterpret_cast<uint64_t*>(M + to[i].s0[l]);
             v.s1 = reinterpret_cast<uint64_t*>(M + to[i].s1[l]);
-            LevelArgs& a = la[(size_t)l * ntrees + i];
-            const bool last = l + 1 == L;
-            a.bits = reinterpret_cast<const uint32_t*>(v.words);
-            a.in = planes[l & 1];
-            a.out0 = last ? nullptr : reinterpret_cast<uint32_t*>(M + to[i].words[l + 1]);
-            a.out = planes[(l + 1) & 1];
-            a.pstride = ps;
+            LevelPassArgs& a = lpa[(size_t)l * ntrees + i];
+            a.src = l == 0 ? h_symbols[i] : static_cast<const void*>(M + to[i].tbuf[(l - 1) & 1]);
+            a.dst = (l + 1 < L) ? static_cast<void*>(M + to[i].tbuf[l & 1]) : nullptr;
+            a.words_alloc = to[i].walloc[l];
+            a.words = const_cast<uint64_t*>(v.words);
             a.l1 = const_cast<uint64_t*>(v.l1);
             a.l2 = const_cast<uint16_t*>(v.l2);
             a.s0 = const_cast<uint64_t*>(v.s0);
             a.s1 = const_cast<uint64_t*>(v.s1);
             a.nodes = ti.nodes + ((1ull << l) - 1);
-            a.nnodes = internal_nodes(cps[i], l);
-            a.count = count;
-            a.prefix = reinterpret_cast<uint64_t*>(M + to[i].prefix);
-            a.next_count = count;
-            a.first_node = reinterpret_cast<uint32_t*>(M + to[i].first);
+            a.state = state;
             a.status = ti.status;
-            a.R = L - l;
+            a.level = l;
+            a.shift_bit = L - 1 - l;
+            a.pshift = L - l;
             a.k_log2 = kl;
+            a.ctab_n = 0;
+            a.cp = cps[i];
         }
-        if (L) {
-            TransposeArgs& x = ta[i];
-            x.sym = h_symbols[i];
-            x.n = n;
-            x.bits0 = reinterpret_cast<uint32_t*>(M + to[i].words[0]);
-            x.bits0_words = 2 * to[i].walloc[0];
-            x.planes = planes[0];
-            x.pstride = ps;
-            x.count = count;
-            x.sigma = h_sigma[i];
-            x.L = L;
-            x.pow2 = cps[i].pow2;
-        }
-        trpre[i + 1] = trpre[i] + (L ? transpose_chunks(2 * to[i].walloc[0]) : 0);
         cpre[i + 1] = cpre[i] + (n + kBatchChunk - 1) / kBatchChunk;
         spre[i + 1] = spre[i] + nslots;
     }
@@ -362,11 +331,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     bd.total_slots = spre[ntrees];
     bd.info = reinterpret_cast<BatchTreeInfo*>(M + o_info);
     bd.desc = reinterpret_cast<TreeDesc*>(M + o_desc);
-    bd.la = reinterpret_cast<LevelArgs*>(M + o_la);
-    bd.ta = reinterpret_cast<TransposeArgs*>(M + o_ta);
-    bd.tr_prefix = reinterpret_cast<uint64_t*>(M + o_trpre);
-    bd.total_tr_chunks = trpre[ntrees];
-    bd.max_tiles = max_tiles;
+    bd.lpa = reinterpret_cast<LevelPassArgs*>(M + o_lpa);
     bd.tiles = reinterpret_cast<uint64_t*>(M + o_tiles);
     bd.tile_prefix = reinterpret_cast<uint64_t*>(M + o_tpre);
     bd.counters = reinterpret_cast<unsigned long long*>(M + o_cnt);
@@ -374,17 +339,13 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     bd.slot_prefix = reinterpret_cast<uint64_t*>(M + o_spre);
     bd.hist_pool = reinterpret_cast<uint64_t*>(M + o_hist);
     bd.hist_bytes = hist_total;
-    bd.count_pool = reinterpret_cast<uint32_t*>(M + o_count);
-    bd.count_bytes = count_total;
-    bd.words_pool = reinterpret_cast<uint64_t*>(M + o_words);
-    bd.words_bytes = words_total;
+    bd.state_pool = reinterpret_cast<uint64_t*>(M + o_state);
+    bd.state_bytes = state_total;
     bd.status_pool = reinterpret_cast<uint32_t*>(M + o_status);
     bool ok = cudaMemcpy(bd.info, info.data(), ntrees * sizeof(BatchTreeInfo), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(bd.desc, b->h_desc.data(), ntrees * sizeof(TreeDesc), cudaMemcpyHostToDevice) == cudaSuccess &&
-              (la.empty() || cudaMemcpy(bd.la, la.data(), la.size() * sizeof(LevelArgs), cudaMemcpyHostToDevice) ==
-                                 cudaSuccess) &&
-              cudaMemcpy(bd.ta, ta.data(), ntrees * sizeof(TransposeArgs), cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(bd.tr_prefix, trpre.data(), trpre.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+              (lpa.empty() || cudaMemcpy(bd.lpa, lpa.data(), lpa.size() * sizeof(LevelPassArgs),
+                                         cudaMemcpyHostToDevice) == cudaSuccess) &&
               cudaMemcpy(bd.chunk_prefix, cpre.data(), cpre.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(bd.slot_prefix, spre.data(), spre.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;

@@ -25,10 +25,78 @@
 #include <algorithm>
 #include <vector>
 
-#include "wt_device.cuh"
 #include "wt_internal.hpp"
 
 namespace wt {
+
+// ===========================================================================
+// small device utilities
+// ===========================================================================
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1-D TMA bulk copy global -> shared, completion signalled on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// bit i of x -> bit 2i
+__device__ __forceinline__ uint64_t spread2(uint32_t x) {
+    uint64_t v = x;
+    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+// bit i (i < 16) of x -> bit 4i
+__device__ __forceinline__ uint64_t spread4(uint32_t x) {
+    uint64_t v = x & 0xFFFFu;
+    v = (v | (v << 24)) & 0x000000FF000000FFull;
+    v = (v | (v << 12)) & 0x000F000F000F000Full;
+    v = (v | (v << 6)) & 0x0303030303030303ull;
+    v = (v | (v << 3)) & 0x1111111111111111ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // ===========================================================================
 // 1. histogram + validation
@@ -233,13 +301,556 @@ __global__ void meta_kernel(const MetaArgs ma, uint32_t L, const uint64_t* __res
 }
 
 // ===========================================================================
-// 4. level passes: wt_level.cu (bit planes); the bounded look-back's self-test
+// 4. the fused level pass
 // ===========================================================================
+
+constexpr int kTileBytes = 32768;
+constexpr int kLpThreads = 512;
+constexpr int kLpBlocksPerSM = 3;
+constexpr uint64_t kFlagAgg = 1, kFlagIncl = 2;
+
+// look-back state word: flag (2 bits) | aggregate (19 bits) | inclusive prefix (43 bits)
+__device__ __forceinline__ uint64_t lb_pack(uint64_t flag, uint64_t agg, uint64_t incl) {
+    return flag | (agg << 2) | (incl << 21);
+}
+__device__ __forceinline__ uint64_t lb_flag(uint64_t s) { return s & 3u; }
+__device__ __forceinline__ uint64_t lb_agg(uint64_t s) { return (s >> 2) & ((1u << 19) - 1); }
+__device__ __forceinline__ uint64_t lb_incl(uint64_t s) { return s >> 21; }
+
+
+// 32-bit shared-memory addressing for the byte / half / word scatter stores
+__device__ __forceinline__ void sts_elem(uint32_t addr, uint8_t v) {
+    asm volatile("st.shared.u8 [%0], %1;" ::"r"(addr), "h"((unsigned short)v) : "memory");
+}
+__device__ __forceinline__ void sts_elem(uint32_t addr, uint16_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+}
+__device__ __forceinline__ void sts_elem(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Partition one group (32 lanes x 16 bytes) of a tile into the shared-memory
+// image: the lane's element with level bit b goes to slot A1 + (ones before it
+// in the lane) if b = 1, else to A0 + (zeros before it in the lane).  Slots of
+// two elements travel as a 16-bit pair.  For one-byte symbols
+// the in-word ranks come from byte-wise prefix counts of the level bits.
+template <typename T, bool FULL>
+__device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V, uint32_t m, uint32_t A0, uint32_t A1,
+                                              uint32_t j0, uint32_t count, uint32_t shift) {
+    constexpr int W = sizeof(T);
+    constexpr int EPW = 4 / W;
+    const uint32_t wv[4] = {V.x, V.y, V.z, V.w};
+    const uint32_t A0x2 = A0 * 0x00010001u, A1x2 = A1 * 0x00010001u;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint32_t w = wv[i];
+        const uint32_t jw = j0 + i * EPW;
+        // ones among the lane's earlier words
+        const uint32_t ci = (i == 0) ? 0u : __popc(m & ((1u << (i * EPW)) - 1u));
+        const uint32_t b1 = A1x2 + ci * 0x00010001u;                                 // one-slot base, paired
+        const uint32_t b0 = (A0x2 + (uint32_t)(i * EPW) * 0x00010001u) - ci * 0x00010001u;  // zero-slot base, paired
+        if (W == 1) {
+            // bytes of y: level bits of the word's 4 elements; pre: ones before each element
+            const uint32_t y = (w >> shift) & 0x01010101u;
+            const uint32_t pre = y * 0x01010100u;
+            const uint32_t sel = y * 0xFFu;
+            const uint32_t off = (pre & sel) | ((0x03020100u - pre) & ~sel);  // rank among same-bit elements
+            const uint32_t s01 = __byte_perm(sel, 0, 0x1100), s23 = __byte_perm(sel, 0, 0x3322);
+            const uint32_t I01 = ((b1 & s01) | (b0 & ~s01)) + __byte_perm(off, 0, 0x4140);
+            const uint32_t I23 = ((b1 & s23) | (b0 & ~s23)) + __byte_perm(off, 0, 0x4342);
+            if (FULL || jw + 0 < count) sts_elem(out + (I01 & 0xFFFFu), (T)w);
+            if (FULL || jw + 1 < count) sts_elem(out + (I01 >> 16), (T)(w >> 8));
+            if (FULL || jw + 2 < count) sts_elem(out + (I23 & 0xFFFFu), (T)(w >> 16));
+            if (FULL || jw + 3 < count) sts_elem(out + (I23 >> 16), (T)(w >> 24));
+        } else if (W == 2) {
+            const uint32_t bb = (m >> (2 * i)) & 3u;
+            const uint32_t sel = (bb & 1u ? 0x0000FFFFu : 0u) | (bb & 2u ? 0xFFFF0000u : 0u);
+            // second element: ones before it if it is a one, zeros before it otherwise
+            const uint32_t off = ((bb ^ (bb >> 1)) & 1u) ? 0u : 0x00010000u;
+            const uint32_t I = ((b1 & sel) | (b0 & ~sel)) + off;
+            if (FULL || jw + 0 < count) sts_elem(out + 2 * (I & 0xFFFFu), (T)w);
+            if (FULL || jw + 1 < count) sts_elem(out + 2 * (I >> 16), (T)(w >> 16));
+        } else {
+            const uint32_t bit = (m >> i) & 1u;
+            if (FULL || jw < count) sts_elem(out + 4 * ((bit ? b1 : b0) & 0xFFFFu), (T)w);
+        }
+    }
+}
+
+// Decoupled look-back over tiles, run by one full warp: publish this tile's
+// count of ones (as its inclusive prefix if it is tile 0), walk back over the
+// earlier tiles 32 at a time summing aggregates until an inclusive prefix is
+// found, then publish this tile's inclusive prefix.  Returns the ones before
+// the tile.  Every wait is bounded: after spin_cap polls the warp sets
+// kStTimeout in *status, counts the missing predecessor as zero and returns.
+__device__ __forceinline__ uint64_t lookback_warp(uint64_t* state, uint64_t tile, uint64_t ones, uint32_t* status,
+                                               uint32_t spin_cap) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) st_relaxed_u64(state + tile, tile == 0 ? lb_pack(kFlagIncl, ones, ones) : lb_pack(kFlagAgg, ones, 0));
+    uint64_t excl = 0;
+    if (tile == 0) return 0;
+    int64_t base = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    bool timed_out = false;
+    while (true) {
+        const int64_t idx = base - lane;
+        uint64_t st = idx >= 0 ? ld_relaxed_u64(state + idx) : lb_pack(kFlagIncl, 0, 0);
+        while (__any_sync(0xffffffffu, lb_flag(st) == 0)) {
+            if (++spins > spin_cap) {
+                timed_out = true;
+                if (lb_flag(st) == 0) st = lb_pack(kFlagIncl, 0, 0);
+                break;
+            }
+            __nanosleep(20);
+            if (lb_flag(st) == 0) st = ld_relaxed_u64(state + idx);
+        }
+        const uint32_t im = __ballot_sync(0xffffffffu, lb_flag(st) == kFlagIncl);
+        if (im) {
+            const int first = __ffs(im) - 1;
+            const uint64_t v = lane < first ? lb_agg(st) : (lane == first ? lb_incl(st) : 0);
+            excl += warp_sum_u64(v);
+            break;
+        }
+        excl += warp_sum_u64(lb_agg(st));
+        base -= 32;
+    }
+    if (lane == 0) {
+        if (timed_out) set_status(status, kStTimeout);
+        st_relaxed_u64(state + tile, lb_pack(kFlagIncl, ones, excl + ones));
+    }
+    return excl;
+}
 
 // Diagnostic: tile 1 looks back at a tile 0 that never publishes anything.
 __global__ void lookback_timeout_kernel(uint64_t* state, uint32_t* status, uint32_t spin_cap, uint64_t* out) {
     const uint64_t excl = lookback_warp(state, 1, 5, status, spin_cap);
     if (threadIdx.x == 0) *out = excl;
+}
+
+// One tile of one level pass (the phases below).  Called by every thread of the
+// CTA; returns whether the tile's load used the mbarrier (its parity flips).
+template <typename T, bool ENCODE>
+__device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const uint64_t tile, uint8_t* smem,
+                                                uint64_t* mbar_p, uint32_t mphase) {
+    constexpr int W = sizeof(T);
+    constexpr int VEPL = 16 / W;                // elements per lane per group (one uint4 per lane)
+    constexpr int EPW = 4 / W;                  // elements per 32-bit word
+    constexpr int TE = kTileBytes / W;          // elements per tile
+    constexpr int NG = kTileBytes / 512;        // groups per tile: one group = 32 lanes x 16 bytes
+    constexpr int NWARP = kLpThreads / 32;
+    constexpr int GPW = NG / NWARP;             // groups per warp in phase 1
+    constexpr int GE = 512 / W;                 // elements (= bits) per group
+    constexpr int GBYTES = GE / 8;              // bytes of level bits per group
+    constexpr int TPL1 = 65536 / TE;            // tiles per L1 block
+    constexpr int GPL2 = W;                     // groups per 512-bit L2 block
+    constexpr uint32_t EMASK = (W == 4) ? 0xFFFFFFFFu : ((1u << (8 * W)) - 1u);
+    constexpr uint32_t LOWB = (W == 1) ? 0x01010101u : (W == 2 ? 0x00010001u : 1u);  // bit 0 of every element
+    static_assert(NG % NWARP == 0 && NG <= 64, "tile shape");
+
+    uint4* in4 = reinterpret_cast<uint4*>(smem);
+    uint8_t* outb = smem + kTileBytes;
+    uint8_t* wbytes = smem + 2 * kTileBytes + 64;                               // level bits of the tile
+    uint32_t* rpre = reinterpret_cast<uint32_t*>(wbytes + kTileBytes / 8 / W);  // NG + 1
+    T* ctab = reinterpret_cast<T*>(rpre + 64 + 1);                              // code table (ENCODE, small sigma)
+
+    __shared__ uint64_t s_E, s_EL1, s_p;
+    __shared__ uint32_t s_single;
+    __shared__ uint32_t s_gcnt[64];
+    __shared__ uint32_t s_gnext;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t t0 = tile * TE;
+    const uint32_t count = (uint32_t)umin64((uint64_t)TE, a.size - t0);
+    const bool full = count == (uint32_t)TE;
+    const uint32_t bytes = count * W;
+    const uint32_t b16 = bytes & ~15u;
+    const uint8_t* srcb = reinterpret_cast<const uint8_t*>(a.src) + t0 * W;
+    const bool used_mbar = b16 != 0;
+
+    // ---- phase 0: tile -> shared memory (TMA bulk copy + ragged tail) ----
+    if (tid == 0 && b16) {
+        mbar_expect_tx(mbar_p, b16);
+        bulk_g2s(smem, srcb, b16, mbar_p);
+    }
+    for (uint32_t i = b16 + tid; i < bytes; i += kLpThreads) smem[i] = srcb[i];
+    if (b16) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(mbar_p, mphase)) {
+            if (++spins > kSpinCap) {
+                if (lane == 0) set_status(a.status, kStTimeout);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 1: level bits of every lane's 16 bytes -> shared memory ----
+    const uint32_t shift = a.shift_bit;
+#pragma unroll 1
+    for (int gg = 0; gg < GPW; gg++) {
+        const int g = warp * GPW + gg;
+        uint4 V = in4[g * 32 + lane];
+        const uint32_t j0 = g * GE + lane * VEPL;
+        uint32_t wv[4] = {V.x, V.y, V.z, V.w};
+        if (ENCODE) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                uint32_t nv = 0;
+#pragma unroll
+                for (int k = 0; k < EPW; k++) {
+                    const uint32_t e = (wv[i] >> (8 * W * k)) & EMASK;
+                    uint32_t code = 0;
+                    if (j0 + i * EPW + k < count) {
+                        if (a.ctab_n) {
+                            code = ctab[e < a.ctab_n ? e : 0];
+                        } else {
+                            uint32_t len;
+                            encode(a.cp, e, code, len);
+                        }
+                    }
+                    nv |= (code & EMASK) << (8 * W * k);
+                }
+                wv[i] = nv;
+            }
+            in4[g * 32 + lane] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+        uint32_t m = 0;  // bit k = level bit of the lane's element k
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint32_t y = (wv[i] >> shift) & LOWB;
+            uint32_t b;
+            if (W == 1) b = (y * 0x10204080u) >> 28;
+            else if (W == 2) b = (y | (y >> 15)) & 3u;
+            else b = y;
+            m |= b << (i * EPW);
+        }
+        if (!full) {
+            const uint32_t act = j0 < count ? min(count - j0, (uint32_t)VEPL) : 0u;
+            m &= act >= 32 ? 0xFFFFFFFFu : ((1u << act) - 1u);
+        }
+        if (W == 1) {
+            reinterpret_cast<uint16_t*>(wbytes + g * GBYTES)[lane] = (uint16_t)m;
+        } else if (W == 2) {
+            wbytes[g * GBYTES + lane] = (uint8_t)m;
+        } else {
+            const uint32_t x = m | (__shfl_down_sync(0xffffffffu, m, 1) << 4);
+            if ((lane & 1) == 0) wbytes[g * GBYTES + lane / 2] = (uint8_t)x;
+        }
+        const uint32_t gc = __reduce_add_sync(0xffffffffu, __popc(m));
+        if (lane == 0) s_gcnt[g] = gc;
+    }
+    if (tid == kLpThreads - 32) {
+        s_gnext = 0;
+        // does the tile lie inside one node of this level?
+        if (a.level == 0) {
+            s_single = 1;
+            s_p = 0;
+        } else {
+            const T* te = reinterpret_cast<const T*>(smem);
+            const uint64_t p0 = (uint64_t)te[0] >> a.pshift;
+            const uint64_t p1 = (uint64_t)te[count - 1] >> a.pshift;
+            s_single = p0 == p1;
+            s_p = p0;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2 (every warp, no barrier): exclusive scan of the 64 group counts ----
+    // lane l holds the prefixes of groups 2l and 2l+1
+    uint32_t rp0, rp1, ones32;
+    {
+        const uint32_t c0 = 2 * lane < NG ? s_gcnt[2 * lane] : 0u, c1 = 2 * lane + 1 < NG ? s_gcnt[2 * lane + 1] : 0u;
+        const uint32_t sum = c0 + c1;
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        rp0 = inc - sum;
+        rp1 = rp0 + c0;
+        ones32 = __shfl_sync(0xffffffffu, inc, 31);
+        if (warp == 1) {
+            if (2 * lane < NG) rpre[2 * lane] = rp0;
+            if (2 * lane + 1 < NG) rpre[2 * lane + 1] = rp1;
+            if (lane == 0) rpre[NG] = ones32;
+        }
+    }
+    const uint32_t Z = count - ones32;  // zeros of the tile
+
+    // ---- phase 3: look-back (warp 0) || level bits to global + partition into shared memory ----
+    // The shared-memory image holds the tile's zeros at out[0, Z) and its ones at
+    // out[Z, count), each in input order; it does not depend on the look-back.
+    T* out = reinterpret_cast<T*>(outb);
+    const uint32_t out_s = smem_addr(outb);
+    if (warp == 0) {
+        const uint64_t ones = ones32;
+        const uint64_t excl = lookback_warp(a.state, tile, ones, a.status, kSpinCap);
+        // ones before the enclosing L1 block
+        const uint32_t q = (uint32_t)(tile % TPL1);
+        uint64_t sub = 0;
+        if (q && lane < (int)q) sub = lb_agg(ld_relaxed_u64(a.state + tile - q + lane));
+        sub = warp_sum_u64(sub);
+        if (lane == 0) {
+            s_E = excl;
+            s_EL1 = excl - sub;
+        }
+    } else {
+        const uint32_t tw = tid - 32;
+        const uint32_t nw = (count + 63) / 64;
+        const uint64_t* wsrc = reinterpret_cast<const uint64_t*>(wbytes);
+        uint64_t* wdst = a.words + tile * (TE / 64);
+        for (uint32_t i = tw; i < nw; i += kLpThreads - 32) wdst[i] = wsrc[i];
+        if (tile == a.ntiles - 1) {
+            const uint64_t first_pad = (a.size + 63) / 64;
+            for (uint64_t i = first_pad + tw; i < a.words_alloc; i += kLpThreads - 32) a.words[i] = 0;
+        }
+    }
+    if (a.dst != nullptr) {
+        // groups are handed out dynamically; warp 0 joins once its look-back is done
+#pragma unroll 1
+        while (true) {
+            uint32_t g = 0;
+            if (lane == 0) g = atomicAdd(&s_gnext, 1u);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= (uint32_t)NG) break;
+            const uint4 V = in4[g * 32 + lane];
+            const uint32_t j0 = g * GE + lane * VEPL;
+            uint32_t m;
+            if (W == 1) m = reinterpret_cast<const uint16_t*>(wbytes + g * GBYTES)[lane];
+            else if (W == 2) m = wbytes[g * GBYTES + lane];
+            else m = (wbytes[g * GBYTES + lane / 2] >> ((lane & 1) * 4)) & 0xFu;
+            // ones before this lane's elements: group prefix + warp exclusive scan
+            const uint32_t c = __popc(m);
+            uint32_t inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const uint32_t gpre = __shfl_sync(0xffffffffu, (g & 1u) ? rp1 : rp0, g >> 1);
+            const uint32_t ob = gpre + inc - c;
+            if (full) scatter_group<T, true>(out_s, V, m, j0 - ob, Z + ob, j0, count, shift);
+            else scatter_group<T, false>(out_s, V, m, j0 - ob, Z + ob, j0, count, shift);
+        }
+    }
+    __syncthreads();
+
+    const uint64_t E = s_E, EL1 = s_EL1, ones = ones32;
+    const uint64_t zeros = Z;
+    const uint64_t R0 = t0 - E;  // zeros before the tile
+
+    // ---- phase 4: L1/L2 counters and select samples ----
+    {
+        const uint32_t nl2 = (count + 511) / 512;
+        for (uint32_t b = tid; b < nl2; b += kLpThreads)
+            a.l2[(t0 >> 9) + b] = (uint16_t)(E - EL1 + rpre[b * GPL2]);
+        if (tid == 0) {
+            if (tile % TPL1 == 0) a.l1[t0 >> 16] = E;
+            if (tile == a.ntiles - 1) {
+                const uint64_t end = t0 + count;
+                if ((end & 511) == 0) {
+                    if ((end & 65535) == 0) {
+                        a.l1[end >> 16] = E + ones;
+                        a.l2[end >> 9] = 0;
+                    } else {
+                        a.l2[end >> 9] = (uint16_t)(E + ones - EL1);
+                    }
+                }
+            }
+            if (tile == 0) {
+                a.s0[0] = 0;
+                a.s1[0] = 0;
+            }
+        }
+        const uint32_t kl = a.k_log2;
+        const uint64_t m1lo = (E >> kl) + 1, m1hi = (E + ones) >> kl;
+        const uint64_t m0lo = (R0 >> kl) + 1, m0hi = (R0 + zeros) >> kl;
+        const uint64_t ns1 = m1hi + 1 - m1lo, ns0 = m0hi + 1 - m0lo;
+        for (uint64_t idx = tid; idx < ns1 + ns0; idx += kLpThreads) {
+            const uint32_t b = idx < ns1;
+            const uint64_t m = b ? m1lo + idx : m0lo + (idx - ns1);
+            const uint32_t t = (uint32_t)((m << kl) - (b ? E : R0));  // 1-based rank within the tile
+            int lo = 0, hi = NG - 1;  // last group with fewer than t b-bits before it
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                uint32_t c = b ? rpre[mid] : (uint32_t)(mid * GE) - rpre[mid];
+                if (c < t) lo = mid;
+                else hi = mid - 1;
+            }
+            uint32_t tt = t - (b ? rpre[lo] : (uint32_t)(lo * GE) - rpre[lo]);
+            const uint64_t* gw = reinterpret_cast<const uint64_t*>(wbytes + lo * GBYTES);
+            uint32_t pin = 0;
+#pragma unroll 1
+            for (int k = 0; k < GE / 64; k++) {
+                uint64_t x = gw[k];
+                if (!b) x = ~x;
+                const uint32_t c = __popcll(x);
+                if (c >= tt) {
+                    pin = k * 64 + select_in_word(x, tt);
+                    break;
+                }
+                tt -= c;
+            }
+            if (m < (b ? a.n_s1 : a.n_s0)) (b ? a.s1 : a.s0)[m] = t0 + (uint64_t)lo * GE + pin;
+        }
+    }
+
+    if (a.dst == nullptr) return used_mbar;
+
+    // ---- phase 5: shared-memory image -> T_{l+1} ----
+    T* dst = reinterpret_cast<T*>(a.dst);
+    const uint64_t lim = a.size_next;
+    if (s_single != 0) {
+        // two contiguous runs: zeros to off0 + R0, ones to off1 + E.  Global 4-byte
+        // words are assembled from two shared words with a funnel shift.
+        const NodeEntry* ne = a.nodes + s_p;
+        const uint64_t D0 = __ldg(&ne->off0) + R0;
+        const uint64_t D1 = __ldg(&ne->off1) + E;
+#pragma unroll
+        for (int run = 0; run < 2; run++) {
+            const uint64_t D = run ? D1 : D0;
+            uint64_t len64 = run ? ones : zeros;
+            const uint32_t so = run ? Z : 0u;
+            if (D >= lim || len64 == 0) continue;
+            const uint32_t len = (uint32_t)umin64(len64, lim - D);
+            T* dr = dst + D;
+            if (W == 4) {
+                for (uint32_t i = tid; i < len; i += kLpThreads) dr[i] = out[so + i];
+                continue;
+            }
+            // element counts of the unaligned head, the 4-byte body and the tail
+            const uint32_t mis = (uint32_t)(D * W) & 3u;
+            const uint32_t head = min(len, mis ? (4u - mis) / W : 0u);
+            const uint32_t nbody = (len - head) * W / 4;
+            const uint32_t tail0 = head + nbody * (4 / W);
+            if (tid < head) dr[tid] = out[so + tid];
+            uint32_t* db = reinterpret_cast<uint32_t*>(dr + head);
+            const uint32_t sb0 = (so + head) * W;  // shared byte of the first body byte
+            // the shared/global byte shift is the same for the whole run; each lane
+            // reads one shared word and takes the next one from its neighbour lane
+            const uint32_t fs = (sb0 & 3u) * 8u, w0 = sb0 >> 2;
+            const uint32_t nb32 = (nbody + 31u) & ~31u;
+            for (uint32_t i = tid; i < nb32; i += kLpThreads) {
+                const uint32_t lo = lds_u32(out_s + 4 * (w0 + i));
+                uint32_t hi = __shfl_down_sync(0xffffffffu, lo, 1);
+                if (lane == 31) hi = lds_u32(out_s + 4 * (w0 + i + 1));
+                if (i < nbody) db[i] = __funnelshift_r(lo, hi, fs);
+            }
+            for (uint32_t i = tail0 + tid; i < len; i += kLpThreads) dr[i] = out[so + i];
+        }
+    } else {
+        // several nodes: every element finds its node's offsets from its own code
+        const uint32_t ps = a.pshift;
+        for (uint32_t i = tid; i < zeros; i += kLpThreads) {
+            const T x = out[i];
+            const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off0) + R0 + i;
+            if (Dx < lim) dst[Dx] = x;
+        }
+        for (uint32_t i = tid; i < ones; i += kLpThreads) {
+            const T x = out[Z + i];
+            const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off1) + E + i;
+            if (Dx < lim) dst[Dx] = x;
+        }
+    }
+    return used_mbar;
+}
+
+// Single tree: one CTA per tile, tiles taken in order from a counter.
+template <typename T, bool ENCODE>
+__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM)
+    level_pass_kernel(const __grid_constant__ LevelPassArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint64_t s_tile;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_tile = atomicAdd(a.counter, 1u);
+        mbar_init(&mbar, 1);
+        mbar_fence_init();
+    }
+    if (ENCODE && a.ctab_n) {
+        constexpr int W = sizeof(T);
+        T* ctab = reinterpret_cast<T*>(smem + 2 * kTileBytes + 64 + kTileBytes / 8 / W + (64 + 1) * 4);
+        for (uint32_t s = tid; s < a.ctab_n; s += kLpThreads) {
+            uint32_t code, len;
+            encode(a.cp, s, code, len);
+            ctab[s] = (T)code;
+        }
+    }
+    __syncthreads();
+    if (s_tile >= a.ntiles) return;
+    level_pass_tile<T, ENCODE>(a, s_tile, smem, &mbar, 0);
+}
+
+// Many trees: a persistent grid walks the concatenation of every tree's tiles
+// (tile_prefix[i] = tiles of trees before i), so each tree's tiles are taken in
+// order and its look-back only waits on running CTAs.  Codes are computed
+// arithmetically (no shared code table).
+template <typename T, bool ENCODE>
+__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM)
+    level_pass_batched_kernel(const LevelPassArgs* __restrict__ args, const uint64_t* __restrict__ tile_prefix,
+                              uint32_t ntrees, unsigned long long* __restrict__ counter) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint64_t s_g;
+    __shared__ uint32_t s_tree;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const uint64_t total = tile_prefix[ntrees];
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) {
+            const uint64_t g = atomicAdd(counter, 1ull);
+            s_g = g;
+            if (g < total) {
+                uint32_t lo = 0, hi = ntrees - 1;  // last tree whose first tile is <= g
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (tile_prefix[mid] <= g) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_tree = lo;
+            }
+        }
+        __syncthreads();
+        const uint64_t g = s_g;
+        if (g >= total) break;
+        const uint32_t tr = s_tree;
+        if (level_pass_tile<T, ENCODE>(args[tr], g - tile_prefix[tr], smem, &mbar, phase)) phase ^= 1u;
+        __syncthreads();
+    }
+}
+
+constexpr uint32_t kCodeTableBytes = 8192;
+
+template <typename T, bool ENC>
+static size_t level_pass_smem() {
+    constexpr int W = sizeof(T);
+    return 2 * kTileBytes + 64 + kTileBytes / 8 / W + (64 + 1) * 4 + (ENC ? kCodeTableBytes : 0);
+}
+
+template <typename T, bool ENC>
+static cudaError_t launch_level_pass(const LevelPassArgs& a, cudaStream_t s) {
+    static bool configured = false;
+    size_t sm = level_pass_smem<T, ENC>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<T, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    ProfScope ps(sizeof(T) == 1 ? "level_pass_u8" : (sizeof(T) == 2 ? "level_pass_u16" : "level_pass_u32"), s);
+    level_pass_kernel<T, ENC><<<(unsigned)a.ntiles, kLpThreads, sm, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -397,110 +1008,67 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         d.ones = t->level_ones[l];
     }
 
-    // ---- level kernels over bit planes (wt_level.cu) ----
+    // ---- level passes ----
     if (L && n) {
-        const uint64_t ps = plane_stride(n);
-        const uint64_t set_words = (uint64_t)(L - 1) * ps;  // planes 1..L-1 of T_0, the most any level has
-        const uint64_t ntile = level_tiles(n);
-        const uint64_t w0 = 2 * lay[0].walloc;               // 32-bit words of B_0
-        const uint64_t nchunks = transpose_chunks(w0);
-        size_t o = 0;
-        auto take = [&](size_t bytes) {
-            const size_t r = o;
-            o = align_up(o + std::max<size_t>(bytes, 8), 256);
-            return r;
-        };
-        const size_t o_set0 = take(set_words * 4);
-        const size_t o_set1 = take(L > 2 ? set_words * 4 : 0);
-        const size_t o_count = take(ntile * 4);
-        const size_t o_prefix = take(ntile * 8);
-        const size_t o_first = take(ntile * 4);
-        const size_t o_la = take(L * sizeof(LevelArgs));
-        const size_t o_ta = take(sizeof(TransposeArgs));
-        const size_t o_tp = take((L + 1) * 2 * 8);  // tile prefixes {0, tiles} per level + transpose
-        const size_t o_cnt = take(L * 8);
+        const uint64_t te = kTileBytes / w;
+        const uint64_t max_tiles = (n + te - 1) / te;
+        const uint64_t tbytes = align_up(n * w, 256);
+        const size_t b_state = align_up(max_tiles * 8, 256);
         void* work = nullptr;
-        if (dev_alloc(&work, o, s) != cudaSuccess) {
+        const size_t work_bytes = 2 * tbytes + b_state + 256;
+        if (dev_alloc(&work, work_bytes, s) != cudaSuccess) {
             dev_free(scratch, s);
             return WT_ENOMEM;
         }
         uint8_t* Wm = reinterpret_cast<uint8_t*>(work);
-        uint32_t* set[2] = {reinterpret_cast<uint32_t*>(Wm + o_set0), reinterpret_cast<uint32_t*>(Wm + o_set1)};
-        uint32_t* count = reinterpret_cast<uint32_t*>(Wm + o_count);
-        LevelArgs* d_la = reinterpret_cast<LevelArgs*>(Wm + o_la);
-        TransposeArgs* d_ta = reinterpret_cast<TransposeArgs*>(Wm + o_ta);
-        uint64_t* d_tp = reinterpret_cast<uint64_t*>(Wm + o_tp);
-        unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(Wm + o_cnt);
-
-        std::vector<LevelArgs> la(L);
-        std::vector<uint64_t> tp(2 * (L + 1), 0);  // pairs {0, tiles}
+        void* buf[2] = {Wm, Wm + tbytes};
+        uint64_t* state = reinterpret_cast<uint64_t*>(Wm + 2 * tbytes);
+        uint32_t* counters = reinterpret_cast<uint32_t*>(Wm + 2 * tbytes + b_state);
+        WT_CUDA_TRY(cudaMemsetAsync(counters, 0, 256, s));
         for (uint32_t l = 0; l < L; l++) {
-            LevelArgs& a = la[l];
+            const uint64_t size = t->level_size[l];
+            if (size == 0) continue;
+            LevelPassArgs a;
             memset(&a, 0, sizeof(a));
-            const bool last = l + 1 == L;
-            a.bits = reinterpret_cast<const uint32_t*>(M + lay[l].words);
-            a.in = set[l & 1];
-            a.out0 = last ? nullptr : reinterpret_cast<uint32_t*>(M + lay[l + 1].words);
-            a.out = set[(l + 1) & 1];
-            a.pstride = ps;
-            a.size = t->level_size[l];
-            a.size_next = last ? 0 : t->level_size[l + 1];
+            a.src = l == 0 ? d_symbols : buf[(l - 1) & 1];
+            a.dst = (l + 1 < L) ? buf[l & 1] : nullptr;
+            a.size = size;
+            a.size_next = (l + 1 < L) ? t->level_size[l + 1] : 0;
+            a.ntiles = (size + te - 1) / te;
+            a.words_alloc = lay[l].walloc;
+            a.words = reinterpret_cast<uint64_t*>(M + lay[l].words);
             a.l1 = reinterpret_cast<uint64_t*>(M + lay[l].l1);
             a.l2 = reinterpret_cast<uint16_t*>(M + lay[l].l2);
             a.s0 = reinterpret_cast<uint64_t*>(M + lay[l].s0);
             a.s1 = reinterpret_cast<uint64_t*>(M + lay[l].s1);
-            a.n_s0 = ((a.size - t->level_ones[l]) >> k_log2) + 1;
+            a.n_s0 = ((size - t->level_ones[l]) >> k_log2) + 1;
             a.n_s1 = (t->level_ones[l] >> k_log2) + 1;
             a.nodes = nodes + ((1ull << l) - 1);
-            a.nnodes = internal_nodes(cp, l);
-            a.count = count;
-            a.prefix = reinterpret_cast<uint64_t*>(Wm + o_prefix);
-            a.next_count = count;
-            a.first_node = reinterpret_cast<uint32_t*>(Wm + o_first);
+            a.state = state;
+            a.counter = counters + l;
             a.status = t->desc.status;
-            a.R = L - l;
+            a.level = l;
+            a.shift_bit = L - 1 - l;
+            a.pshift = L - l;
             a.k_log2 = k_log2;
-            tp[2 * l + 1] = level_tiles(a.size);
-        }
-        tp[2 * L + 1] = nchunks;
-        TransposeArgs ta;
-        memset(&ta, 0, sizeof(ta));
-        ta.sym = d_symbols;
-        ta.n = n;
-        ta.bits0 = reinterpret_cast<uint32_t*>(M + lay[0].words);
-        ta.bits0_words = w0;
-        ta.planes = set[0];
-        ta.pstride = ps;
-        ta.count = count;
-        ta.sigma = sigma;
-        ta.L = L;
-        ta.pow2 = cp.pow2;
-        WT_CUDA_TRY(cudaMemcpyAsync(d_la, la.data(), L * sizeof(LevelArgs), cudaMemcpyHostToDevice, s));
-        WT_CUDA_TRY(cudaMemcpyAsync(d_ta, &ta, sizeof(ta), cudaMemcpyHostToDevice, s));
-        WT_CUDA_TRY(cudaMemcpyAsync(d_tp, tp.data(), tp.size() * 8, cudaMemcpyHostToDevice, s));
-        WT_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, L * 8, s));
-        // outputs are ORed into where two runs share a word: they start at zero
-        WT_CUDA_TRY(cudaMemsetAsync(t->lvl_mem, 0, t->lvl_bytes, s));
-        if (L > 2) WT_CUDA_TRY(cudaMemsetAsync(set[1], 0, set_words * 4, s));
-        WT_CUDA_TRY(cudaMemsetAsync(count, 0, ntile * 4, s));
-        wt_status st = launch_transpose(d_ta, d_tp + 2 * L, 1, nchunks, w, s);
-        for (uint32_t l = 0; l < L && st == WT_OK; l++) {
-            if (t->level_size[l] == 0) continue;
-            st = launch_count_scan(d_la + l, 1, s);
-            if (st == WT_OK && l + 1 < L && cudaMemsetAsync(count, 0, ntile * 4, s) != cudaSuccess) st = WT_ECUDA;
-            if (st == WT_OK && l + 1 < L && la[l].nnodes > 1)
-                st = launch_first_node(d_la + l, d_tp + 2 * l, 1, tp[2 * l + 1], s);
-            if (st == WT_OK) st = launch_level(d_la + l, d_tp + 2 * l, 1, tp[2 * l + 1], s);
+            a.cp = cp;
+            a.ctab_n = ((uint64_t)sigma * w <= kCodeTableBytes) ? sigma : 0;
+            WT_CUDA_TRY(cudaMemsetAsync(state, 0, a.ntiles * 8, s));
+            const bool enc = (l == 0) && !cp.pow2;
+            cudaError_t e;
+            if (w == 1) e = enc ? launch_level_pass<uint8_t, true>(a, s) : launch_level_pass<uint8_t, false>(a, s);
+            else if (w == 2) e = enc ? launch_level_pass<uint16_t, true>(a, s) : launch_level_pass<uint16_t, false>(a, s);
+            else e = enc ? launch_level_pass<uint32_t, true>(a, s) : launch_level_pass<uint32_t, false>(a, s);
+            if (e != cudaSuccess) {
+                dev_free(work, s);
+                dev_free(scratch, s);
+                return WT_ECUDA;
+            }
         }
         dev_free(work, s);
-        if (st != WT_OK) {
-            dev_free(scratch, s);
-            return st;
-        }
-    }
-    // empty levels (no code reaches them) still need zero words and first counter / sample entries
-    for (uint32_t l = 0; l < L; l++) {
-        if (n == 0 || t->level_size[l] == 0) {
+    } else {
+        // empty levels still need their first counter / sample entries
+        for (uint32_t l = 0; l < L; l++) {
             WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].words, 0, lay[l].walloc * 8, s));
             WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].l1, 0, 8, s));
             WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].l2, 0, 2, s));
@@ -517,6 +1085,18 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
 // (every size the host would read back is computed on the device), so the
 // whole sequence can be captured in one CUDA graph
 // ===========================================================================
+
+uint64_t batch_tile_elems(uint32_t w) { return (uint64_t)kTileBytes / w; }
+
+__device__ __forceinline__ uint32_t find_tree(const uint64_t* prefix, uint32_t ntrees, uint64_t g) {
+    uint32_t lo = 0, hi = ntrees - 1;  // last tree whose first item is <= g
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 constexpr uint32_t kBatchSmemBins = 4096;
 
@@ -613,24 +1193,24 @@ __global__ void batch_node_finish_kernel(const BatchTreeInfo* __restrict__ info,
 }
 
 // one thread per (tree, level): level sizes and ones into the tree descriptors
-// and the level arguments; tiles per level
+// and the level-pass arguments; tiles per level
 __global__ void batch_meta_kernel(const BatchTreeInfo* __restrict__ info, TreeDesc* __restrict__ desc,
-                                  LevelArgs* __restrict__ la, uint64_t* __restrict__ tiles, uint32_t ntrees,
-                                  uint32_t maxL, uint32_t kl) {
+                                  LevelPassArgs* __restrict__ lpa, uint64_t* __restrict__ tiles, uint32_t ntrees,
+                                  uint32_t maxL, uint64_t te, uint32_t kl) {
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (uint64_t)ntrees * maxL) return;
     const uint32_t tr = (uint32_t)(g % ntrees), l = (uint32_t)(g / ntrees);
     const BatchTreeInfo& ti = info[tr];
-    uint64_t* rt = tiles + (uint64_t)l * ntrees + tr;
+    LevelPassArgs& a = lpa[(uint64_t)l * ntrees + tr];
     if (l >= ti.L || ti.n == 0) {
-        *rt = 0;
+        a.ntiles = 0;
+        tiles[(uint64_t)l * ntrees + tr] = 0;
         if (l < ti.L) {
             desc[tr].lv[l].size = 0;
             desc[tr].lv[l].ones = 0;
         }
         return;
     }
-    LevelArgs& a = la[(uint64_t)l * ntrees + tr];
     const uint64_t size = ti.C[ti.s0[l]];
     const uint64_t zeros = ti.excl[(2ull << l) - 1] - ti.excl[(1ull << l) - 1];
     const uint64_t ones = size - zeros;
@@ -638,9 +1218,10 @@ __global__ void batch_meta_kernel(const BatchTreeInfo* __restrict__ info, TreeDe
     desc[tr].lv[l].ones = ones;
     a.size = size;
     a.size_next = (l + 1 < ti.L) ? ti.C[ti.s0[l + 1]] : 0;
+    a.ntiles = (size + te - 1) / te;
     a.n_s0 = (zeros >> kl) + 1;
     a.n_s1 = (ones >> kl) + 1;
-    *rt = level_tiles(size);
+    tiles[(uint64_t)l * ntrees + tr] = a.ntiles;
 }
 
 // one CTA per level: exclusive scan of the trees' tile counts
@@ -657,14 +1238,28 @@ __global__ void __launch_bounds__(kScanThreads) batch_tile_scan_kernel(const uin
     if (threadIdx.x == 0) out[ntrees] = carry;
 }
 
+template <typename T, bool ENC>
+static cudaError_t launch_level_pass_batched(const BatchDev& b, uint32_t l, cudaStream_t s) {
+    static bool configured = false;
+    const size_t sm = level_pass_smem<T, ENC>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(level_pass_batched_kernel<T, ENC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int grid = sm_count() * (ENC ? kLpBlocksPerSM - 1 : kLpBlocksPerSM);
+    level_pass_batched_kernel<T, ENC><<<grid, kLpThreads, sm, s>>>(b.lpa + (uint64_t)l * b.ntrees,
+                                                                   b.tile_prefix + (uint64_t)l * (b.ntrees + 1),
+                                                                   b.ntrees, b.counters + l);
+    return cudaGetLastError();
+}
+
 wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kernels) {
     uint32_t nk = 0;
     WT_CUDA_TRY(cudaMemsetAsync(b.hist_pool, 0, b.hist_bytes, s));
     WT_CUDA_TRY(cudaMemsetAsync(b.status_pool, 0, (size_t)b.ntrees * 4, s));
-    WT_CUDA_TRY(cudaMemsetAsync(b.counters, 0, (size_t)(b.maxL ? b.maxL : 1) * 8, s));
-    // level outputs are ORed into where two runs share a word: they start at zero
-    WT_CUDA_TRY(cudaMemsetAsync(b.words_pool, 0, b.words_bytes, s));
-    WT_CUDA_TRY(cudaMemsetAsync(b.count_pool, 0, b.count_bytes, s));
+    WT_CUDA_TRY(cudaMemsetAsync(b.counters, 0, (size_t)b.maxL * 8, s));
     if (b.total_chunks) {
         nk++;
         if (b.w == 1) batch_hist_kernel<uint8_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
@@ -682,26 +1277,23 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
                                                                                         b.ntrees, b.total_slots);
     }
     if (b.maxL) {
+        const uint64_t te = batch_tile_elems(b.w);
         const uint64_t nm = (uint64_t)b.ntrees * b.maxL;
         nk += 2;
-        batch_meta_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(b.info, b.desc, b.la, b.tiles, b.ntrees, b.maxL,
-                                                                       b.k_log2);
+        batch_meta_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(b.info, b.desc, b.lpa, b.tiles, b.ntrees, b.maxL,
+                                                                       te, b.k_log2);
         batch_tile_scan_kernel<<<b.maxL, kScanThreads, 0, s>>>(b.tiles, b.tile_prefix, b.ntrees);
     }
     WT_CUDA_TRY(cudaGetLastError());
-    if (b.maxL && b.total_tr_chunks) {
-        if (launch_transpose(b.ta, b.tr_prefix, b.ntrees, b.total_tr_chunks, b.w, s) != WT_OK) return WT_ECUDA;
-        nk++;
-    }
     for (uint32_t l = 0; l < b.maxL; l++) {
-        const LevelArgs* la = b.la + (uint64_t)l * b.ntrees;
-        if (launch_count_scan(la, b.ntrees, s) != WT_OK) return WT_ECUDA;
-        WT_CUDA_TRY(cudaMemsetAsync(b.count_pool, 0, b.count_bytes, s));
-        if (launch_first_node(la, b.tile_prefix + (uint64_t)l * (b.ntrees + 1), b.ntrees, b.max_tiles, s) != WT_OK)
-            return WT_ECUDA;
-        if (launch_level(la, b.tile_prefix + (uint64_t)l * (b.ntrees + 1), b.ntrees, b.max_tiles, s) != WT_OK)
-            return WT_ECUDA;
-        nk += 3;
+        WT_CUDA_TRY(cudaMemsetAsync(b.state_pool, 0, b.state_bytes, s));
+        cudaError_t e;
+        const bool enc = l == 0;
+        if (b.w == 1) e = enc ? launch_level_pass_batched<uint8_t, true>(b, l, s) : launch_level_pass_batched<uint8_t, false>(b, l, s);
+        else if (b.w == 2) e = enc ? launch_level_pass_batched<uint16_t, true>(b, l, s) : launch_level_pass_batched<uint16_t, false>(b, l, s);
+        else e = enc ? launch_level_pass_batched<uint32_t, true>(b, l, s) : launch_level_pass_batched<uint32_t, false>(b, l, s);
+        if (e != cudaSuccess) return WT_ECUDA;
+        nk++;
     }
     if (kernels) *kernels = nk;
     return WT_OK;

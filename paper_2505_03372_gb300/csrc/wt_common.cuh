@@ -188,46 +188,29 @@ struct TreeDesc {
 };
 
 // Arguments of one level pass over one tree (see wt_build.cu).
-// Construction keeps T_l (S stably sorted by the first l code bits) as
-// R = L - l bit planes over its positions: plane j holds code bit L-1-(l+j) of
-// every element, so plane 0 is the level bitvector B_l itself.
-
-// One tree at one level: one kernel builds level l's counters and samples
-// from B_l and moves planes 1..R-1 of T_l into T_{l+1}.
-struct LevelArgs {
-    const uint32_t* bits;     // B_l = plane 0 of T_l: the level's words read as 32-bit words
-    uint32_t* in;             // planes 1..R-1 of T_l (plane j at in + (j - 1) * pstride); cleared as consumed
-    uint32_t* out0;           // B_{l+1} = plane 0 of T_{l+1} (the next level's words, zero); null at the last level
-    uint32_t* out;            // planes 1..R-2 of T_{l+1} (zero); plane j at out + (j - 1) * pstride
-    uint64_t pstride;         // 32-bit words per plane, a multiple of one tile (512)
-    uint64_t size;            // size_l
-    uint64_t size_next;       // size_{l+1}
+struct LevelPassArgs {
+    const void* src;   // T_l
+    void* dst;         // T_{l+1}, or null at the last level
+    uint64_t size;     // size_l
+    uint64_t size_next;
+    uint64_t ntiles;
+    uint64_t words_alloc;
+    uint64_t* words;
     uint64_t* l1;
     uint16_t* l2;
     uint64_t* s0;
     uint64_t* s1;
-    uint64_t n_s0, n_s1;      // allocated sample entries (writes beyond are dropped)
-    const NodeEntry* nodes;   // level-l slice of the node table
-    uint64_t nnodes;          // internal nodes at level l; they come first and their starts increase
-    uint32_t* count;          // per tile: ones of B_l in it
-    uint64_t* prefix;         // per tile: ones of B_l before it (exclusive scan of count)
-    uint32_t* next_count;     // per tile of level l+1: ones of B_{l+1}, accumulated here (zeroed before)
-    uint32_t* first_node;     // per tile: node holding its first position (levels with several nodes)
+    uint64_t n_s0, n_s1;     // allocated sample entries (writes beyond are dropped)
+    const NodeEntry* nodes;  // level-l slice of the node table
+    uint64_t* state;         // ntiles look-back words, zeroed
+    uint32_t* counter;       // tile counter, zeroed
     uint32_t* status;
-    uint32_t R;               // planes of T_l (L - l)
+    uint32_t level;
+    uint32_t shift_bit;  // L - 1 - l
+    uint32_t pshift;     // L - l (prefix = code >> pshift), unused at level 0
     uint32_t k_log2;
-};
-
-// Level 0: S -> the L planes of T_0 (plane 0 into B_0, planes 1..L-1 into in-planes).
-struct TransposeArgs {
-    const void* sym;
-    uint64_t n;
-    uint32_t* bits0;          // B_0 as 32-bit words
-    uint64_t bits0_words;     // 32-bit words of B_0 to write (zeros past n)
-    uint32_t* planes;         // planes 1..L-1; plane j at planes + (j - 1) * pstride
-    uint64_t pstride;
-    uint32_t* count;          // per tile of level 0: ones of B_0 (zeroed before)
-    uint32_t sigma, L, pow2;
+    uint32_t ctab_n;     // level 0 re-encoding: table size (0 = compute codes arithmetically)
+    CodeParams cp;       // used when re-encoding at level 0
 };
 
 // Learned select (wt_train_select): per level and bit value b, the position of

@@ -75,44 +75,26 @@ struct BatchTreeInfo {
 
 struct BatchDev {
     uint32_t ntrees, w, maxL, k_log2;
-    uint64_t total_chunks, total_slots, total_tr_chunks;
-    uint64_t max_tiles;              // upper bound of a level's tiles over all trees (grid size)
+    uint64_t total_chunks, total_slots;
     BatchTreeInfo* info;
     TreeDesc* desc;
-    LevelArgs* la;                   // [maxL][ntrees]
-    TransposeArgs* ta;               // [ntrees]
+    LevelPassArgs* lpa;              // [maxL][ntrees]
     uint64_t* tiles;                 // [maxL][ntrees]
     uint64_t* tile_prefix;           // [maxL][ntrees + 1]
     unsigned long long* counters;    // [maxL]
-    uint32_t* count_pool;            // per-tile counts of every tree (zeroed before each level)
-    size_t count_bytes;
-    uint64_t* words_pool;            // every tree's level words (zeroed before a run)
-    size_t words_bytes;
     uint64_t* chunk_prefix;          // [ntrees + 1] histogram chunks per tree
     uint64_t* slot_prefix;           // [ntrees + 1] node slots per tree
-    uint64_t* tr_prefix;             // [ntrees + 1] transpose chunks per tree
     uint64_t* hist_pool;
     size_t hist_bytes;
+    uint64_t* state_pool;
+    size_t state_bytes;
     uint32_t* status_pool;           // [ntrees]
 };
 
 constexpr uint64_t kBatchChunk = 65536;  // symbols per histogram work item
 
 wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kernels);
-
-// ---- level passes over bit planes (wt_level.cu) ----
-constexpr uint32_t kTile = 16384;  // positions per tile of a level kernel
-__host__ __device__ inline uint64_t level_tiles(uint64_t size) { return (size + kTile - 1) / kTile; }
-uint64_t transpose_chunks(uint64_t words32);
-uint64_t plane_stride(uint64_t n);         // 32-bit words per plane for n elements
-uint64_t internal_nodes(const CodeParams& cp, uint32_t l);
-wt_status launch_transpose(const TransposeArgs* d_args, const uint64_t* d_chunk_prefix, uint32_t ntrees,
-                           uint64_t chunks, uint32_t w, cudaStream_t s);
-wt_status launch_level(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
-                       uint64_t max_tiles, cudaStream_t s);
-wt_status launch_first_node(const LevelArgs* d_args, const uint64_t* d_tile_prefix, uint32_t ntrees,
-                            uint64_t max_tiles, cudaStream_t s);
-wt_status launch_count_scan(const LevelArgs* d_args, uint32_t ntrees, cudaStream_t s);
+uint64_t batch_tile_elems(uint32_t w);
 
 // ---- queries (wt_query.cu) ----
 wt_status launch_access(const wt_tree_s* t, const uint64_t* d_i, uint32_t* d_out, uint64_t q, cudaStream_t s);
