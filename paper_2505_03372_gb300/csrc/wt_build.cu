@@ -51,14 +51,15 @@ __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
+// try_wait that suspends the thread for up to 1 us while the phase is open
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(1000u)
         : "memory");
     return ok != 0;
 }
@@ -328,6 +329,26 @@ __device__ __forceinline__ void sts_elem(uint32_t addr, uint16_t v) {
 __device__ __forceinline__ void sts_elem(uint32_t addr, uint32_t v) {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint4 lds_u128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+// Bytes 4q + fs/8 .. 4q + fs/8 + 15 of the 32 bytes x:y (q < 4, fs a multiple of 8 below 32).
+__device__ __forceinline__ uint4 shift16(const uint4 x, const uint4 y, uint32_t q, uint32_t fs) {
+    const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    switch (q) {
+        case 0: return make_uint4(__funnelshift_r(w[0], w[1], fs), __funnelshift_r(w[1], w[2], fs),
+                                  __funnelshift_r(w[2], w[3], fs), __funnelshift_r(w[3], w[4], fs));
+        case 1: return make_uint4(__funnelshift_r(w[1], w[2], fs), __funnelshift_r(w[2], w[3], fs),
+                                  __funnelshift_r(w[3], w[4], fs), __funnelshift_r(w[4], w[5], fs));
+        case 2: return make_uint4(__funnelshift_r(w[2], w[3], fs), __funnelshift_r(w[3], w[4], fs),
+                                  __funnelshift_r(w[4], w[5], fs), __funnelshift_r(w[5], w[6], fs));
+        default: return make_uint4(__funnelshift_r(w[3], w[4], fs), __funnelshift_r(w[4], w[5], fs),
+                                   __funnelshift_r(w[5], w[6], fs), __funnelshift_r(w[6], w[7], fs));
+    }
+}
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
     uint32_t v;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
@@ -478,7 +499,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
         bulk_g2s(smem, srcb, b16, mbar_p);
     }
     for (uint32_t i = b16 + tid; i < bytes; i += kLpThreads) smem[i] = srcb[i];
-    if (b16) {
+    if (b16 && warp == 0) {  // one warp waits; the barrier hands the tile to all
         uint32_t spins = 0;
         while (!mbar_try_wait(mbar_p, mphase)) {
             if (++spins > kSpinCap) {
@@ -668,36 +689,30 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
                 a.s1[0] = 0;
             }
         }
+        // one 64-bit word of the tile's bits per thread: a sample falls in the word
+        // when the count of b-bits crosses a multiple of K there (at most once, K >= 256)
         const uint32_t kl = a.k_log2;
-        const uint64_t m1lo = (E >> kl) + 1, m1hi = (E + ones) >> kl;
-        const uint64_t m0lo = (R0 >> kl) + 1, m0hi = (R0 + zeros) >> kl;
-        const uint64_t ns1 = m1hi + 1 - m1lo, ns0 = m0hi + 1 - m0lo;
-        for (uint64_t idx = tid; idx < ns1 + ns0; idx += kLpThreads) {
-            const uint32_t b = idx < ns1;
-            const uint64_t m = b ? m1lo + idx : m0lo + (idx - ns1);
-            const uint32_t t = (uint32_t)((m << kl) - (b ? E : R0));  // 1-based rank within the tile
-            int lo = 0, hi = NG - 1;  // last group with fewer than t b-bits before it
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                uint32_t c = b ? rpre[mid] : (uint32_t)(mid * GE) - rpre[mid];
-                if (c < t) lo = mid;
-                else hi = mid - 1;
+        constexpr uint32_t WPG = GE / 64;  // words per group
+        const uint64_t* w64 = reinterpret_cast<const uint64_t*>(wbytes);
+        for (uint32_t t = tid; t * 64 < count; t += kLpThreads) {
+            const uint64_t x = w64[t];
+            const uint32_t g = t / WPG;
+            uint32_t pre = rpre[g];  // ones of the tile before word t
+            for (uint32_t k = g * WPG; k < t; k++) pre += __popcll(w64[k]);
+            const uint32_t nv = count - t * 64;
+            const uint64_t valid = nv >= 64 ? ~0ull : ((1ull << nv) - 1ull);
+            const uint64_t z = ~x & valid;
+            const uint64_t g1 = E + pre, g0 = R0 + (uint64_t)t * 64 - pre;  // ones / zeros before the word
+            const uint32_t c1 = __popcll(x), c0 = __popcll(z);
+            const uint64_t base = t0 + (uint64_t)t * 64;
+            if (((g1 + c1) >> kl) != (g1 >> kl)) {
+                const uint64_t m = (g1 + c1) >> kl;
+                if (m < a.n_s1) a.s1[m] = base + select_in_word(x, (uint32_t)((m << kl) - g1));
             }
-            uint32_t tt = t - (b ? rpre[lo] : (uint32_t)(lo * GE) - rpre[lo]);
-            const uint64_t* gw = reinterpret_cast<const uint64_t*>(wbytes + lo * GBYTES);
-            uint32_t pin = 0;
-#pragma unroll 1
-            for (int k = 0; k < GE / 64; k++) {
-                uint64_t x = gw[k];
-                if (!b) x = ~x;
-                const uint32_t c = __popcll(x);
-                if (c >= tt) {
-                    pin = k * 64 + select_in_word(x, tt);
-                    break;
-                }
-                tt -= c;
+            if (((g0 + c0) >> kl) != (g0 >> kl)) {
+                const uint64_t m = (g0 + c0) >> kl;
+                if (m < a.n_s0) a.s0[m] = base + select_in_word(z, (uint32_t)((m << kl) - g0));
             }
-            if (m < (b ? a.n_s1 : a.n_s0)) (b ? a.s1 : a.s0)[m] = t0 + (uint64_t)lo * GE + pin;
         }
     }
 
@@ -720,28 +735,20 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             if (D >= lim || len64 == 0) continue;
             const uint32_t len = (uint32_t)umin64(len64, lim - D);
             T* dr = dst + D;
-            if (W == 4) {
-                for (uint32_t i = tid; i < len; i += kLpThreads) dr[i] = out[so + i];
-                continue;
-            }
-            // element counts of the unaligned head, the 4-byte body and the tail
-            const uint32_t mis = (uint32_t)(D * W) & 3u;
-            const uint32_t head = min(len, mis ? (4u - mis) / W : 0u);
-            const uint32_t nbody = (len - head) * W / 4;
-            const uint32_t tail0 = head + nbody * (4 / W);
+            // element counts of the unaligned head, the 16-byte body and the tail
+            const uint32_t mis = (uint32_t)(D * W) & 15u;
+            const uint32_t head = min(len, mis ? (16u - mis) / W : 0u);
+            const uint32_t nb16 = (len - head) * W / 16;
+            const uint32_t tail0 = head + nb16 * (16 / W);
             if (tid < head) dr[tid] = out[so + tid];
-            uint32_t* db = reinterpret_cast<uint32_t*>(dr + head);
+            uint4* db = reinterpret_cast<uint4*>(dr + head);
+            // the shared/global byte shift is the same for the whole run: every
+            // global 16-byte unit is cut from two aligned shared 16-byte units
             const uint32_t sb0 = (so + head) * W;  // shared byte of the first body byte
-            // the shared/global byte shift is the same for the whole run; each lane
-            // reads one shared word and takes the next one from its neighbour lane
-            const uint32_t fs = (sb0 & 3u) * 8u, w0 = sb0 >> 2;
-            const uint32_t nb32 = (nbody + 31u) & ~31u;
-            for (uint32_t i = tid; i < nb32; i += kLpThreads) {
-                const uint32_t lo = lds_u32(out_s + 4 * (w0 + i));
-                uint32_t hi = __shfl_down_sync(0xffffffffu, lo, 1);
-                if (lane == 31) hi = lds_u32(out_s + 4 * (w0 + i + 1));
-                if (i < nbody) db[i] = __funnelshift_r(lo, hi, fs);
-            }
+            const uint32_t src0 = out_s + (sb0 & ~15u);
+            const uint32_t q = (sb0 >> 2) & 3u, fs = (sb0 & 3u) * 8u;
+            for (uint32_t i = tid; i < nb16; i += kLpThreads)
+                db[i] = shift16(lds_u128(src0 + 16 * i), lds_u128(src0 + 16 * i + 16), q, fs);
             for (uint32_t i = tail0 + tid; i < len; i += kLpThreads) dr[i] = out[so + i];
         }
     } else {
