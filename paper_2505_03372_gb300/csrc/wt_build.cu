@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint64_t
 }
 
 // tmp must hold ceil(count / kScanChunk) + 1 + ceil(count / kScanChunk) + 1 entries
-static void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s) {
+void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s) {
     if (count <= (uint64_t)kScanChunk * 4) {
         ProfScope ps("scan_single", s);
         scan_single_kernel<<<1, kScanThreads, 0, s>>>(in, out, count);

@@ -51,6 +51,10 @@ void dev_free(void* p, cudaStream_t s);
 wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t w, uint32_t sample_k,
                      cudaStream_t s, wt_tree_s* t);
 
+// out[k] = sum of in[0..k) for k <= count (count + 1 entries); tmp holds
+// 2 * (ceil(count / 8192) + 1) entries
+void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s);
+
 // ---- learned select (wt_learned.cu) ----
 wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, uint32_t pairs, cudaStream_t s);
 wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out,

@@ -343,3 +343,36 @@ def test_bounded_wait_times_out_and_context_survives():
         i = np.arange(0, 50000, 7, dtype=np.uint64)
         assert np.array_equal(_u32(t.access(_dev(i, np.int64))), S[i.astype(np.int64)].astype(np.uint32))
         assert t.status_sync() == wt.WT_OK
+
+
+@pytest.mark.parametrize("name,n,nq", [("text", 1 << 27, 1 << 17), ("large_alphabet", 1 << 25, 1 << 17)])
+def test_large_batches_in_walk_order(name, n, nq):
+    """Batches of at least 2^16 queries on trees above 64 MB are walked in bucket
+    order (by position, or by code prefix and position / rank); every answer must
+    still land in its own slot and equal the definition, invalid queries included."""
+    w = workloads.WORKLOADS[name]
+    w = workloads.Workload(w.name, w.index, n, w.sigma, w.symbol_bytes, w.dist, w.zipf_s,
+                           {k: nq for k in w.queries}, w.sample_k)
+    sym = workloads.make_symbols(n, w.sigma, w.symbol_bytes, w.dist, w.zipf_s, seed=4242, device="cuda")
+    q = workloads.make_queries(w, sym, seed=4343)
+    S = _host(sym, w.symbol_bytes)
+    o1 = oracle.O1(S, w.sigma)
+    with wt.build(sym, w.sigma) as t:
+        assert t.info().tree_bytes >= 64 << 20
+        if "access_i" in q:
+            i = q["access_i"].clone()
+            i[:7] = n + torch.arange(7, device="cuda")  # out of range: sentinel in place
+            g = _u32(t.access(i))
+            ii = i.cpu().numpy()
+            want = np.full(ii.size, np.uint32(0xFFFFFFFF), np.uint32)
+            ok = ii < n
+            want[ok] = o1.access(ii[ok])
+            assert np.array_equal(g, want)
+            assert t.status_sync() == wt.WT_EQUERY
+            assert np.array_equal(_u64(t.rank(q["rank_c"], q["rank_i"])),
+                                  o1.rank(q["rank_c"].cpu().numpy(), q["rank_i"].cpu().numpy()))
+            assert np.array_equal(_u64(t.select(q["select_c"], q["select_j"])),
+                                  o1.select(q["select_c"].cpu().numpy(), q["select_j"].cpu().numpy()))
+        if "mixed_kind" in q:
+            _check_mixed(t, q["mixed_kind"], q["mixed_c"], q["mixed_arg"], o1)
+        assert t.status_sync() == wt.WT_OK
