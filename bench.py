@@ -300,9 +300,11 @@ def run_ours(args):
     code_len = _mean_code_len(wl, q, counts)
     L = len(sizes)
     kern = {k: v for k, v in rep.items()}
-    build_ms = sum(v["ms"] for k, v in kern.items() if k not in ("access", "rank", "select", "mixed")) / args.steps
+    qkern = ("access", "rank", "select", "mixed", "order_hist", "order_scan", "order_scatter")
+    build_ms = sum(v["ms"] for k, v in kern.items() if k not in qkern) / args.steps
     phases = {"build_ms": build_ms, "build_GBps": b_build / (build_ms * 1e-3) / 1e9,
               "build_input_GBps": wl.n * w / (build_ms * 1e-3) / 1e9}
+    phases["query_order_ms"] = sum(v["ms"] for k, v in kern.items() if k.startswith("order_")) / args.steps
     for kind, qk in (("access", "access_i"), ("rank", "rank_i"), ("select", "select_j"), ("mixed", "mixed_arg")):
         if kind in kern and kern[kind]["launches"]:
             ms = kern[kind]["ms"] / kern[kind]["launches"]

@@ -43,6 +43,7 @@ constexpr uint64_t kBatchMagic = 0x5754424154434831ull;
 namespace wt {
 
 constexpr int kBqMaxThreads = 512;
+__device__ const NodeCache kNoCache = {nullptr, 0};
 
 __global__ void __launch_bounds__(kBqMaxThreads) batch_query_kernel(const TreeDesc* __restrict__ desc, uint32_t ntrees,
                                                                     const uint32_t* __restrict__ qt,
@@ -63,15 +64,15 @@ __global__ void __launch_bounds__(kBqMaxThreads) batch_query_kernel(const TreeDe
         bool bad;
         if (kd == 0) {
             bad = x >= t.n;
-            if (!bad) r = do_access(t, x);
+            if (!bad) r = do_access(t, kNoCache, x);
         } else if (kd == 1) {
             const uint32_t c = __ldg(qc + k);
             bad = c >= t.cp.sigma || x > t.n;
-            if (!bad) r = do_rank(t, c, x);
+            if (!bad) r = do_rank(t, kNoCache, c, x);
         } else if (kd == 2) {
             const uint32_t c = __ldg(qc + k);
             bad = !select_valid(t, c, x);
-            if (!bad) r = do_select(t, c, x);
+            if (!bad) r = do_select(t, kNoCache, c, x);
         } else {
             bad = true;
         }

@@ -224,9 +224,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint64_t
 }
 
 // tmp must hold ceil(count / kScanChunk) + 1 + ceil(count / kScanChunk) + 1 entries
-void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s) {
+void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s,
+                           const char* name) {
     if (count <= (uint64_t)kScanChunk * 4) {
-        ProfScope ps("scan_single", s);
+        ProfScope ps(name, s);
         scan_single_kernel<<<1, kScanThreads, 0, s>>>(in, out, count);
         return;
     }
@@ -234,15 +235,15 @@ void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, ui
     uint64_t* part = tmp;
     uint64_t* part_ex = tmp + nb + 1;
     {
-        ProfScope ps("scan_partials", s);
+        ProfScope ps(name, s);
         scan_partials_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, count, part);
     }
     {
-        ProfScope ps("scan_single", s);
+        ProfScope ps(name, s);
         scan_single_kernel<<<1, kScanThreads, 0, s>>>(part, part_ex, nb);
     }
     {
-        ProfScope ps("scan_apply", s);
+        ProfScope ps(name, s);
         scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, count, part_ex);
     }
 }
@@ -770,7 +771,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
 
 // Single tree: one CTA per tile, tiles taken in order from a counter.
 template <typename T, bool ENCODE>
-__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM)
+__global__ void __launch_bounds__(kLpThreads, kLpBlocksPerSM)
     level_pass_kernel(const __grid_constant__ LevelPassArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -800,7 +801,7 @@ __global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpB
 // order and its look-back only waits on running CTAs.  Codes are computed
 // arithmetically (no shared code table).
 template <typename T, bool ENCODE>
-__global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpBlocksPerSM)
+__global__ void __launch_bounds__(kLpThreads, kLpBlocksPerSM)
     level_pass_batched_kernel(const LevelPassArgs* __restrict__ args, const uint64_t* __restrict__ tile_prefix,
                               uint32_t ntrees, unsigned long long* __restrict__ counter) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -840,18 +841,21 @@ __global__ void __launch_bounds__(kLpThreads, ENCODE ? kLpBlocksPerSM - 1 : kLpB
 
 constexpr uint32_t kCodeTableBytes = 8192;
 
-template <typename T, bool ENC>
-static size_t level_pass_smem() {
+// dynamic shared memory: input tile, image, level bits, group prefixes, and the
+// code table of level 0 (ctab_n codes, 0 when codes are computed)
+template <typename T>
+static size_t level_pass_smem(uint32_t ctab_n) {
     constexpr int W = sizeof(T);
-    return 2 * kTileBytes + 64 + kTileBytes / 8 / W + (64 + 1) * 4 + (ENC ? kCodeTableBytes : 0);
+    return 2 * kTileBytes + 64 + kTileBytes / 8 / W + (64 + 1) * 4 + ((ctab_n * W + 15) & ~15u);
 }
 
 template <typename T, bool ENC>
 static cudaError_t launch_level_pass(const LevelPassArgs& a, cudaStream_t s) {
     static bool configured = false;
-    size_t sm = level_pass_smem<T, ENC>();
+    const size_t sm = level_pass_smem<T>(ENC ? a.ctab_n : 0);
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<T, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<T, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)level_pass_smem<T>(ENC ? kCodeTableBytes / sizeof(T) : 0));
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -1248,14 +1252,14 @@ __global__ void __launch_bounds__(kScanThreads) batch_tile_scan_kernel(const uin
 template <typename T, bool ENC>
 static cudaError_t launch_level_pass_batched(const BatchDev& b, uint32_t l, cudaStream_t s) {
     static bool configured = false;
-    const size_t sm = level_pass_smem<T, ENC>();
+    const size_t sm = level_pass_smem<T>(0);
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(level_pass_batched_kernel<T, ENC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int grid = sm_count() * (ENC ? kLpBlocksPerSM - 1 : kLpBlocksPerSM);
+    const int grid = sm_count() * kLpBlocksPerSM;
     level_pass_batched_kernel<T, ENC><<<grid, kLpThreads, sm, s>>>(b.lpa + (uint64_t)l * b.ntrees,
                                                                    b.tile_prefix + (uint64_t)l * (b.ntrees + 1),
                                                                    b.ntrees, b.counters + l);

@@ -53,7 +53,8 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
 
 // out[k] = sum of in[0..k) for k <= count (count + 1 entries); tmp holds
 // 2 * (ceil(count / 8192) + 1) entries
-void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s);
+void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s,
+                           const char* name = "scan");
 
 // ---- learned select (wt_learned.cu) ----
 wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, uint32_t pairs, cudaStream_t s);

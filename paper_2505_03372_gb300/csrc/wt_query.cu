@@ -35,11 +35,13 @@ template <bool ORD>
 __global__ void __launch_bounds__(kQThreads) access_kernel(const __grid_constant__ TreeDesc t,
                                                            const uint64_t* __restrict__ qi,
                                                            const uint32_t* __restrict__ idx,
-                                                           uint32_t* __restrict__ out, uint64_t q) {
+                                                           uint32_t* __restrict__ out, uint64_t q, uint32_t slots) {
+    extern __shared__ ulonglong2 s_nodes[];
+    const NodeCache nc = load_node_cache(t, s_nodes, slots);
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < q; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i = __ldg(qi + k);
         const bool bad = i >= t.n;
-        out[ORD ? __ldg(idx + k) : k] = bad ? UINT32_MAX : do_access(t, i);
+        out[ORD ? __ldg(idx + k) : k] = bad ? UINT32_MAX : do_access(t, nc, i);
         flag_query_error(t, bad);
     }
 }
@@ -49,12 +51,14 @@ __global__ void __launch_bounds__(kQThreads) rank_kernel(const __grid_constant__
                                                          const uint32_t* __restrict__ qc,
                                                          const uint64_t* __restrict__ qi,
                                                          const uint32_t* __restrict__ idx,
-                                                         uint64_t* __restrict__ out, uint64_t q) {
+                                                         uint64_t* __restrict__ out, uint64_t q, uint32_t slots) {
+    extern __shared__ ulonglong2 s_nodes[];
+    const NodeCache nc = load_node_cache(t, s_nodes, slots);
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < q; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t c = __ldg(qc + k);
         const uint64_t i = __ldg(qi + k);
         const bool bad = c >= t.cp.sigma || i > t.n;
-        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : do_rank(t, c, i);
+        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : do_rank(t, nc, c, i);
         flag_query_error(t, bad);
     }
 }
@@ -64,12 +68,14 @@ __global__ void __launch_bounds__(kQThreads) select_kernel(const __grid_constant
                                                            const uint32_t* __restrict__ qc,
                                                            const uint64_t* __restrict__ qj,
                                                            const uint32_t* __restrict__ idx,
-                                                           uint64_t* __restrict__ out, uint64_t q) {
+                                                           uint64_t* __restrict__ out, uint64_t q, uint32_t slots) {
+    extern __shared__ ulonglong2 s_nodes[];
+    const NodeCache nc = load_node_cache(t, s_nodes, slots);
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < q; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t c = __ldg(qc + k);
         const uint64_t j = __ldg(qj + k);
         const bool bad = !select_valid(t, c, j);
-        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : do_select(t, c, j);
+        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : do_select(t, nc, c, j);
         flag_query_error(t, bad);
     }
 }
@@ -80,7 +86,9 @@ __global__ void __launch_bounds__(kQThreads) mixed_kernel(const __grid_constant_
                                                           const uint32_t* __restrict__ qc,
                                                           const uint64_t* __restrict__ qa,
                                                           const uint32_t* __restrict__ idx,
-                                                          uint64_t* __restrict__ out, uint64_t q) {
+                                                          uint64_t* __restrict__ out, uint64_t q, uint32_t slots) {
+    extern __shared__ ulonglong2 s_nodes[];
+    const NodeCache nc = load_node_cache(t, s_nodes, slots);
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < q; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t kd = __ldg(kind + k);
         const uint64_t x = __ldg(qa + k);
@@ -88,15 +96,15 @@ __global__ void __launch_bounds__(kQThreads) mixed_kernel(const __grid_constant_
         bool bad;
         if (kd == 0) {
             bad = x >= t.n;
-            if (!bad) r = do_access(t, x);
+            if (!bad) r = do_access(t, nc, x);
         } else if (kd == 1) {
             const uint32_t c = __ldg(qc + k);
             bad = c >= t.cp.sigma || x > t.n;
-            if (!bad) r = do_rank(t, c, x);
+            if (!bad) r = do_rank(t, nc, c, x);
         } else if (kd == 2) {
             const uint32_t c = __ldg(qc + k);
             bad = !select_valid(t, c, x);
-            if (!bad) r = do_select(t, c, x);
+            if (!bad) r = do_select(t, nc, c, x);
         } else {
             bad = true;
         }
@@ -220,7 +228,7 @@ static wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8
         ProfScope ps("order_hist", s);
         order_hist_kernel<<<(unsigned)nchunks, kOrdThreads, 0, s>>>(t->desc, ok, d_kind, d_c, d_a, q, hist, nchunks);
     }
-    device_exclusive_scan(hist, offs, nh, reinterpret_cast<uint64_t*>(M + o_tmp), s);
+    device_exclusive_scan(hist, offs, nh, reinterpret_cast<uint64_t*>(M + o_tmp), s, "order_scan");
     {
         ProfScope ps("order_scatter", s);
         order_scatter_kernel<<<(unsigned)nchunks, kOrdThreads, 0, s>>>(t->desc, ok, d_kind, d_c, d_a, q, offs, nchunks,
@@ -233,17 +241,31 @@ static wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8
 // launches
 // ---------------------------------------------------------------------------
 
+constexpr uint32_t kNodeCacheSlots = 2048;  // levels 0..10: 32 KB of {start, r0}
+
+static uint32_t cache_slots(const wt_tree_s* t) {
+    const uint32_t L = t->desc.cp.L;
+    const uint64_t nslots = L ? (1ull << L) - 1 : 0;
+    return (uint32_t)(nslots < kNodeCacheSlots ? nslots : kNodeCacheSlots);
+}
+
 template <typename K>
-static int grid_for(K kernel, uint64_t q) {
-    static int per_sm = 0;
-    if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kQThreads, 0);
-        if (per_sm <= 0) per_sm = 1;
-    }
+static int grid_for(K kernel, uint64_t q, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kQThreads, smem);
+    if (per_sm <= 0) per_sm = 1;
     uint64_t need = (q + kQThreads - 1) / kQThreads;
     uint64_t full = (uint64_t)per_sm * sm_count();
     return (int)(need < full ? need : full);
 }
+
+// launch a walk kernel with the node cache of the tree's top levels
+#define WALK_LAUNCH(kernel, t, q, s, ...)                                                             \
+    do {                                                                                              \
+        const uint32_t slots_ = cache_slots(t);                                                       \
+        const size_t sm_ = (size_t)slots_ * sizeof(ulonglong2);                                       \
+        kernel<<<grid_for(kernel, q, sm_), kQThreads, sm_, s>>>(t->desc, __VA_ARGS__, q, slots_);     \
+    } while (0)
 
 wt_status launch_access(const wt_tree_s* t, const uint64_t* d_i, uint32_t* d_out, uint64_t q, cudaStream_t s) {
     if (!q) return WT_OK;
@@ -252,14 +274,14 @@ wt_status launch_access(const wt_tree_s* t, const uint64_t* d_i, uint32_t* d_out
         wt_status st = order_queries(t, 0, nullptr, nullptr, d_i, q, s, o);
         if (st == WT_OK) {
             ProfScope ps("access", s);
-            access_kernel<true><<<grid_for(access_kernel<true>, q), kQThreads, 0, s>>>(t->desc, o.a, o.idx, d_out, q);
+            WALK_LAUNCH(access_kernel<true>, t, q, s, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
         if (o.mem) dev_free(o.mem, s);
         return st;
     }
     ProfScope ps("access", s);
-    access_kernel<false><<<grid_for(access_kernel<false>, q), kQThreads, 0, s>>>(t->desc, d_i, nullptr, d_out, q);
+    WALK_LAUNCH(access_kernel<false>, t, q, s, d_i, nullptr, d_out);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
@@ -271,14 +293,14 @@ wt_status launch_rank(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d
         wt_status st = order_queries(t, 1, nullptr, d_c, d_i, q, s, o);
         if (st == WT_OK) {
             ProfScope ps("rank", s);
-            rank_kernel<true><<<grid_for(rank_kernel<true>, q), kQThreads, 0, s>>>(t->desc, o.c, o.a, o.idx, d_out, q);
+            WALK_LAUNCH(rank_kernel<true>, t, q, s, o.c, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
         if (o.mem) dev_free(o.mem, s);
         return st;
     }
     ProfScope ps("rank", s);
-    rank_kernel<false><<<grid_for(rank_kernel<false>, q), kQThreads, 0, s>>>(t->desc, d_c, d_i, nullptr, d_out, q);
+    WALK_LAUNCH(rank_kernel<false>, t, q, s, d_c, d_i, nullptr, d_out);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
@@ -290,15 +312,14 @@ wt_status launch_select(const wt_tree_s* t, const uint32_t* d_c, const uint64_t*
         wt_status st = order_queries(t, 2, nullptr, d_c, d_j, q, s, o);
         if (st == WT_OK) {
             ProfScope ps("select", s);
-            select_kernel<true><<<grid_for(select_kernel<true>, q), kQThreads, 0, s>>>(t->desc, o.c, o.a, o.idx, d_out,
-                                                                                       q);
+            WALK_LAUNCH(select_kernel<true>, t, q, s, o.c, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
         if (o.mem) dev_free(o.mem, s);
         return st;
     }
     ProfScope ps("select", s);
-    select_kernel<false><<<grid_for(select_kernel<false>, q), kQThreads, 0, s>>>(t->desc, d_c, d_j, nullptr, d_out, q);
+    WALK_LAUNCH(select_kernel<false>, t, q, s, d_c, d_j, nullptr, d_out);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
@@ -310,16 +331,14 @@ wt_status launch_mixed(const wt_tree_s* t, const uint8_t* d_kind, const uint32_t
         wt_status st = order_queries(t, 3, d_kind, d_c, d_arg, q, s, o);
         if (st == WT_OK) {
             ProfScope ps("mixed", s);
-            mixed_kernel<true><<<grid_for(mixed_kernel<true>, q), kQThreads, 0, s>>>(t->desc, o.kind, o.c, o.a, o.idx,
-                                                                                     d_out, q);
+            WALK_LAUNCH(mixed_kernel<true>, t, q, s, o.kind, o.c, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
         if (o.mem) dev_free(o.mem, s);
         return st;
     }
     ProfScope ps("mixed", s);
-    mixed_kernel<false><<<grid_for(mixed_kernel<false>, q), kQThreads, 0, s>>>(t->desc, d_kind, d_c, d_arg, nullptr,
-                                                                               d_out, q);
+    WALK_LAUNCH(mixed_kernel<false>, t, q, s, d_kind, d_c, d_arg, nullptr, d_out);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 

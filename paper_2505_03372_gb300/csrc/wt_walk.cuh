@@ -6,13 +6,22 @@
 
 namespace wt {
 
-__device__ __forceinline__ ulonglong2 node_sr(const TreeDesc& t, uint32_t l, uint64_t p) {
+// {start, r0} of the first `slots` node-table slots, copied into shared memory
+// by the query kernels (the top levels of the tree: every walk passes them)
+struct NodeCache {
+    const ulonglong2* s;
+    uint32_t slots;
+};
+
+__device__ __forceinline__ ulonglong2 node_sr(const TreeDesc& t, const NodeCache& nc, uint32_t l, uint64_t p) {
     // {start, r0} of node (l, p); slots are 32-byte aligned
-    return ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + ((1ull << l) - 1 + p)));
+    const uint64_t slot = (1ull << l) - 1 + p;
+    if (slot < nc.slots) return nc.s[slot];
+    return ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + slot));
 }
 
 // Algorithm 5 with the early stop at nodes of at most two symbols.
-__device__ __forceinline__ uint32_t do_access(const TreeDesc& t, uint64_t i) {
+__device__ __forceinline__ uint32_t do_access(const TreeDesc& t, const NodeCache& nc, uint64_t i) {
     const CodeParams& cp = t.cp;
     if (cp.L == 0) return 0;
     uint64_t p = 0;
@@ -25,7 +34,7 @@ __device__ __forceinline__ uint32_t do_access(const TreeDesc& t, uint64_t i) {
             width = node_info(cp, l, p, a);
         }
         if (width == 1) return (uint32_t)a;
-        const ulonglong2 ne = node_sr(t, l, p);
+        const ulonglong2 ne = node_sr(t, nc, l, p);
         const uint64_t pos = ne.x + i;
         if (width == 2) return (uint32_t)(a + bit_at(t.lv[l], pos));
         uint32_t b;
@@ -38,17 +47,17 @@ __device__ __forceinline__ uint32_t do_access(const TreeDesc& t, uint64_t i) {
 }
 
 // Algorithm 6: the code of c gives the direction at every level.
-__device__ __forceinline__ uint64_t do_rank(const TreeDesc& t, uint32_t c, uint64_t i) {
+__device__ __forceinline__ uint64_t do_rank(const TreeDesc& t, const NodeCache& nc, uint32_t c, uint64_t i) {
     const CodeParams& cp = t.cp;
     uint32_t code, len;
     encode(cp, c, code, len);
-    ulonglong2 ne = node_sr(t, 0, 0);
+    ulonglong2 ne = node_sr(t, nc, 0, 0);
     for (uint32_t l = 0; l < len; l++) {
         if (i == 0) return 0;
         const uint32_t b = (code >> (cp.L - 1 - l)) & 1u;
         const uint64_t pos = ne.x + i;
         const uint64_t r0n = ne.y;
-        if (l + 1 < len) ne = node_sr(t, l + 1, code >> (cp.L - 1 - l));  // next node, issued early
+        if (l + 1 < len) ne = node_sr(t, nc, l + 1, code >> (cp.L - 1 - l));  // next node, issued early
         const uint64_t r1 = rank1(t.lv[l], pos);
         const uint64_t zb = (pos - r1) - r0n;
         i = b ? i - zb : zb;
@@ -58,22 +67,34 @@ __device__ __forceinline__ uint64_t do_rank(const TreeDesc& t, uint32_t c, uint6
 
 // Algorithms 7 and 8: leaf to root; the node of c at level l is the prefix of
 // its code, so getNodeStart becomes a table index.
-__device__ __forceinline__ uint64_t do_select(const TreeDesc& t, uint32_t c, uint64_t j) {
+__device__ __forceinline__ uint64_t do_select(const TreeDesc& t, const NodeCache& nc, uint32_t c, uint64_t j) {
     const CodeParams& cp = t.cp;
     uint32_t code, len;
     encode(cp, c, code, len);
     if (len == 0) return j - 1;
     int l = (int)len - 1;
-    ulonglong2 ne = node_sr(t, (uint32_t)l, (uint64_t)code >> (cp.L - (uint32_t)l));
+    ulonglong2 ne = node_sr(t, nc, (uint32_t)l, (uint64_t)code >> (cp.L - (uint32_t)l));
     for (; l >= 0; l--) {
         const uint32_t b = (code >> (cp.L - 1 - (uint32_t)l)) & 1u;
         const uint64_t start = ne.x;
         const uint64_t kb = b ? (start - ne.y) : ne.y;  // b-bits before the node
-        if (l > 0) ne = node_sr(t, (uint32_t)l - 1, (uint64_t)code >> (cp.L - (uint32_t)l + 1));
+        if (l > 0) ne = node_sr(t, nc, (uint32_t)l - 1, (uint64_t)code >> (cp.L - (uint32_t)l + 1));
         const uint64_t pos = select_b(t.lv[l], b, kb + j, t.k_log2);
         j = pos + 1 - start;
     }
     return j - 1;
+}
+
+// Copy the first `slots` {start, r0} pairs of the node table into shared memory
+// (every thread of the CTA calls this; it ends with a barrier).
+__device__ __forceinline__ NodeCache load_node_cache(const TreeDesc& t, ulonglong2* s, uint32_t slots) {
+    for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x)
+        s[i] = ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + i));
+    __syncthreads();
+    NodeCache nc;
+    nc.s = s;
+    nc.slots = slots;
+    return nc;
 }
 
 __device__ __forceinline__ bool select_valid(const TreeDesc& t, uint32_t c, uint64_t j) {
