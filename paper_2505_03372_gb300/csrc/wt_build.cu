@@ -105,12 +105,12 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 
 template <typename T>
 __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint64_t n, uint32_t sigma, uint32_t sbins,
-                                                   uint32_t copies, unsigned long long* __restrict__ hist,
-                                                   uint32_t* __restrict__ status) {
+                                                   uint32_t cstride, uint32_t copies,
+                                                   unsigned long long* __restrict__ hist, uint32_t* __restrict__ status) {
     extern __shared__ uint32_t sh[];
-    for (uint32_t i = threadIdx.x; i < sbins * copies; i += blockDim.x) sh[i] = 0;
+    for (uint32_t i = threadIdx.x; i < cstride * copies; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    uint32_t* mine = sh + (threadIdx.x % copies) * sbins;
+    uint32_t* mine = sh + (threadIdx.x % copies) * cstride;
     bool bad = false;
     constexpr int V = 16 / sizeof(T);
     const uint64_t nvec = n / V;
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStSymbol);
     for (uint32_t b = threadIdx.x; b < sbins; b += blockDim.x) {
         uint32_t c = 0;
-        for (uint32_t k = 0; k < copies; k++) c += sh[k * sbins + b];
+        for (uint32_t k = 0; k < copies; k++) c += sh[k * cstride + b];
         if (c) atomicAdd(hist + b, (unsigned long long)c);
     }
 }
@@ -867,10 +867,14 @@ static cudaError_t launch_level_pass(const LevelPassArgs& a, cudaStream_t s) {
 template <typename T>
 static cudaError_t launch_hist(const void* S, uint64_t n, uint32_t sigma, unsigned long long* hist, uint32_t* status,
                                cudaStream_t s) {
+    // Sub-histograms in shared memory, one per lane where they fit.  Their
+    // stride is 1 mod 32 words, so lanes counting the same symbol (the common
+    // case on skewed inputs) hit different banks and different addresses.
     const uint32_t budget = 64 * 1024;  // bytes of shared memory for sub-histograms
-    uint32_t sbins = std::min<uint32_t>(sigma, budget / 4);
-    uint32_t copies = std::max<uint32_t>(1, std::min<uint32_t>(16, budget / (4 * std::max<uint32_t>(sbins, 1))));
-    size_t sm = (size_t)sbins * copies * 4;
+    const uint32_t sbins = std::min<uint32_t>(sigma, budget / 4 - 1);
+    const uint32_t stride = ((sbins + 31) & ~31u) + 1;
+    const uint32_t copies = std::max<uint32_t>(1, std::min<uint32_t>(32, budget / (4 * stride)));
+    size_t sm = (size_t)stride * copies * 4;
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(hist_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -878,7 +882,7 @@ static cudaError_t launch_hist(const void* S, uint64_t n, uint32_t sigma, unsign
     }
     int blocks = sm_count() * 3;
     ProfScope ps("histogram", s);
-    hist_kernel<T><<<blocks, 512, sm, s>>>(reinterpret_cast<const T*>(S), n, sigma, sbins, copies, hist, status);
+    hist_kernel<T><<<blocks, 512, sm, s>>>(reinterpret_cast<const T*>(S), n, sigma, sbins, stride, copies, hist, status);
     return cudaGetLastError();
 }
 

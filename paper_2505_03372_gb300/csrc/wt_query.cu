@@ -11,12 +11,12 @@
 //
 // Query order.  Queries in random order touch one random 64-byte block per
 // level in a tree far larger than L2.  A large batch on a large tree is first
-// grouped by where its walk goes -- access by position, rank by (code prefix
-// of c, position), select by (code prefix of c, rank j) -- with a counting sort
-// over 4096 buckets; the walks then run in that order and write each answer to
-// the query's own slot.  The queries in flight at any moment then cover a few
-// megabytes of every level, which L2 holds, instead of the whole tree.  Answers
-// are the same in either order.
+// sorted by where its walks go -- access and rank by the position i, select by
+// the expected position of the j-th c, 16-bit keys (kind-major for mixed
+// batches) in two stable counting passes of 8 bits; the walks then run in that
+// order and write each answer to the query's own slot.  The queries in flight
+// at any moment then cover a few megabytes of every level, which L2 holds,
+// instead of the whole tree.  Answers are the same in either order.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -114,79 +114,171 @@ __global__ void __launch_bounds__(kQThreads) mixed_kernel(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// query order: counting sort over kBuckets buckets in chunks of kChunk queries
+// query order: 16-bit keys, sorted by two stable counting passes of 8 bits
+// (low byte, then high byte) over chunks of kChunk queries
 // ---------------------------------------------------------------------------
 
-constexpr uint32_t kBucketBits = 12;
-constexpr uint32_t kBuckets = 1u << kBucketBits;
-constexpr uint32_t kOrdThreads = 1024;
-constexpr uint32_t kOrdPer = 32;
-constexpr uint64_t kChunk = (uint64_t)kOrdThreads * kOrdPer;  // queries per CTA
+constexpr uint32_t kKeyBits = 16;
+constexpr uint32_t kOrdBuckets = 256;
+constexpr uint32_t kOrdThreads = 512;
+constexpr uint32_t kOrdWarps = kOrdThreads / 32;
+constexpr uint32_t kOrdPer = 8;
+constexpr uint32_t kChunk = kOrdThreads * kOrdPer;  // queries per CTA; warp w owns [256 w, 256 w + 256)
 constexpr uint64_t kOrderMinQueries = 1ull << 16;
 constexpr size_t kOrderMinTreeBytes = (size_t)64 << 20;
+// staging of one chunk in shared memory: argument, index, symbol, kind, bucket
+constexpr size_t kStageBytes = (size_t)kChunk * (8 + 4 + 4 + 1 + 1);
 
 struct OrderKey {
-    uint32_t lgn;    // ceil(lg n): positions and ranks above 2^lgn fall in the last bucket
-    uint32_t kind;   // 0 access, 1 rank, 2 select, 3 mixed (kind per query)
+    uint32_t lgn;   // ceil(lg n)
+    uint32_t kind;  // 0 access, 1 rank, 2 select, 3 mixed (kind per query)
 };
 
-// nbits-bit key of a query: access by position; rank and select by the top bits
-// of c's code, then by the top bits of i or j.
+struct OrdIn {
+    const uint8_t* kind;  // mixed batches only
+    const uint32_t* c;    // rank, select and mixed
+    const uint64_t* a;
+    const uint32_t* idx;  // null: the query's own index
+};
+struct OrdOut {
+    uint8_t* kind;
+    uint32_t* c;
+    uint64_t* a;
+    uint32_t* idx;
+};
+
+// nbits-bit key of a query: where in the sequence its walk goes.  Access and
+// rank by the position i; select by where the j-th c is expected, j / n_c of
+// the way through the sequence.  The walks touch the blocks at and below that
+// point on every level, so queries close in key share blocks in L1 and L2.
 __device__ __forceinline__ uint32_t sub_key(const TreeDesc& t, uint32_t lgn, uint32_t kd, uint32_t c, uint64_t x,
                                             uint32_t nbits) {
-    const uint32_t L = t.cp.L;
-    uint32_t pre = 0, cb = 0;
-    if (kd != 0) {
-        cb = L < nbits ? L : nbits;
-        uint32_t code = 0, len;
-        if (c < t.cp.sigma) encode(t.cp, c, code, len);
-        pre = cb ? code >> (L - cb) : 0u;
+    const uint64_t top = (1ull << nbits) - 1;
+    if (kd == 2) {
+        if (c >= t.cp.sigma || x == 0) return 0u;
+        const uint64_t nc = __ldg(t.C + c + 1) - __ldg(t.C + c);
+        if (x > nc) return 0u;
+        return (uint32_t)umin64(((x - 1) << nbits) / nc, top);
     }
-    const uint32_t xb = nbits - cb;
-    const uint32_t sh = lgn > xb ? lgn - xb : 0u;
-    const uint64_t xs = x >> sh;
-    const uint32_t xm = (uint32_t)umin64(xs, (1ull << xb) - 1);
-    return (pre << xb) | xm;
+    const uint32_t sh = lgn > nbits ? lgn - nbits : 0u;
+    return (uint32_t)umin64(x >> sh, top);
 }
-__device__ __forceinline__ uint32_t query_key(const TreeDesc& t, const OrderKey& ok, const uint8_t* kind,
-                                              const uint32_t* qc, const uint64_t* qa, uint64_t k) {
-    if (ok.kind < 3) return sub_key(t, ok.lgn, ok.kind, qc ? __ldg(qc + k) : 0u, __ldg(qa + k), kBucketBits);
-    const uint32_t kd = umin64(__ldg(kind + k), 3);
-    const uint32_t c = kd == 0 ? 0u : __ldg(qc + k);
-    return (kd << (kBucketBits - 2)) | sub_key(t, ok.lgn, kd == 3 ? 0u : kd, c, __ldg(qa + k), kBucketBits - 2);
+// kKeyBits-bit key (kind-major for mixed batches)
+__device__ __forceinline__ uint32_t query_key(const TreeDesc& t, const OrderKey& ok, const OrdIn& in, uint64_t k) {
+    if (ok.kind < 3) return sub_key(t, ok.lgn, ok.kind, ok.kind == 2 ? __ldg(in.c + k) : 0u, __ldg(in.a + k), kKeyBits);
+    const uint32_t kd = umin64(__ldg(in.kind + k), 3);
+    const uint32_t c = kd == 2 ? __ldg(in.c + k) : 0u;
+    return (kd << (kKeyBits - 2)) | sub_key(t, ok.lgn, kd == 3 ? 0u : kd, c, __ldg(in.a + k), kKeyBits - 2);
 }
 
-// per chunk and bucket: queries of the chunk in the bucket; hist[bucket * nchunks + chunk]
+// per chunk and bucket (byte `shift / 8` of the key): queries of the chunk in
+// the bucket; hist[bucket * nchunks + chunk]
 __global__ void __launch_bounds__(kOrdThreads) order_hist_kernel(const __grid_constant__ TreeDesc t, OrderKey ok,
-                                                                 const uint8_t* __restrict__ kind,
-                                                                 const uint32_t* __restrict__ qc,
-                                                                 const uint64_t* __restrict__ qa, uint64_t q,
+                                                                 OrdIn in, uint64_t q, uint32_t shift,
                                                                  uint64_t* __restrict__ hist, uint64_t nchunks) {
-    __shared__ uint32_t h[kBuckets];
-    for (uint32_t b = threadIdx.x; b < kBuckets; b += kOrdThreads) h[b] = 0;
+    __shared__ uint32_t h[kOrdBuckets];
+    for (uint32_t b = threadIdx.x; b < kOrdBuckets; b += kOrdThreads) h[b] = 0;
     __syncthreads();
     const uint64_t c0 = (uint64_t)blockIdx.x * kChunk, c1 = umin64(q, c0 + kChunk);
-    for (uint64_t k = c0 + threadIdx.x; k < c1; k += kOrdThreads) atomicAdd(h + query_key(t, ok, kind, qc, qa, k), 1u);
+    for (uint64_t k = c0 + threadIdx.x; k < c1; k += kOrdThreads)
+        atomicAdd(h + ((query_key(t, ok, in, k) >> shift) & (kOrdBuckets - 1)), 1u);
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < kBuckets; b += kOrdThreads) hist[(uint64_t)b * nchunks + blockIdx.x] = h[b];
+    for (uint32_t b = threadIdx.x; b < kOrdBuckets; b += kOrdThreads) hist[(uint64_t)b * nchunks + blockIdx.x] = h[b];
 }
 
-// place every query of the chunk at its bucket's next slot
-__global__ void __launch_bounds__(kOrdThreads) order_scatter_kernel(
-    const __grid_constant__ TreeDesc t, OrderKey ok, const uint8_t* __restrict__ kind, const uint32_t* __restrict__ qc,
-    const uint64_t* __restrict__ qa, uint64_t q, const uint64_t* __restrict__ offs, uint64_t nchunks,
-    uint8_t* __restrict__ skind, uint32_t* __restrict__ sc, uint64_t* __restrict__ sa, uint32_t* __restrict__ sidx) {
-    __shared__ uint32_t h[kBuckets];  // next slot of each bucket within this chunk's range
-    for (uint32_t b = threadIdx.x; b < kBuckets; b += kOrdThreads) h[b] = 0;
+// One stable counting pass: the chunk's queries go to their buckets' slots in
+// chunk order.  The chunk is first sorted by bucket in shared memory (each
+// warp ranks its own 256 queries in order with match masks; per-bucket counts
+// of the warps are then prefix-summed), then written out in that order, so
+// consecutive threads write consecutive slots of one bucket's run.
+__global__ void __launch_bounds__(kOrdThreads, 2) order_scatter_kernel(const __grid_constant__ TreeDesc t, OrderKey ok,
+                                                                       OrdIn in, uint64_t q, uint32_t shift,
+                                                                       const uint64_t* __restrict__ offs,
+                                                                       uint64_t nchunks, OrdOut out) {
+    extern __shared__ __align__(16) uint8_t stage[];
+    __shared__ uint16_t wcnt[kOrdWarps][kOrdBuckets];  // per warp and bucket: count, then first rank
+    __shared__ uint32_t lbase[kOrdBuckets];             // first staging slot of each bucket
+    __shared__ uint64_t gofs[kOrdBuckets];              // global slot minus staging slot, per bucket
+    __shared__ uint32_t wsum[kOrdBuckets / 32];
+    uint64_t* st_a = reinterpret_cast<uint64_t*>(stage);
+    uint32_t* st_i = reinterpret_cast<uint32_t*>(st_a + kChunk);
+    uint32_t* st_c = st_i + kChunk;
+    uint8_t* st_k = reinterpret_cast<uint8_t*>(st_c + kChunk);
+    uint8_t* st_b = st_k + kChunk;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t i = tid; i < kOrdWarps * kOrdBuckets / 2; i += kOrdThreads) reinterpret_cast<uint32_t*>(wcnt)[i] = 0;
     __syncthreads();
-    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk, c1 = umin64(q, c0 + kChunk);
-    for (uint64_t k = c0 + threadIdx.x; k < c1; k += kOrdThreads) {
-        const uint32_t b = query_key(t, ok, kind, qc, qa, k);
-        const uint64_t slot = offs[(uint64_t)b * nchunks + blockIdx.x] + atomicAdd(h + b, 1u);
-        sa[slot] = __ldg(qa + k);
-        sidx[slot] = (uint32_t)k;
-        if (qc) sc[slot] = __ldg(qc + k);
-        if (kind) skind[slot] = __ldg(kind + k);
+    const uint64_t c0 = (uint64_t)blockIdx.x * kChunk;
+    const uint32_t cn = (uint32_t)umin64(q - c0, kChunk);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t kr[kOrdPer];  // bucket, then bucket << 16 | rank among the warp's queries of the bucket
+#pragma unroll
+    for (uint32_t r = 0; r < kOrdPer; r++) {  // all keys first, so that their loads overlap
+        const uint32_t i = warp * (kOrdPer * 32) + r * 32 + lane;
+        kr[r] = i < cn ? (query_key(t, ok, in, c0 + i) >> shift) & (kOrdBuckets - 1) : kOrdBuckets;
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < kOrdPer; r++) {
+        const uint32_t i = warp * (kOrdPer * 32) + r * 32 + lane;
+        const bool valid = i < cn;
+        const uint32_t b = kr[r];
+        const uint32_t mask = __match_any_sync(0xffffffffu, b);  // lanes past the end match only each other
+        const uint32_t bi = valid ? b : 0u;
+        const uint32_t old = wcnt[warp][bi];
+        __syncwarp();
+        if (valid && lane == (uint32_t)(__ffs(mask) - 1)) wcnt[warp][bi] = (uint16_t)(old + __popc(mask));
+        __syncwarp();
+        kr[r] = (b << 16) | (old + __popc(mask & lt_mask));
+    }
+    __syncthreads();
+    if (tid < kOrdBuckets) {
+        // prefix over the warps of this bucket's counts, then over the buckets
+        uint32_t run = 0;
+#pragma unroll
+        for (uint32_t w = 0; w < kOrdWarps; w++) {
+            const uint32_t v = wcnt[w][tid];
+            wcnt[w][tid] = (uint16_t)run;
+            run += v;
+        }
+        uint32_t x = run;
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        lbase[tid] = x - run;  // exclusive within the warp
+    }
+    __syncthreads();
+    if (tid < kOrdBuckets) {
+        uint32_t before = 0;
+        for (uint32_t w = 0; w < warp; w++) before += wsum[w];
+        const uint32_t ex = lbase[tid] + before;
+        lbase[tid] = ex;
+        gofs[tid] = offs[(uint64_t)tid * nchunks + blockIdx.x] - ex;
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t r = 0; r < kOrdPer; r++) {
+        const uint32_t i = warp * (kOrdPer * 32) + r * 32 + lane;
+        if (i < cn) {
+            const uint32_t b = kr[r] >> 16;
+            const uint32_t p = lbase[b] + wcnt[warp][b] + (kr[r] & 0xffffu);
+            const uint64_t k = c0 + i;
+            st_a[p] = __ldg(in.a + k);
+            st_i[p] = in.idx ? __ldg(in.idx + k) : (uint32_t)k;
+            st_b[p] = (uint8_t)b;
+            if (in.c) st_c[p] = __ldg(in.c + k);
+            if (in.kind) st_k[p] = __ldg(in.kind + k);
+        }
+    }
+    __syncthreads();
+    for (uint32_t p = tid; p < cn; p += kOrdThreads) {
+        const uint64_t slot = gofs[st_b[p]] + p;
+        out.a[slot] = st_a[p];
+        out.idx[slot] = st_i[p];
+        if (in.c) out.c[slot] = st_c[p];
+        if (in.kind) out.kind[slot] = st_k[p];
     }
 }
 
@@ -202,7 +294,7 @@ static bool use_order(const wt_tree_s* t, uint64_t q) {
     return q >= kOrderMinQueries && q < (1ull << 32) && t->lvl_bytes >= kOrderMinTreeBytes && t->desc.cp.L > 0;
 }
 
-// Sort the queries into bucket order (fills o; o.mem must be freed by the caller).
+// Sort the queries by key (fills o; o.mem must be freed by the caller).
 static wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_kind, const uint32_t* d_c,
                                const uint64_t* d_a, uint64_t q, cudaStream_t s, Ordered& o) {
     OrderKey ok;
@@ -210,30 +302,48 @@ static wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8
     while ((1ull << ok.lgn) < t->desc.n) ok.lgn++;
     ok.kind = kindsel;
     const uint64_t nchunks = (q + kChunk - 1) / kChunk;
-    const uint64_t nh = (uint64_t)kBuckets * nchunks;
+    const uint64_t nh = (uint64_t)kOrdBuckets * nchunks;
     const uint64_t ntmp = 2 * ((nh + 8191) / 8192 + 2);
     auto al = [](uint64_t x) { return (x + 255) & ~255ull; };
-    const uint64_t o_hist = 0, o_offs = al(nh * 8), o_tmp = o_offs + al((nh + 1) * 8), o_a = o_tmp + al(ntmp * 8);
-    const uint64_t o_idx = o_a + al(q * 8), o_c = o_idx + al(q * 4), o_k = o_c + al(d_c ? q * 4 : 8);
-    const uint64_t total = o_k + al(d_kind ? q : 8);
+    const uint64_t per_copy = al(q * 8) + al(q * 4) + al(d_c ? q * 4 : 8) + al(d_kind ? q : 8);
+    const uint64_t o_hist = 0, o_offs = al(nh * 8), o_tmp = o_offs + al((nh + 1) * 8), o_copy = o_tmp + al(ntmp * 8);
+    const uint64_t total = o_copy + 2 * per_copy;
     if (dev_alloc(&o.mem, total, s) != cudaSuccess) return WT_ENOMEM;
     uint8_t* M = static_cast<uint8_t*>(o.mem);
     uint64_t* hist = reinterpret_cast<uint64_t*>(M + o_hist);
     uint64_t* offs = reinterpret_cast<uint64_t*>(M + o_offs);
-    o.a = reinterpret_cast<uint64_t*>(M + o_a);
-    o.idx = reinterpret_cast<uint32_t*>(M + o_idx);
-    o.c = d_c ? reinterpret_cast<uint32_t*>(M + o_c) : nullptr;
-    o.kind = d_kind ? reinterpret_cast<uint8_t*>(M + o_k) : nullptr;
-    {
-        ProfScope ps("order_hist", s);
-        order_hist_kernel<<<(unsigned)nchunks, kOrdThreads, 0, s>>>(t->desc, ok, d_kind, d_c, d_a, q, hist, nchunks);
+    OrdOut cp[2];
+    for (int i = 0; i < 2; i++) {
+        uint8_t* B = M + o_copy + i * per_copy;
+        cp[i].a = reinterpret_cast<uint64_t*>(B);
+        cp[i].idx = reinterpret_cast<uint32_t*>(B + al(q * 8));
+        cp[i].c = d_c ? reinterpret_cast<uint32_t*>(B + al(q * 8) + al(q * 4)) : nullptr;
+        cp[i].kind = d_kind ? B + al(q * 8) + al(q * 4) + al(d_c ? q * 4 : 8) : nullptr;
     }
-    device_exclusive_scan(hist, offs, nh, reinterpret_cast<uint64_t*>(M + o_tmp), s, "order_scan");
-    {
-        ProfScope ps("order_scatter", s);
-        order_scatter_kernel<<<(unsigned)nchunks, kOrdThreads, 0, s>>>(t->desc, ok, d_kind, d_c, d_a, q, offs, nchunks,
-                                                                         o.kind, o.c, o.a, o.idx);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(order_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+        attr = true;
     }
+    OrdIn in{d_kind, d_c, d_a, nullptr};
+    for (uint32_t pass = 0; pass < 2; pass++) {
+        const uint32_t shift = 8 * pass;
+        {
+            ProfScope ps("order_hist", s);
+            order_hist_kernel<<<(unsigned)nchunks, kOrdThreads, 0, s>>>(t->desc, ok, in, q, shift, hist, nchunks);
+        }
+        device_exclusive_scan(hist, offs, nh, reinterpret_cast<uint64_t*>(M + o_tmp), s, "order_scan");
+        {
+            ProfScope ps("order_scatter", s);
+            order_scatter_kernel<<<(unsigned)nchunks, kOrdThreads, kStageBytes, s>>>(t->desc, ok, in, q, shift, offs,
+                                                                                      nchunks, cp[pass]);
+        }
+        in = OrdIn{cp[pass].kind, cp[pass].c, cp[pass].a, cp[pass].idx};
+    }
+    o.a = cp[1].a;
+    o.idx = cp[1].idx;
+    o.c = cp[1].c;
+    o.kind = cp[1].kind;
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
