@@ -108,9 +108,43 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
                                                    uint32_t cstride, uint32_t copies,
                                                    unsigned long long* __restrict__ hist, uint32_t* __restrict__ status) {
     extern __shared__ uint32_t sh[];
+    if constexpr (sizeof(T) == 1) {
+        // Bytes: all 256 bins, one copy per lane, bin-major (copy k of bin b at
+        // b * 32 + k: every lane counts in its own bank).  No test per symbol:
+        // a symbol >= sigma shows as a nonzero bin >= sigma at the end.
+        for (uint32_t i = threadIdx.x; i < 256 * 32; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+        uint32_t* mine = sh + (threadIdx.x & 31);
+        const uint64_t nvec = n / 16;
+        const uint4* S4 = reinterpret_cast<const uint4*>(S);
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+            const uint4 x = __ldg(S4 + v);
+            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) atomicAdd(mine + (((w4[k] >> (8 * j)) & 0xffu) << 5), 1u);
+        }
+        for (uint64_t j = nvec * 16 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride)
+            atomicAdd(mine + ((uint32_t)S[j] << 5), 1u);
+        __syncthreads();
+        bool bad = false;
+        for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
+            uint32_t c = 0;
+            for (uint32_t k = 0; k < 32; k++) c += sh[b * 32 + ((k + b) & 31)];
+            if (b >= sigma) bad |= c != 0;
+            else if (c) atomicAdd(hist + b, (unsigned long long)c);
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStSymbol);
+        return;
+    }
     for (uint32_t i = threadIdx.x; i < cstride * copies; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    uint32_t* mine = sh + (threadIdx.x % copies) * cstride;
+    // copy k of bin b at b * 32 + k (one copy per lane: every lane has its own
+    // bank) or at k * cstride + b
+    const bool lanes = copies == 32;
+    uint32_t* mine = lanes ? sh + (threadIdx.x & 31) : sh + (threadIdx.x % copies) * cstride;
     bool bad = false;
     constexpr int V = 16 / sizeof(T);
     const uint64_t nvec = n / V;
@@ -118,7 +152,7 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     auto add = [&](uint32_t s) {
         if (s >= sigma) bad = true;
-        else if (s < sbins) atomicAdd(mine + s, 1u);
+        else if (s < sbins) atomicAdd(mine + (lanes ? s * 32 : s), 1u);
         else atomicAdd(hist + s, 1ull);
     };
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
@@ -131,7 +165,7 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStSymbol);
     for (uint32_t b = threadIdx.x; b < sbins; b += blockDim.x) {
         uint32_t c = 0;
-        for (uint32_t k = 0; k < copies; k++) c += sh[k * cstride + b];
+        for (uint32_t k = 0; k < copies; k++) c += lanes ? sh[b * 32 + k] : sh[k * cstride + b];
         if (c) atomicAdd(hist + b, (unsigned long long)c);
     }
 }
@@ -867,14 +901,18 @@ static cudaError_t launch_level_pass(const LevelPassArgs& a, cudaStream_t s) {
 template <typename T>
 static cudaError_t launch_hist(const void* S, uint64_t n, uint32_t sigma, unsigned long long* hist, uint32_t* status,
                                cudaStream_t s) {
-    // Sub-histograms in shared memory, one per lane where they fit.  Their
-    // stride is 1 mod 32 words, so lanes counting the same symbol (the common
-    // case on skewed inputs) hit different banks and different addresses.
+    // Sub-histograms in shared memory.  Up to 512 bins, one per lane, bin-major
+    // (every lane counts in its own bank, so a warp's atomics never conflict);
+    // else as many copies as fit, their stride 1 mod 32 words.
     const uint32_t budget = 64 * 1024;  // bytes of shared memory for sub-histograms
     const uint32_t sbins = std::min<uint32_t>(sigma, budget / 4 - 1);
-    const uint32_t stride = ((sbins + 31) & ~31u) + 1;
-    const uint32_t copies = std::max<uint32_t>(1, std::min<uint32_t>(32, budget / (4 * stride)));
-    size_t sm = (size_t)stride * copies * 4;
+    uint32_t stride = ((sbins + 31) & ~31u) + 1;
+    uint32_t copies = std::max<uint32_t>(1, std::min<uint32_t>(31, budget / (4 * stride)));
+    if (sbins * 32 * 4 <= budget) {
+        copies = 32;
+        stride = sbins;
+    }
+    size_t sm = sizeof(T) == 1 ? 256 * 32 * 4 : (size_t)stride * copies * 4;
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(hist_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);

@@ -126,8 +126,6 @@ constexpr uint32_t kOrdPer = 8;
 constexpr uint32_t kChunk = kOrdThreads * kOrdPer;  // queries per CTA; warp w owns [256 w, 256 w + 256)
 constexpr uint64_t kOrderMinQueries = 1ull << 16;
 constexpr size_t kOrderMinTreeBytes = (size_t)64 << 20;
-// staging of one chunk in shared memory: argument, index, symbol, kind, bucket
-constexpr size_t kStageBytes = (size_t)kChunk * (8 + 4 + 4 + 1 + 1);
 
 struct OrderKey {
     uint32_t lgn;   // ceil(lg n)
@@ -187,24 +185,21 @@ __global__ void __launch_bounds__(kOrdThreads) order_hist_kernel(const __grid_co
 }
 
 // One stable counting pass: the chunk's queries go to their buckets' slots in
-// chunk order.  The chunk is first sorted by bucket in shared memory (each
-// warp ranks its own 256 queries in order with match masks; per-bucket counts
-// of the warps are then prefix-summed), then written out in that order, so
+// chunk order.  The chunk is first ranked by bucket in shared memory (each warp
+// ranks its own 256 queries in order with match masks; per-bucket counts of the
+// warps are then prefix-summed), giving the chunk's permutation; the queries
+// are then copied out in permuted order (their second read hits L1), so
 // consecutive threads write consecutive slots of one bucket's run.
-__global__ void __launch_bounds__(kOrdThreads, 2) order_scatter_kernel(const __grid_constant__ TreeDesc t, OrderKey ok,
+__global__ void __launch_bounds__(kOrdThreads, 3) order_scatter_kernel(const __grid_constant__ TreeDesc t, OrderKey ok,
                                                                        OrdIn in, uint64_t q, uint32_t shift,
                                                                        const uint64_t* __restrict__ offs,
                                                                        uint64_t nchunks, OrdOut out) {
-    extern __shared__ __align__(16) uint8_t stage[];
     __shared__ uint16_t wcnt[kOrdWarps][kOrdBuckets];  // per warp and bucket: count, then first rank
-    __shared__ uint32_t lbase[kOrdBuckets];             // first staging slot of each bucket
-    __shared__ uint64_t gofs[kOrdBuckets];              // global slot minus staging slot, per bucket
+    __shared__ uint16_t perm[kChunk];                   // chunk offset of the query at each sorted place
+    __shared__ uint8_t pbkt[kChunk];                    // its bucket
+    __shared__ uint32_t lbase[kOrdBuckets];             // first sorted place of each bucket
+    __shared__ uint64_t gofs[kOrdBuckets];              // global slot minus sorted place, per bucket
     __shared__ uint32_t wsum[kOrdBuckets / 32];
-    uint64_t* st_a = reinterpret_cast<uint64_t*>(stage);
-    uint32_t* st_i = reinterpret_cast<uint32_t*>(st_a + kChunk);
-    uint32_t* st_c = st_i + kChunk;
-    uint8_t* st_k = reinterpret_cast<uint8_t*>(st_c + kChunk);
-    uint8_t* st_b = st_k + kChunk;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t i = tid; i < kOrdWarps * kOrdBuckets / 2; i += kOrdThreads) reinterpret_cast<uint32_t*>(wcnt)[i] = 0;
     __syncthreads();
@@ -264,21 +259,22 @@ __global__ void __launch_bounds__(kOrdThreads, 2) order_scatter_kernel(const __g
         if (i < cn) {
             const uint32_t b = kr[r] >> 16;
             const uint32_t p = lbase[b] + wcnt[warp][b] + (kr[r] & 0xffffu);
-            const uint64_t k = c0 + i;
-            st_a[p] = __ldg(in.a + k);
-            st_i[p] = in.idx ? __ldg(in.idx + k) : (uint32_t)k;
-            st_b[p] = (uint8_t)b;
-            if (in.c) st_c[p] = __ldg(in.c + k);
-            if (in.kind) st_k[p] = __ldg(in.kind + k);
+            perm[p] = (uint16_t)i;
+            pbkt[p] = (uint8_t)b;
         }
     }
     __syncthreads();
-    for (uint32_t p = tid; p < cn; p += kOrdThreads) {
-        const uint64_t slot = gofs[st_b[p]] + p;
-        out.a[slot] = st_a[p];
-        out.idx[slot] = st_i[p];
-        if (in.c) out.c[slot] = st_c[p];
-        if (in.kind) out.kind[slot] = st_k[p];
+#pragma unroll
+    for (uint32_t r = 0; r < kOrdPer; r++) {
+        const uint32_t p = tid + r * kOrdThreads;
+        if (p < cn) {
+            const uint64_t k = c0 + perm[p];
+            const uint64_t slot = gofs[pbkt[p]] + p;
+            out.a[slot] = __ldg(in.a + k);
+            out.idx[slot] = in.idx ? __ldg(in.idx + k) : (uint32_t)k;
+            if (in.c) out.c[slot] = __ldg(in.c + k);
+            if (in.kind) out.kind[slot] = __ldg(in.kind + k);
+        }
     }
 }
 
@@ -320,11 +316,6 @@ static wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8
         cp[i].c = d_c ? reinterpret_cast<uint32_t*>(B + al(q * 8) + al(q * 4)) : nullptr;
         cp[i].kind = d_kind ? B + al(q * 8) + al(q * 4) + al(d_c ? q * 4 : 8) : nullptr;
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(order_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
-        attr = true;
-    }
     OrdIn in{d_kind, d_c, d_a, nullptr};
     for (uint32_t pass = 0; pass < 2; pass++) {
         const uint32_t shift = 8 * pass;
@@ -335,7 +326,7 @@ static wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8
         device_exclusive_scan(hist, offs, nh, reinterpret_cast<uint64_t*>(M + o_tmp), s, "order_scan");
         {
             ProfScope ps("order_scatter", s);
-            order_scatter_kernel<<<(unsigned)nchunks, kOrdThreads, kStageBytes, s>>>(t->desc, ok, in, q, shift, offs,
+            order_scatter_kernel<<<(unsigned)nchunks, kOrdThreads, 0, s>>>(t->desc, ok, in, q, shift, offs,
                                                                                       nchunks, cp[pass]);
         }
         in = OrdIn{cp[pass].kind, cp[pass].c, cp[pass].a, cp[pass].idx};
