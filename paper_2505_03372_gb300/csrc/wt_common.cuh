@@ -235,8 +235,13 @@ struct LearnedDesc {
 
 __device__ __forceinline__ ulonglong2 ldg_nc_v2(const uint64_t* p) {
     ulonglong2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
+    asm("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
     return v;
+}
+
+// 32 bytes (one sector) in one request; p 32-byte aligned
+__device__ __forceinline__ void ldg_nc_v4(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
 }
 
 // Binary rank_1 (Algorithm 1 with 64-bit words): ones in B_l[0, pos), and the
@@ -246,15 +251,11 @@ __device__ __forceinline__ uint64_t rank1_bit(const LevelDesc& lv, uint64_t pos,
     const uint64_t blk = pos >> 9;
     const uint32_t wi = (uint32_t)(pos >> 6) & 7u;
     const uint32_t bi = (uint32_t)pos & 63u;
-    const uint64_t* base = lv.words + (blk << 3);
+    const uint64_t* base = lv.words + (blk << 3);  // 64-byte aligned
     uint64_t w[8];
-    ulonglong2 v = ldg_nc_v2(base);
-    w[0] = v.x;
-    w[1] = v.y;
-    w[2] = w[3] = w[4] = w[5] = w[6] = w[7] = 0;
-    if (wi >= 2) { v = ldg_nc_v2(base + 2); w[2] = v.x; w[3] = v.y; }
-    if (wi >= 4) { v = ldg_nc_v2(base + 4); w[4] = v.x; w[5] = v.y; }
-    if (wi >= 6) { v = ldg_nc_v2(base + 6); w[6] = v.x; w[7] = v.y; }
+    ldg_nc_v4(base, w[0], w[1], w[2], w[3]);
+    w[4] = w[5] = w[6] = w[7] = 0;
+    if (wi >= 4) ldg_nc_v4(base + 4, w[4], w[5], w[6], w[7]);
     uint64_t r = __ldg(lv.l1 + (pos >> 16)) + (uint64_t)__ldg(lv.l2 + blk);
     uint32_t c = 0;
 #pragma unroll
@@ -331,23 +332,42 @@ __device__ __forceinline__ uint64_t select_b(const LevelDesc& lv, uint32_t b, ui
         uint64_t c2 = __ldg(lv.l2 + lo2);
         kk -= b ? c2 : ((lo2 << 9) - (i1 << 16)) - c2;
     }
-    // words of the 512-bit block
+    // words of the 512-bit block, one 32-byte half at a time
     const uint64_t* wp = lv.words + (lo2 << 3);
     uint32_t kw = (uint32_t)kk;
-    uint64_t wv = 0;
+    uint64_t w0, w1, w2, w3;
+    ldg_nc_v4(wp, w0, w1, w2, w3);
     uint32_t wi = 0;
-#pragma unroll 1
-    for (; wi < 8; wi += 2) {
-        ulonglong2 v = ldg_nc_v2(wp + wi);
-        uint64_t a0 = b ? v.x : ~v.x, a1 = b ? v.y : ~v.y;
-        uint32_t p0 = __popcll(a0);
-        if (p0 >= kw) { wv = a0; break; }
-        kw -= p0;
-        uint32_t p1 = __popcll(a1);
-        if (p1 >= kw) { wv = a1; wi += 1; break; }
-        kw -= p1;
+    {
+        const uint32_t h = __popcll(b ? w0 : ~w0) + __popcll(b ? w1 : ~w1) + __popcll(b ? w2 : ~w2) +
+                           __popcll(b ? w3 : ~w3);
+        if (h < kw) {
+            kw -= h;
+            wi = 4;
+            ldg_nc_v4(wp + 4, w0, w1, w2, w3);
+        }
     }
-    return ((lo2 << 9) + ((uint64_t)wi << 6)) + select_in_word(wv, kw);
+    uint64_t wv = b ? w3 : ~w3;
+    uint32_t wj = 3;
+    {
+        const uint64_t a0 = b ? w0 : ~w0, a1 = b ? w1 : ~w1, a2 = b ? w2 : ~w2;
+        const uint32_t p0 = __popcll(a0), p1 = __popcll(a1), p2 = __popcll(a2);
+        if (p0 >= kw) {
+            wv = a0;
+            wj = 0;
+        } else if (p0 + p1 >= kw) {
+            wv = a1;
+            wj = 1;
+            kw -= p0;
+        } else if (p0 + p1 + p2 >= kw) {
+            wv = a2;
+            wj = 2;
+            kw -= p0 + p1;
+        } else {
+            kw -= p0 + p1 + p2;
+        }
+    }
+    return ((lo2 << 9) + ((uint64_t)(wi + wj) << 6)) + select_in_word(wv, kw);
 }
 
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t bits) { atomicOr(st, bits); }
