@@ -103,10 +103,15 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 // 1. histogram + validation
 // ===========================================================================
 
+// Also counts, per tile of 32 KB of S, the symbols whose level-0 bit is 1 (the
+// symbols >= m0, as codes grow with the symbol), so that the level-0 pass knows
+// every tile's prefix of ones (tcnt zeroed; null: not counted).
 template <typename T>
 __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint64_t n, uint32_t sigma, uint32_t sbins,
                                                    uint32_t cstride, uint32_t copies,
-                                                   unsigned long long* __restrict__ hist, uint32_t* __restrict__ status) {
+                                                   unsigned long long* __restrict__ hist, uint32_t* __restrict__ status,
+                                                   uint32_t m0, unsigned long long* __restrict__ tcnt) {
+    constexpr uint32_t TE = 32768 / sizeof(T);  // elements per tile; a tile is 2048 16-byte vectors
     extern __shared__ uint32_t sh[];
     if constexpr (sizeof(T) == 1) {
         // Bytes: all 256 bins, one copy per lane, bin-major (copy k of bin b at
@@ -118,6 +123,9 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
         const uint64_t nvec = n / 16;
         const uint4* S4 = reinterpret_cast<const uint4*>(S);
         const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        // bytes >= m0, two at a time in 16-bit lanes: b + 256 - m0 carries into bit 8 exactly when b >= m0
+        const uint32_t madd = (256u - (m0 < 256 ? m0 : 0u)) * 0x00010001u;
+        const bool tc = tcnt != nullptr && m0 < 256;
         for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
             const uint4 x = __ldg(S4 + v);
             const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
@@ -125,9 +133,25 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
             for (int k = 0; k < 4; k++)
 #pragma unroll
                 for (int j = 0; j < 4; j++) atomicAdd(mine + (((w4[k] >> (8 * j)) & 0xffu) << 5), 1u);
+            if (tc) {
+                // the warp's 32 vectors lie in one tile
+                uint32_t c = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t e = ((w4[k] & 0x00FF00FFu) + madd) & 0x01000100u;
+                    const uint32_t o = (((w4[k] >> 8) & 0x00FF00FFu) + madd) & 0x01000100u;
+                    c += __popc(e | (o << 1));
+                }
+                const uint32_t am = __activemask();
+                c = __reduce_add_sync(am, c);
+                if ((threadIdx.x & 31) == (uint32_t)(__ffs(am) - 1) && c) atomicAdd(tcnt + (v >> 11), (unsigned long long)c);
+            }
         }
-        for (uint64_t j = nvec * 16 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride)
-            atomicAdd(mine + ((uint32_t)S[j] << 5), 1u);
+        for (uint64_t j = nvec * 16 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+            const uint32_t b = (uint32_t)S[j];
+            atomicAdd(mine + (b << 5), 1u);
+            if (tc && b >= m0) atomicAdd(tcnt + j / TE, 1ull);
+        }
         __syncthreads();
         bool bad = false;
         for (uint32_t b = threadIdx.x; b < 256; b += blockDim.x) {
@@ -158,10 +182,22 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
         uint4 x = __ldg(S4 + v);
         const T* e = reinterpret_cast<const T*>(&x);
+        uint32_t c = 0;
 #pragma unroll
-        for (int k = 0; k < V; k++) add((uint32_t)e[k]);
+        for (int k = 0; k < V; k++) {
+            add((uint32_t)e[k]);
+            c += (uint32_t)e[k] >= m0;
+        }
+        if (tcnt != nullptr) {
+            const uint32_t am = __activemask();
+            c = __reduce_add_sync(am, c);
+            if ((threadIdx.x & 31) == (uint32_t)(__ffs(am) - 1) && c) atomicAdd(tcnt + (v >> 11), (unsigned long long)c);
+        }
     }
-    for (uint64_t j = nvec * V + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) add((uint32_t)S[j]);
+    for (uint64_t j = nvec * V + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        add((uint32_t)S[j]);
+        if (tcnt != nullptr && (uint32_t)S[j] >= m0) atomicAdd(tcnt + j / TE, 1ull);
+    }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStSymbol);
     for (uint32_t b = threadIdx.x; b < sbins; b += blockDim.x) {
         uint32_t c = 0;
@@ -260,7 +296,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint64_t
 // tmp must hold ceil(count / kScanChunk) + 1 + ceil(count / kScanChunk) + 1 entries
 void device_exclusive_scan(const uint64_t* in, uint64_t* out, uint64_t count, uint64_t* tmp, cudaStream_t s,
                            const char* name) {
-    if (count <= (uint64_t)kScanChunk * 4) {
+    if (count <= (uint64_t)kScanChunk) {
         ProfScope ps(name, s);
         scan_single_kernel<<<1, kScanThreads, 0, s>>>(in, out, count);
         return;
@@ -516,6 +552,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
 
     __shared__ uint64_t s_E, s_EL1, s_p;
     __shared__ uint32_t s_single;
+    __shared__ uint32_t s_nc[4];  // ones of T_{l+1} written by this tile: per run, in its first / second tile
     __shared__ uint32_t s_gcnt[64];
     __shared__ uint32_t s_gnext;
 
@@ -533,6 +570,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
         mbar_expect_tx(mbar_p, b16);
         bulk_g2s(smem, srcb, b16, mbar_p);
     }
+    if (tid < 4) s_nc[tid] = 0;
     for (uint32_t i = b16 + tid; i < bytes; i += kLpThreads) smem[i] = srcb[i];
     if (b16 && warp == 0) {  // one warp waits; the barrier hands the tile to all
         uint32_t spins = 0;
@@ -553,7 +591,17 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
         uint4 V = in4[g * 32 + lane];
         const uint32_t j0 = g * GE + lane * VEPL;
         uint32_t wv[4] = {V.x, V.y, V.z, V.w};
-        if (ENCODE) {
+        if (ENCODE && W == 1 && a.ctab_n == 256) {
+            // byte symbols: a 256-entry table, no bounds tests (entries past
+            // sigma and past the tile's end are never used)
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint32_t x = wv[i];
+                wv[i] = (uint32_t)ctab[x & 0xffu] | ((uint32_t)ctab[(x >> 8) & 0xffu] << 8) |
+                        ((uint32_t)ctab[(x >> 16) & 0xffu] << 16) | ((uint32_t)ctab[x >> 24] << 24);
+            }
+            in4[g * 32 + lane] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        } else if (ENCODE) {
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 uint32_t nv = 0;
@@ -644,7 +692,13 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
     // out[Z, count), each in input order; it does not depend on the look-back.
     T* out = reinterpret_cast<T*>(outb);
     const uint32_t out_s = smem_addr(outb);
-    if (warp == 0) {
+    if (warp == 0 && a.tile_excl != nullptr) {
+        // the ones before every tile are known (counted by the previous pass)
+        if (lane == 0) {
+            s_E = a.tile_excl[tile];
+            s_EL1 = a.tile_excl[tile - tile % TPL1];
+        }
+    } else if (warp == 0) {
         const uint64_t ones = ones32;
         const uint64_t excl = lookback_warp(a.state, tile, ones, a.status, kSpinCap);
         // ones before the enclosing L1 block
@@ -756,18 +810,27 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
     // ---- phase 5: shared-memory image -> T_{l+1} ----
     T* dst = reinterpret_cast<T*>(a.dst);
     const uint64_t lim = a.size_next;
+    // While copying out, count the ones of level l + 1 per tile of T_{l+1}, so
+    // that the next pass knows every tile's prefix without a look-back.
+    const bool cnt_next = a.next_cnt != nullptr;
+    const uint32_t nsh = a.shift_bit - 1;  // bit of level l + 1 (valid when cnt_next)
+    auto next_ones = [&](uint32_t x) { return (uint32_t)__popc((x >> nsh) & LOWB); };
     if (s_single != 0) {
         // two contiguous runs: zeros to off0 + R0, ones to off1 + E.  Global 4-byte
         // words are assembled from two shared words with a funnel shift.
         const NodeEntry* ne = a.nodes + s_p;
         const uint64_t D0 = __ldg(&ne->off0) + R0;
         const uint64_t D1 = __ldg(&ne->off1) + E;
+        uint64_t T0r[2] = {0, 0};  // first tile of T_{l+1} of each run
+        uint32_t clo[2] = {0, 0}, chi[2] = {0, 0};  // per run: in its first tile / in the next
 #pragma unroll
         for (int run = 0; run < 2; run++) {
             const uint64_t D = run ? D1 : D0;
             uint64_t len64 = run ? ones : zeros;
             const uint32_t so = run ? Z : 0u;
             if (D >= lim || len64 == 0) continue;
+            T0r[run] = D / TE;
+            const uint64_t bnd = (T0r[run] + 1) * TE - D;  // elements of the run in its first tile
             const uint32_t len = (uint32_t)umin64(len64, lim - D);
             T* dr = dst + D;
             // element counts of the unaligned head, the 16-byte body and the tail
@@ -775,29 +838,74 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             const uint32_t head = min(len, mis ? (16u - mis) / W : 0u);
             const uint32_t nb16 = (len - head) * W / 16;
             const uint32_t tail0 = head + nb16 * (16 / W);
-            if (tid < head) dr[tid] = out[so + tid];
+            if (tid < head) {
+                const T x = out[so + tid];
+                dr[tid] = x;
+                if (cnt_next) {
+                    const uint32_t c = next_ones((uint32_t)x);
+                    if (tid < bnd) clo[run] += c;
+                    else chi[run] += c;
+                }
+            }
             uint4* db = reinterpret_cast<uint4*>(dr + head);
             // the shared/global byte shift is the same for the whole run: every
             // global 16-byte unit is cut from two aligned shared 16-byte units
             const uint32_t sb0 = (so + head) * W;  // shared byte of the first body byte
             const uint32_t src0 = out_s + (sb0 & ~15u);
             const uint32_t q = (sb0 >> 2) & 3u, fs = (sb0 & 3u) * 8u;
-            for (uint32_t i = tid; i < nb16; i += kLpThreads)
-                db[i] = shift16(lds_u128(src0 + 16 * i), lds_u128(src0 + 16 * i + 16), q, fs);
-            for (uint32_t i = tail0 + tid; i < len; i += kLpThreads) dr[i] = out[so + i];
+            for (uint32_t i = tid; i < nb16; i += kLpThreads) {
+                const uint4 v = shift16(lds_u128(src0 + 16 * i), lds_u128(src0 + 16 * i + 16), q, fs);
+                db[i] = v;
+                if (cnt_next) {
+                    // a 16-byte unit of T_{l+1} never straddles one of its tiles
+                    const uint32_t c = next_ones(v.x) + next_ones(v.y) + next_ones(v.z) + next_ones(v.w);
+                    if (head + i * (16 / W) < bnd) clo[run] += c;
+                    else chi[run] += c;
+                }
+            }
+            for (uint32_t i = tail0 + tid; i < len; i += kLpThreads) {
+                const T x = out[so + i];
+                dr[i] = x;
+                if (cnt_next) {
+                    const uint32_t c = next_ones((uint32_t)x);
+                    if (i < bnd) clo[run] += c;
+                    else chi[run] += c;
+                }
+            }
+        }
+        if (cnt_next) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t c = __reduce_add_sync(0xffffffffu, (k & 1) ? chi[k >> 1] : clo[k >> 1]);
+                if (lane == 0 && c) atomicAdd(&s_nc[k], c);
+            }
+            __syncthreads();
+            if (tid < 4 && s_nc[tid])
+                atomicAdd(a.next_cnt + ((tid >> 1) ? T0r[1] : T0r[0]) + (tid & 1), (unsigned long long)s_nc[tid]);
         }
     } else {
         // several nodes: every element finds its node's offsets from its own code
         const uint32_t ps = a.pshift;
+        // ones of level l + 1 per tile of T_{l+1}: one atomic per tile per warp
+        auto count_multi = [&](const T x, uint64_t Dx) {
+            const uint32_t bit = Dx < lim ? ((uint32_t)x >> nsh) & 1u : 0u;
+            const uint64_t tl = Dx / TE;
+            const uint32_t am = __activemask();
+            const uint32_t grp = __match_any_sync(am, tl);
+            const uint32_t c = __popc(__ballot_sync(am, bit) & grp);
+            if (lane == __ffs(grp) - 1 && c) atomicAdd(a.next_cnt + tl, (unsigned long long)c);
+        };
         for (uint32_t i = tid; i < zeros; i += kLpThreads) {
             const T x = out[i];
             const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off0) + R0 + i;
             if (Dx < lim) dst[Dx] = x;
+            if (cnt_next) count_multi(x, Dx);
         }
         for (uint32_t i = tid; i < ones; i += kLpThreads) {
             const T x = out[Z + i];
             const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off1) + E + i;
             if (Dx < lim) dst[Dx] = x;
+            if (cnt_next) count_multi(x, Dx);
         }
     }
     return used_mbar;
@@ -820,8 +928,8 @@ __global__ void __launch_bounds__(kLpThreads, kLpBlocksPerSM)
         constexpr int W = sizeof(T);
         T* ctab = reinterpret_cast<T*>(smem + 2 * kTileBytes + 64 + kTileBytes / 8 / W + (64 + 1) * 4);
         for (uint32_t s = tid; s < a.ctab_n; s += kLpThreads) {
-            uint32_t code, len;
-            encode(a.cp, s, code, len);
+            uint32_t code = 0, len;
+            if (s < a.cp.sigma) encode(a.cp, s, code, len);
             ctab[s] = (T)code;
         }
     }
@@ -900,7 +1008,7 @@ static cudaError_t launch_level_pass(const LevelPassArgs& a, cudaStream_t s) {
 
 template <typename T>
 static cudaError_t launch_hist(const void* S, uint64_t n, uint32_t sigma, unsigned long long* hist, uint32_t* status,
-                               cudaStream_t s) {
+                               uint32_t m0, unsigned long long* tcnt, cudaStream_t s) {
     // Sub-histograms in shared memory.  Up to 512 bins, one per lane, bin-major
     // (every lane counts in its own bank, so a warp's atomics never conflict);
     // else as many copies as fit, their stride 1 mod 32 words.
@@ -920,7 +1028,8 @@ static cudaError_t launch_hist(const void* S, uint64_t n, uint32_t sigma, unsign
     }
     int blocks = sm_count() * 3;
     ProfScope ps("histogram", s);
-    hist_kernel<T><<<blocks, 512, sm, s>>>(reinterpret_cast<const T*>(S), n, sigma, sbins, stride, copies, hist, status);
+    hist_kernel<T><<<blocks, 512, sm, s>>>(reinterpret_cast<const T*>(S), n, sigma, sbins, stride, copies, hist, status,
+                                           m0, tcnt);
     return cudaGetLastError();
 }
 
@@ -966,7 +1075,10 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     size_t s_excl = align_up(s_left + std::max<uint64_t>(nslots, 1) * 8, 256);
     size_t s_tmp = align_up(s_excl + (nslots + 1) * 8, 256);
     size_t s_meta = align_up(s_tmp + scan_tmp * 8, 256);
-    size_t s_end = align_up(s_meta + 2 * kMaxLevels * 8, 256);
+    // ones of level 0 per 32 KB tile of S, counted by the histogram
+    const uint64_t tiles0 = (n * w + kTileBytes - 1) / kTileBytes;
+    size_t s_tcnt = align_up(s_meta + 2 * kMaxLevels * 8, 256);
+    size_t s_end = align_up(s_tcnt + std::max<uint64_t>(tiles0, 1) * 8, 256);
     void* scratch = nullptr;
     WT_CUDA_TRY(dev_alloc(&scratch, s_end, s));
     uint8_t* X = reinterpret_cast<uint8_t*>(scratch);
@@ -975,15 +1087,32 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     uint64_t* excl = reinterpret_cast<uint64_t*>(X + s_excl);
     uint64_t* tmp = reinterpret_cast<uint64_t*>(X + s_tmp);
     uint64_t* meta = reinterpret_cast<uint64_t*>(X + s_meta);
+    unsigned long long* tcnt0 = reinterpret_cast<unsigned long long*>(X + s_tcnt);
+    // m0: the first symbol whose code starts with a 1 (codes grow with the symbol)
+    uint32_t m0 = sigma;
+    if (L) {
+        uint32_t lo = 0, hi = sigma;
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            uint32_t code, len;
+            encode(cp, mid, code, len);
+            if ((code >> (L - 1)) & 1u) hi = mid;
+            else lo = mid + 1;
+        }
+        m0 = lo;
+    }
 
     WT_CUDA_TRY(cudaMemsetAsync(t->hdr_mem, 0, hdr, s));
     WT_CUDA_TRY(cudaMemsetAsync(hist, 0, (uint64_t)sigma * 8, s));
+    WT_CUDA_TRY(cudaMemsetAsync(tcnt0, 0, std::max<uint64_t>(tiles0, 1) * 8, s));
 
     // 1. histogram
     if (n) {
-        cudaError_t e = w == 1 ? launch_hist<uint8_t>(d_symbols, n, sigma, (unsigned long long*)hist, t->desc.status, s)
-                        : w == 2 ? launch_hist<uint16_t>(d_symbols, n, sigma, (unsigned long long*)hist, t->desc.status, s)
-                                 : launch_hist<uint32_t>(d_symbols, n, sigma, (unsigned long long*)hist, t->desc.status, s);
+        unsigned long long* hh = (unsigned long long*)hist;
+        unsigned long long* tc = L ? tcnt0 : nullptr;
+        cudaError_t e = w == 1   ? launch_hist<uint8_t>(d_symbols, n, sigma, hh, t->desc.status, m0, tc, s)
+                        : w == 2 ? launch_hist<uint16_t>(d_symbols, n, sigma, hh, t->desc.status, m0, tc, s)
+                                 : launch_hist<uint32_t>(d_symbols, n, sigma, hh, t->desc.status, m0, tc, s);
         if (e != cudaSuccess) { dev_free(scratch, s); return WT_ECUDA; }
     }
     // 2. C
@@ -1067,8 +1196,11 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         const uint64_t max_tiles = (n + te - 1) / te;
         const uint64_t tbytes = align_up(n * w, 256);
         const size_t b_state = align_up(max_tiles * 8, 256);
+        // per-tile ones of the next level (two, alternating), their exclusive scan, scan scratch
+        const size_t b_cnt = b_state, b_excl = align_up((max_tiles + 1) * 8, 256);
+        const size_t b_stmp = align_up(2 * ((max_tiles + kScanChunk - 1) / kScanChunk + 2) * 8, 256);
         void* work = nullptr;
-        const size_t work_bytes = 2 * tbytes + b_state + 256;
+        const size_t work_bytes = 2 * tbytes + b_state + 256 + 2 * b_cnt + b_excl + b_stmp;
         if (dev_alloc(&work, work_bytes, s) != cudaSuccess) {
             dev_free(scratch, s);
             return WT_ENOMEM;
@@ -1077,7 +1209,15 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         void* buf[2] = {Wm, Wm + tbytes};
         uint64_t* state = reinterpret_cast<uint64_t*>(Wm + 2 * tbytes);
         uint32_t* counters = reinterpret_cast<uint32_t*>(Wm + 2 * tbytes + b_state);
+        unsigned long long* ncnt[2];
+        ncnt[0] = reinterpret_cast<unsigned long long*>(Wm + 2 * tbytes + b_state + 256);
+        ncnt[1] = reinterpret_cast<unsigned long long*>(Wm + 2 * tbytes + b_state + 256 + b_cnt);
+        uint64_t* texcl = reinterpret_cast<uint64_t*>(Wm + 2 * tbytes + b_state + 256 + 2 * b_cnt);
+        uint64_t* stmp = reinterpret_cast<uint64_t*>(Wm + 2 * tbytes + b_state + 256 + 2 * b_cnt + b_excl);
         WT_CUDA_TRY(cudaMemsetAsync(counters, 0, 256, s));
+        // texcl holds the tile prefixes of the current level; level 0's come from the histogram
+        device_exclusive_scan(reinterpret_cast<const uint64_t*>(tcnt0), texcl, tiles0, stmp, s, "tile_scan");
+        bool have_excl = true;
         for (uint32_t l = 0; l < L; l++) {
             const uint64_t size = t->level_size[l];
             if (size == 0) continue;
@@ -1105,8 +1245,15 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.pshift = L - l;
             a.k_log2 = k_log2;
             a.cp = cp;
-            a.ctab_n = ((uint64_t)sigma * w <= kCodeTableBytes) ? sigma : 0;
-            WT_CUDA_TRY(cudaMemsetAsync(state, 0, a.ntiles * 8, s));
+            a.ctab_n = w == 1 ? 256u : ((uint64_t)sigma * w <= kCodeTableBytes) ? sigma : 0;
+            // Tile prefixes: from the counts the previous pass gathered, else by look-back.
+            if (have_excl) a.tile_excl = texcl;
+            else WT_CUDA_TRY(cudaMemsetAsync(state, 0, a.ntiles * 8, s));
+            const uint64_t ntiles_next = (a.size_next + te - 1) / te;
+            if (a.dst != nullptr && ntiles_next) {
+                a.next_cnt = ncnt[l & 1];
+                WT_CUDA_TRY(cudaMemsetAsync(a.next_cnt, 0, ntiles_next * 8, s));
+            }
             const bool enc = (l == 0) && !cp.pow2;
             cudaError_t e;
             if (w == 1) e = enc ? launch_level_pass<uint8_t, true>(a, s) : launch_level_pass<uint8_t, false>(a, s);
@@ -1117,6 +1264,10 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
                 dev_free(scratch, s);
                 return WT_ECUDA;
             }
+            have_excl = a.next_cnt != nullptr;
+            if (have_excl)
+                device_exclusive_scan(reinterpret_cast<const uint64_t*>(a.next_cnt), texcl, ntiles_next, stmp, s,
+                                      "tile_scan");
         }
         dev_free(work, s);
     } else {

@@ -202,7 +202,9 @@ struct LevelPassArgs {
     uint64_t* s1;
     uint64_t n_s0, n_s1;     // allocated sample entries (writes beyond are dropped)
     const NodeEntry* nodes;  // level-l slice of the node table
-    uint64_t* state;         // ntiles look-back words, zeroed
+    uint64_t* state;         // ntiles look-back words, zeroed (used when tile_excl is null)
+    const uint64_t* tile_excl;           // ones of T_l before each tile (ntiles + 1), or null: look-back
+    unsigned long long* next_cnt;        // ones of T_{l+1} per tile of T_{l+1}, zeroed; or null
     uint32_t* counter;       // tile counter, zeroed
     uint32_t* status;
     uint32_t level;
