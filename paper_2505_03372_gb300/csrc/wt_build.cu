@@ -430,8 +430,9 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
 // image: the lane's element with level bit b goes to slot A1 + (ones before it
 // in the lane) if b = 1, else to A0 + (zeros before it in the lane).  Slots of
 // two elements travel as a 16-bit pair.  For one-byte symbols
-// the in-word ranks come from byte-wise prefix counts of the level bits.
-template <typename T, bool FULL>
+// the in-word ranks come from byte-wise prefix counts of the level bits; with
+// ABS the slots are shared-memory addresses already (A0, A1 include out).
+template <typename T, bool FULL, bool ABS = false>
 __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V, uint32_t m, uint32_t A0, uint32_t A1,
                                               uint32_t j0, uint32_t count, uint32_t shift) {
     constexpr int W = sizeof(T);
@@ -455,10 +456,11 @@ __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V,
             const uint32_t s01 = __byte_perm(sel, 0, 0x1100), s23 = __byte_perm(sel, 0, 0x3322);
             const uint32_t I01 = ((b1 & s01) | (b0 & ~s01)) + __byte_perm(off, 0, 0x4140);
             const uint32_t I23 = ((b1 & s23) | (b0 & ~s23)) + __byte_perm(off, 0, 0x4342);
-            if (FULL || jw + 0 < count) sts_elem(out + (I01 & 0xFFFFu), (T)w);
-            if (FULL || jw + 1 < count) sts_elem(out + (I01 >> 16), (T)(w >> 8));
-            if (FULL || jw + 2 < count) sts_elem(out + (I23 & 0xFFFFu), (T)(w >> 16));
-            if (FULL || jw + 3 < count) sts_elem(out + (I23 >> 16), (T)(w >> 24));
+            const uint32_t ob = ABS ? 0u : out;
+            if (FULL || jw + 0 < count) sts_elem(ob + (I01 & 0xFFFFu), (T)w);
+            if (FULL || jw + 1 < count) sts_elem(ob + (I01 >> 16), (T)(w >> 8));
+            if (FULL || jw + 2 < count) sts_elem(ob + (I23 & 0xFFFFu), (T)(w >> 16));
+            if (FULL || jw + 3 < count) sts_elem(ob + (I23 >> 16), (T)(w >> 24));
         } else if (W == 2) {
             const uint32_t bb = (m >> (2 * i)) & 3u;
             const uint32_t sel = (bb & 1u ? 0x0000FFFFu : 0u) | (bb & 2u ? 0xFFFF0000u : 0u);
@@ -544,8 +546,10 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
     constexpr uint32_t LOWB = (W == 1) ? 0x01010101u : (W == 2 ? 0x00010001u : 1u);  // bit 0 of every element
     static_assert(NG % NWARP == 0 && NG <= 64, "tile shape");
 
-    uint4* in4 = reinterpret_cast<uint4*>(smem);
-    uint8_t* outb = smem + kTileBytes;
+    // the partitioned image first: its byte addresses fit in 16 bits (see ABS)
+    uint8_t* outb = smem;
+    uint8_t* inb = smem + kTileBytes;
+    uint4* in4 = reinterpret_cast<uint4*>(inb);
     uint8_t* wbytes = smem + 2 * kTileBytes + 64;                               // level bits of the tile
     uint32_t* rpre = reinterpret_cast<uint32_t*>(wbytes + kTileBytes / 8 / W);  // NG + 1
     T* ctab = reinterpret_cast<T*>(rpre + 64 + 1);                              // code table (ENCODE, small sigma)
@@ -568,10 +572,10 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
     // ---- phase 0: tile -> shared memory (TMA bulk copy + ragged tail) ----
     if (tid == 0 && b16) {
         mbar_expect_tx(mbar_p, b16);
-        bulk_g2s(smem, srcb, b16, mbar_p);
+        bulk_g2s(inb, srcb, b16, mbar_p);
     }
     if (tid < 4) s_nc[tid] = 0;
-    for (uint32_t i = b16 + tid; i < bytes; i += kLpThreads) smem[i] = srcb[i];
+    for (uint32_t i = b16 + tid; i < bytes; i += kLpThreads) inb[i] = srcb[i];
     if (b16 && warp == 0) {  // one warp waits; the barrier hands the tile to all
         uint32_t spins = 0;
         while (!mbar_try_wait(mbar_p, mphase)) {
@@ -655,7 +659,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             s_single = 1;
             s_p = 0;
         } else {
-            const T* te = reinterpret_cast<const T*>(smem);
+            const T* te = reinterpret_cast<const T*>(inb);
             const uint64_t p0 = (uint64_t)te[0] >> a.pshift;
             const uint64_t p1 = (uint64_t)te[count - 1] >> a.pshift;
             s_single = p0 == p1;
@@ -721,7 +725,49 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             for (uint64_t i = first_pad + tw; i < a.words_alloc; i += kLpThreads - 32) a.words[i] = 0;
         }
     }
-    if (a.dst != nullptr) {
+    if (a.dst != nullptr && a.tile_excl != nullptr) {
+        // every warp partitions its own GPW groups, two at a time: one scan of
+        // the lanes' one counts (16-bit halves) serves both groups
+        const uint16_t* m16 = reinterpret_cast<const uint16_t*>(wbytes);
+        const bool abs_ok = W == 1 && out_s + kTileBytes <= 65536u;
+#pragma unroll 1
+        for (int pr = 0; pr < GPW / 2; pr++) {
+            const int g = warp * GPW + 2 * pr;
+            uint32_t ma, mb;
+            if (W == 1) {
+                ma = m16[g * 32 + lane];
+                mb = m16[(g + 1) * 32 + lane];
+            } else if (W == 2) {
+                ma = wbytes[g * GBYTES + lane];
+                mb = wbytes[(g + 1) * GBYTES + lane];
+            } else {
+                ma = (wbytes[g * GBYTES + lane / 2] >> ((lane & 1) * 4)) & 0xFu;
+                mb = (wbytes[(g + 1) * GBYTES + lane / 2] >> ((lane & 1) * 4)) & 0xFu;
+            }
+            const uint32_t c = __popc(ma) | (__popc(mb) << 16);
+            uint32_t inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const uint32_t ex = inc - c;
+            const uint32_t ga = __shfl_sync(0xffffffffu, rp0, g >> 1), gb = __shfl_sync(0xffffffffu, rp1, g >> 1);
+            const uint32_t oba = ga + (ex & 0xFFFFu), obb = gb + (ex >> 16);
+            const uint32_t ja = g * GE + lane * VEPL, jb = ja + GE;
+            const uint4 Va = in4[g * 32 + lane], Vb = in4[(g + 1) * 32 + lane];
+            if (full && abs_ok) {
+                scatter_group<T, true, true>(out_s, Va, ma, out_s + ja - oba, out_s + Z + oba, ja, count, shift);
+                scatter_group<T, true, true>(out_s, Vb, mb, out_s + jb - obb, out_s + Z + obb, jb, count, shift);
+            } else if (full) {
+                scatter_group<T, true>(out_s, Va, ma, ja - oba, Z + oba, ja, count, shift);
+                scatter_group<T, true>(out_s, Vb, mb, jb - obb, Z + obb, jb, count, shift);
+            } else {
+                scatter_group<T, false>(out_s, Va, ma, ja - oba, Z + oba, ja, count, shift);
+                scatter_group<T, false>(out_s, Vb, mb, jb - obb, Z + obb, jb, count, shift);
+            }
+        }
+    } else if (a.dst != nullptr) {
         // groups are handed out dynamically; warp 0 joins once its look-back is done
 #pragma unroll 1
         while (true) {
