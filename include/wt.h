@@ -136,6 +136,33 @@ wt_status wt_select(wt_tree tree, const uint32_t* d_c, const uint64_t* d_j, uint
 wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_c, const uint64_t* d_arg,
                          uint64_t* d_out, uint64_t q, wt_stream stream);
 
+/*
+ * wt_query_host — the end-to-end query path of Section 6 (queries copied in
+ * from the host, answers copied back): the batch is split into chunks of
+ * `chunk` queries (0: min(q, 2^24)); chunk i+1 is copied in while chunk i
+ * walks and chunk i-1 is copied out, with at most two chunks resident on the
+ * device.  Each chunk is answered exactly as wt_access / wt_rank / wt_select /
+ * wt_query_mixed would answer it (including the query ordering of large
+ * chunks).
+ *  kind    0 access, 1 rank, 2 select, 3 mixed (per-query kinds in h_kind).
+ *  h_kind  host, q uint8 kinds (kind 3 only; else ignored, may be null).
+ *  h_c     host, q symbols (kinds 1-3; ignored for access, may be null).
+ *  h_arg   host, q positions i (access, rank) or ranks j (select), uint64.
+ *  h_out   host, q answers: uint32 for access, uint64 for kinds 1-3.
+ * Host buffers may be pinned (page-locked: the copies are asynchronous) or
+ * pageable (the driver stages the copies and may block the calling thread).
+ * Device pointers are rejected with WT_EINVAL.  The walks run on `stream`,
+ * after the work already queued there (typically the build); the copies run
+ * on two internal streams and do not wait for that work, so the first chunk's
+ * copy overlaps it.  The call returns once everything is queued; h_out holds
+ * the answers after `stream` has been synchronised, and the host buffers must
+ * stay valid until then.  Data errors are reported as for the device calls.
+ * Device memory: two chunks of arguments and answers, from the stream-ordered
+ * pool, returned when the last copy-out completes.
+ */
+wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, const uint32_t* h_c,
+                        const uint64_t* h_arg, void* h_out, uint64_t q, uint64_t chunk, wt_stream stream);
+
 /* Synchronise `stream`, then return and clear the tree's sticky device status
  * (WT_OK if no data-dependent error happened since the last call). */
 wt_status wt_status_sync(wt_tree tree, wt_stream stream);

@@ -25,7 +25,7 @@ MAX_LEVELS = 26
 
 # every symbol include/wt.h declares (checked by the ABI test)
 EXPORTED = (
-    "wt_build", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync",
+    "wt_build", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_query_host", "wt_status_sync",
     "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
     "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
     "wt_mlp_gradient", "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync",
@@ -94,6 +94,7 @@ def lib():
         L.wt_rank.argtypes = [vp, vp, vp, vp, u64, vp]
         L.wt_select.argtypes = [vp, vp, vp, vp, u64, vp]
         L.wt_query_mixed.argtypes = [vp, vp, vp, vp, vp, u64, vp]
+        L.wt_query_host.argtypes = [vp, u32, vp, vp, vp, vp, u64, u64, vp]
         L.wt_status_sync.argtypes = [vp, vp]
         L.wt_info.argtypes = [vp, ctypes.POINTER(Info)]
         L.wt_export.argtypes = [vp, u32, u32, vp, ctypes.POINTER(u64)]
@@ -126,7 +127,8 @@ def lib():
         L.wt_batch_destroy.restype = None
         L.wt_selftest_lookback_timeout.argtypes = [u32, vp]
         L.wt_selftest_lookback_timeout.restype = ctypes.c_int
-        for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_status_sync", "wt_info",
+        for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_query_host", "wt_status_sync",
+                  "wt_info",
                   "wt_export", "wt_train_select", "wt_select_learned", "wt_learned_info", "wt_mlp_gradient",
                   "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync", "wt_batch_tree"):
             getattr(L, f).restype = ctypes.c_int
@@ -280,6 +282,37 @@ class Tree:
         if q:
             _check(lib().wt_query_mixed(self._h, _dptr(kind, "kind"), _as_u32(c, "c"), _as_u64(arg, "arg"),
                                         _dptr(out, "out"), q, _stream(stream)), "wt_query_mixed")
+        return out
+
+    def query_host(self, kind: int, arg, c=None, kinds=None, out=None, chunk: int = 0, stream=None):
+        """wt_query_host: CPU tensors in (pinned or pageable), answers to the CPU
+        tensor ``out`` (int32 for access, int64 otherwise).  Asynchronous: the
+        answers are in ``out`` once ``stream`` has been synchronised."""
+        import torch
+
+        def host(t, name, dtypes):
+            if not isinstance(t, torch.Tensor) or t.is_cuda:
+                raise TypeError(f"{name} must be a CPU tensor")
+            if t.dtype not in dtypes:
+                raise TypeError(f"{name} has dtype {t.dtype}")
+            if not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+            return t.data_ptr()
+
+        q = arg.numel()
+        a = host(arg, "arg", (torch.int64, getattr(torch, "uint64", torch.int64)))
+        cp = host(c, "c", (torch.int32, getattr(torch, "uint32", torch.int32))) if kind != 0 else None
+        kp = host(kinds, "kinds", (torch.uint8,)) if kind == 3 else None
+        for t, name in ((c, "c"), (kinds, "kinds")):
+            if t is not None and t.numel() != q:
+                raise ValueError(f"{name} and arg must have the same length")
+        if out is None:
+            out = torch.empty(q, dtype=torch.int32 if kind == 0 else torch.int64, pin_memory=True)
+        if out.numel() != q:
+            raise ValueError("out must have one entry per query")
+        op = host(out, "out", (torch.int32,) if kind == 0 else (torch.int64,))
+        if q:
+            _check(lib().wt_query_host(self._h, kind, kp, cp, a, op, q, chunk, _stream(stream)), "wt_query_host")
         return out
 
     # ---- learned select ----

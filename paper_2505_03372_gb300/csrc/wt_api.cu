@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -226,6 +227,132 @@ wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_
     if (!is_device_ptr(d_kind) || !is_device_ptr(d_c) || !is_device_ptr(d_arg) || !is_device_ptr(d_out))
         return WT_EINVAL;
     return launch_mixed(tree, d_kind, d_c, d_arg, d_out, q, stream);
+}
+
+// ---------------------------------------------------------------------------
+// host-resident query pipeline
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// True if p is host memory (pinned or pageable), not device or managed memory.
+bool is_host_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // unknown to CUDA: ordinary pageable memory
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+struct HostPipe {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_walk[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    bool ok = true;
+    HostPipe() {
+        ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess;
+        for (int b = 0; b < 2 && ok; b++)
+            ok = cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ev_walk[b], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ev_out[b], cudaEventDisableTiming) == cudaSuccess;
+    }
+    ~HostPipe() {  // destruction is deferred by CUDA until the queued work completes
+        for (int b = 0; b < 2; b++) {
+            if (ev_in[b]) cudaEventDestroy(ev_in[b]);
+            if (ev_walk[b]) cudaEventDestroy(ev_walk[b]);
+            if (ev_out[b]) cudaEventDestroy(ev_out[b]);
+        }
+        if (h2d) cudaStreamDestroy(h2d);
+        if (d2h) cudaStreamDestroy(d2h);
+    }
+};
+
+}  // namespace
+
+wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, const uint32_t* h_c,
+                        const uint64_t* h_arg, void* h_out, uint64_t q, uint64_t chunk, wt_stream stream) {
+    if (!tree_ok(tree) || kind > 3) return WT_EINVAL;
+    if (!q) return WT_OK;
+    const bool need_c = kind != 0, need_kind = kind == 3;
+    if (!is_host_ptr(h_arg) || !is_host_ptr(h_out) || (need_c && !is_host_ptr(h_c)) ||
+        (need_kind && !is_host_ptr(h_kind)))
+        return WT_EINVAL;
+    if (!chunk) chunk = std::min<uint64_t>(q, 1ull << 24);
+    chunk = std::min(chunk, q);
+    const uint64_t nch = (q + chunk - 1) / chunk;
+    const size_t osz = kind == 0 ? 4 : 8;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    // per buffer: arguments, symbols, kinds, answers
+    const size_t o_c = al(chunk * 8), o_k = o_c + (need_c ? al(chunk * 4) : 0),
+                 o_o = o_k + (need_kind ? al(chunk) : 0), per = o_o + al(chunk * osz);
+    const int nbuf = nch > 1 ? 2 : 1;
+    HostPipe hp;
+    if (!hp.ok) return WT_ECUDA;
+    void* mem = nullptr;
+    if (dev_alloc(&mem, per * nbuf, hp.h2d) != cudaSuccess) return WT_ENOMEM;
+    uint8_t* M = static_cast<uint8_t*>(mem);
+    cudaStream_t s = stream;
+    wt_status st = WT_OK;
+    for (uint64_t i = 0; i < nch && st == WT_OK; i++) {
+        const int b = (int)(i & 1);
+        const uint64_t off = i * chunk, len = std::min(chunk, q - off);
+        uint8_t* B = M + b * per;
+        uint64_t* d_arg = reinterpret_cast<uint64_t*>(B);
+        uint32_t* d_c = need_c ? reinterpret_cast<uint32_t*>(B + o_c) : nullptr;
+        uint8_t* d_kind = need_kind ? B + o_k : nullptr;
+        void* d_out = B + o_o;
+        // copy in (the buffer's previous chunk has been copied out)
+        if (i >= 2 && cudaStreamWaitEvent(hp.h2d, hp.ev_out[b], 0) != cudaSuccess) st = WT_ECUDA;
+        if (st == WT_OK && cudaMemcpyAsync(d_arg, h_arg + off, len * 8, cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
+            st = WT_ECUDA;
+        if (st == WT_OK && need_c &&
+            cudaMemcpyAsync(d_c, h_c + off, len * 4, cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
+            st = WT_ECUDA;
+        if (st == WT_OK && need_kind &&
+            cudaMemcpyAsync(d_kind, h_kind + off, len, cudaMemcpyHostToDevice, hp.h2d) != cudaSuccess)
+            st = WT_ECUDA;
+        if (st == WT_OK && cudaEventRecord(hp.ev_in[b], hp.h2d) != cudaSuccess) st = WT_ECUDA;
+        // walk on the caller's stream
+        if (st == WT_OK && cudaStreamWaitEvent(s, hp.ev_in[b], 0) != cudaSuccess) st = WT_ECUDA;
+        if (st == WT_OK) {
+            switch (kind) {
+                case 0: st = launch_access(tree, d_arg, static_cast<uint32_t*>(d_out), len, s); break;
+                case 1: st = launch_rank(tree, d_c, d_arg, static_cast<uint64_t*>(d_out), len, s); break;
+                case 2: st = launch_select(tree, d_c, d_arg, static_cast<uint64_t*>(d_out), len, s); break;
+                default: st = launch_mixed(tree, d_kind, d_c, d_arg, static_cast<uint64_t*>(d_out), len, s); break;
+            }
+        }
+        if (st == WT_OK && cudaEventRecord(hp.ev_walk[b], s) != cudaSuccess) st = WT_ECUDA;
+        // copy out
+        if (st == WT_OK && cudaStreamWaitEvent(hp.d2h, hp.ev_walk[b], 0) != cudaSuccess) st = WT_ECUDA;
+        if (st == WT_OK && cudaMemcpyAsync(static_cast<uint8_t*>(h_out) + off * osz, d_out, len * osz,
+                                           cudaMemcpyDeviceToHost, hp.d2h) != cudaSuccess)
+            st = WT_ECUDA;
+        if (st == WT_OK && cudaEventRecord(hp.ev_out[b], hp.d2h) != cudaSuccess) st = WT_ECUDA;
+    }
+    // The copy-out stream waits for everything queued on the caller's stream
+    // (all walks, even after an error), then the caller's stream waits for the
+    // last copy-out; the buffers go back to the pool after both.
+    cudaEvent_t walked = nullptr, done = nullptr;
+    if (cudaEventCreateWithFlags(&walked, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamSynchronize(s);  // no events: order by waiting on the host instead
+        cudaStreamSynchronize(hp.d2h);
+        cudaStreamSynchronize(hp.h2d);
+        dev_free(mem, s);
+        if (walked) cudaEventDestroy(walked);
+        return WT_ECUDA;
+    }
+    cudaEventRecord(walked, s);
+    cudaStreamWaitEvent(hp.d2h, walked, 0);
+    cudaEventRecord(done, hp.d2h);
+    cudaStreamWaitEvent(s, done, 0);
+    dev_free(mem, hp.d2h);
+    cudaEventDestroy(walked);
+    cudaEventDestroy(done);
+    return st;
 }
 
 wt_status wt_status_sync(wt_tree tree, wt_stream stream) {
