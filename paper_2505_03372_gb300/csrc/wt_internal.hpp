@@ -102,6 +102,21 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
 uint64_t batch_tile_elems(uint32_t w);
 
 // ---- queries (wt_query.cu) ----
+// Large batches are sorted by where their walks go before walking (wt_query.cu):
+// the sorted arguments, symbols and kinds and each sorted query's original index;
+// mem (one pool allocation) must be freed by the caller on the same stream.
+struct Ordered {
+    void* mem = nullptr;
+    uint8_t* kind = nullptr;
+    uint32_t* c = nullptr;
+    uint64_t* a = nullptr;
+    uint32_t* idx = nullptr;
+};
+bool use_order(const wt_tree_s* t, uint64_t q);
+// kindsel: 0 access, 1 rank, 2 select, 3 mixed (d_kind per query)
+wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_kind, const uint32_t* d_c,
+                        const uint64_t* d_a, uint64_t q, cudaStream_t s, Ordered& o);
+
 wt_status launch_access(const wt_tree_s* t, const uint64_t* d_i, uint32_t* d_out, uint64_t q, cudaStream_t s);
 wt_status launch_rank(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d_i, uint64_t* d_out, uint64_t q,
                       cudaStream_t s);

@@ -299,18 +299,20 @@ __device__ __forceinline__ uint64_t select_b_window(const LevelDesc& lv, uint32_
         }
         kk -= cb;
     }
+    // words of the 512-bit block, one 32-byte half at a time
     const uint64_t* wp = lv.words + (lo2 << 3);
     uint32_t kw = (uint32_t)kk;
 #pragma unroll 1
-    for (uint32_t wi = 0; wi < 8; wi += 2) {
-        const ulonglong2 v = ldg_nc_v2(wp + wi);
-        const uint64_t a0 = b ? v.x : ~v.x, a1 = b ? v.y : ~v.y;
-        const uint32_t p0 = __popcll(a0);
-        if (p0 >= kw) return (lo2 << 9) + ((uint64_t)wi << 6) + select_in_word(a0, kw);
-        kw -= p0;
-        const uint32_t p1 = __popcll(a1);
-        if (p1 >= kw) return (lo2 << 9) + ((uint64_t)(wi + 1) << 6) + select_in_word(a1, kw);
-        kw -= p1;
+    for (uint32_t h = 0; h < 8; h += 4) {
+        uint64_t w[4];
+        ldg_nc_v4(wp + h, w[0], w[1], w[2], w[3]);
+#pragma unroll
+        for (uint32_t e = 0; e < 4; e++) {
+            const uint64_t a = b ? w[e] : ~w[e];
+            const uint32_t p = __popcll(a);
+            if (p >= kw) return (lo2 << 9) + ((uint64_t)(h + e) << 6) + select_in_word(a, kw);
+            kw -= p;
+        }
     }
     ok = false;  // not in this 512-bit block: the window did not hold the bit
     return 0;
@@ -334,10 +336,13 @@ __device__ __forceinline__ uint64_t select_b_learned(const TreeDesc& t, const Le
 
 constexpr int kLqThreads = 256;
 
+// ORD: the queries were sorted by walk key; idx[k] is query k's original slot.
+template <bool ORD>
 __global__ void __launch_bounds__(kLqThreads) select_learned_kernel(const __grid_constant__ TreeDesc t,
                                                                     const __grid_constant__ LearnedDesc ld,
                                                                     const uint32_t* __restrict__ qc,
                                                                     const uint64_t* __restrict__ qj,
+                                                                    const uint32_t* __restrict__ idx,
                                                                     uint64_t* __restrict__ out, uint64_t q) {
     extern __shared__ float mlp_s[];
     if (ld.mode == kLearnMlp) {
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(kLqThreads) select_learned_kernel(const __grid
             }
             res = j - 1;
         }
-        out[kq] = res;
+        out[ORD ? __ldg(idx + kq) : kq] = res;
         if (__any_sync(__activemask(), bad) && bad) atomicOr(t.status, kStQuery);
     }
     if (fb) atomicAdd(ld.fallbacks, (unsigned long long)fb);
@@ -489,13 +494,26 @@ wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const u
     const size_t sm = t->learned.mode == kLearnMlp ? (size_t)2 * t->desc.cp.L * kMlpParams * 4 : 0;
     static int per_sm = 0;
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_learned_kernel, kLqThreads, 20 * 1024);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_learned_kernel<false>, kLqThreads, 20 * 1024);
         if (per_sm <= 0) per_sm = 1;
     }
     uint64_t need = (q + kLqThreads - 1) / kLqThreads, full = (uint64_t)per_sm * sm_count();
-    ProfScope ps(t->learned.mode == kLearnMlp ? "select_learned_mlp" : "select_learned_pla", s);
-    select_learned_kernel<<<(unsigned)(need < full ? need : full), kLqThreads, sm, s>>>(t->desc, t->learned, d_c, d_j,
-                                                                                       d_out, q);
+    const unsigned grid = (unsigned)(need < full ? need : full);
+    const char* name = t->learned.mode == kLearnMlp ? "select_learned_mlp" : "select_learned_pla";
+    // large batches walk in the same order as the sampled select's
+    if (use_order(t, q)) {
+        Ordered o;
+        wt_status st = order_queries(t, 2, nullptr, d_c, d_j, q, s, o);
+        if (st == WT_OK) {
+            ProfScope ps(name, s);
+            select_learned_kernel<true><<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, o.c, o.a, o.idx, d_out, q);
+            if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
+        }
+        if (o.mem) dev_free(o.mem, s);
+        return st;
+    }
+    ProfScope ps(name, s);
+    select_learned_kernel<false><<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, d_c, d_j, nullptr, d_out, q);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 

@@ -278,20 +278,12 @@ __global__ void __launch_bounds__(kOrdThreads, 3) order_scatter_kernel(const __g
     }
 }
 
-struct Ordered {
-    void* mem = nullptr;
-    uint8_t* kind = nullptr;
-    uint32_t* c = nullptr;
-    uint64_t* a = nullptr;
-    uint32_t* idx = nullptr;
-};
-
-static bool use_order(const wt_tree_s* t, uint64_t q) {
+bool use_order(const wt_tree_s* t, uint64_t q) {
     return q >= kOrderMinQueries && q < (1ull << 32) && t->lvl_bytes >= kOrderMinTreeBytes && t->desc.cp.L > 0;
 }
 
 // Sort the queries by key (fills o; o.mem must be freed by the caller).
-static wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_kind, const uint32_t* d_c,
+wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_kind, const uint32_t* d_c,
                                const uint64_t* d_a, uint64_t q, cudaStream_t s, Ordered& o) {
     OrderKey ok;
     ok.lgn = 0;
