@@ -338,6 +338,19 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": dom_ms / nlaunch, "traffic": traffic}
     if lp_name in kern:
         roof["level_pass_frac"] = (sum(lp_bytes) * args.steps / (kern[lp_name]["ms"] * 1e-3) / 1e9) / peak
+    # queries against the DRAM sector rate (random 32-byte sectors, the sector
+    # model of query_sectors; sorted batches reuse sectors in L1/L2, so the
+    # fraction can exceed 1)
+    qroof = {}
+    for kind, qk in (("access", "access_i"), ("rank", "rank_i"), ("select", "select_j"), ("mixed", "mixed_arg")):
+        if kind in kern and kern[kind]["launches"]:
+            sec = query_sectors(kind, L, code_len) if kind != "mixed" else statistics.mean(
+                [query_sectors(k, L, code_len) for k in ("access", "rank", "select")])
+            ms = kern[kind]["ms"] / kern[kind]["launches"]
+            gsec = q[qk].numel() * sec / (ms * 1e-3) / 1e9
+            qroof[kind] = {"sectors_per_query": sec, "achieved_Gsectors_s": gsec, "peak_Gsectors_s": peak / 32,
+                           "frac": gsec / (peak / 32)}
+    roof["queries"] = qroof
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
