@@ -656,12 +656,121 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_bitvector(args):
+    """The paper's standalone binary rank / select experiment on synthetic
+    Kurpicz-style bitvectors: 2^32 bits with a fill of 10, 50 or 90 %, ones
+    uniform or 99 % at the end; per bitvector 1e8 rank, 1e8 select_0 and 1e8
+    select_1 queries (uniform positions / ranks), one thread per query.  A step
+    answers all of them on all six bitvectors."""
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2505_03372_gb300 import binding as wt, workloads
+
+    nbits = int(args.n) if args.n else 1 << 32
+    q = max(1, int(1e8 * args.query_scale))
+    K = 4096
+    g = workloads.generator(workloads.SEED_BASE + 6 + 7919 * rank, "cuda")
+    cases = []
+    for layout in ("uniform", "adversarial"):
+        for fill in workloads.BITVECTOR_FILLS:
+            words = workloads.make_bitvector(nbits, fill, layout, seed=workloads.SEED_BASE + 5 + int(fill * 100),
+                                             device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bv = wt.Bitvector(words, nbits, sample_k=K)
+            e1.record()
+            torch.cuda.synchronize()
+            del words
+            i = torch.randint(0, nbits + 1, (q,), generator=g, device="cuda", dtype=torch.int64)
+            cnt = {1: bv.ones, 0: nbits - bv.ones}
+            j = {b: (torch.rand(q, generator=g, device="cuda", dtype=torch.float64) * cnt[b]).to(torch.int64) + 1
+                 for b in (0, 1)}
+            cases.append({"name": f"{layout} {int(fill * 100)} %", "bv": bv, "i": i, "j": j,
+                          "support_ms": e0.elapsed_time(e1), "out": torch.empty(q, dtype=torch.int64, device="cuda")})
+
+    def step():
+        for c in cases:
+            c["bv"].rank(c["i"], out=c["out"])
+            c["bv"].select(0, c["j"][0], out=c["out"])
+            c["bv"].select(1, c["j"][1], out=c["out"])
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    for c in cases:
+        if c["bv"].status_sync() != wt.WT_OK:
+            raise RuntimeError("bitvector status after warm-up")
+    launches0 = wt.profile_launches()
+    clocks = ClockSampler(local) if rank == 0 else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    launches = wt.profile_launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    Q = 3 * q * len(cases)
+    # per-kind times, measured again call by call (outside the timed region)
+    peak, peak_kind = peaks()
+    phases, qroof = {}, {}
+    tot = {"rank": 0.0, "select": 0.0}
+    for c in cases:
+        row = {"support_ms": c["support_ms"], "ones": c["bv"].ones}
+        for kind, fn in (("rank", lambda: c["bv"].rank(c["i"], out=c["out"])),
+                         ("select0", lambda: c["bv"].select(0, c["j"][0], out=c["out"])),
+                         ("select1", lambda: c["bv"].select(1, c["j"][1], out=c["out"]))):
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record()
+            fn()
+            f1.record()
+            torch.cuda.synchronize()
+            t = f0.elapsed_time(f1)
+            row[f"{kind}_Mqps"] = q / (t * 1e-3) / 1e6
+            tot["rank" if kind == "rank" else "select"] += t
+        phases[c["name"]] = row
+    for kind, sec in (("rank", 2.5), ("select", 6.5)):
+        nq = q * len(cases) * (1 if kind == "rank" else 2)
+        gsec = nq * sec / (tot[kind] * 1e-3) / 1e9
+        qroof[kind] = {"sectors_per_query": sec, "achieved_Gsectors_s": gsec, "peak_Gsectors_s": peak / 32,
+                       "frac": gsec / (peak / 32)}
+    dom = max(qroof, key=lambda k: tot[k])
+    line = {
+        "metric": METRIC, "value": world * Q / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "ours",
+        "config": {"workload": f"bitvector: {nbits} bits, fill 10/50/90 %, uniform and adversarial (99 % of the "
+                               f"ones at the end); {q} rank, {q} select_0 and {q} select_1 each; K = {K}",
+                   "queries_per_step_per_gpu": Q,
+                   "l2_flush": "inputs larger than L2 (six 512 MiB bitvectors, 2.4 GB of queries)"},
+        "phases": phases,
+        "roofline": {"bound": "hbm", "kernel": f"bv_{dom}", "achieved": qroof[dom]["achieved_Gsectors_s"] * 32,
+                     "peak": peak, "unit": "GB/s", "frac": qroof[dom]["frac"], "traffic": None,
+                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "queries": qroof},
+        "gpu_launches": launches, "clocks": clk, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "bitvector":
+        run_bitvector(args)
     else:
         run_ours(args)
 

@@ -352,6 +352,32 @@ wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64_t nbits, u
                                       uint32_t* d_status, wt_stream stream);
 
 /*
+ * wt_bitvector_rank / wt_bitvector_select — binary rank (Section 4.1,
+ * Algorithm 1) and sampled binary select (Section 4.2, Algorithm 2) over a
+ * caller-owned bitvector whose support structures wt_bitvector_support_static
+ * wrote (the same layout as one level of a tree).  One thread per query.
+ *  d_words  device, 32-byte aligned, the bits LSB-first; the allocation must hold whole 512-bit
+ *           blocks plus one: at least (floor(nbits / 512) + 1) * 8 words (the
+ *           walks read 32-byte halves of a block); bits at or past nbits must
+ *           be zero.
+ *  d_l1, d_l2, d_s0, d_s1, sample_k  as written by wt_bitvector_support_static.
+ *  ones     number of ones in the bitvector (select's bound and last sample).
+ *  rank:    d_out[k] = ones in B[0, d_i[k]) for d_i[k] <= nbits.
+ *  select:  d_out[k] = position of the d_j[k]-th (1-based) bit equal to b
+ *           (b = 0 or 1) for 1 <= d_j[k] <= count_b.
+ * Out-of-range queries yield UINT64_MAX and OR 1 << WT_EQUERY into *d_status
+ * (optional device word).  Asynchronous on `stream`.  Host-detectable errors
+ * (null or non-device pointers, nbits == 0, b > 1, sample_k not a power of two
+ * in [256, 2^20], ones > nbits) return WT_EINVAL before any work is queued.
+ */
+wt_status wt_bitvector_rank(const uint64_t* d_words, uint64_t nbits, const uint64_t* d_l1, const uint16_t* d_l2,
+                            const uint64_t* d_i, uint64_t* d_out, uint64_t q, uint32_t* d_status, wt_stream stream);
+wt_status wt_bitvector_select(const uint64_t* d_words, uint64_t nbits, uint64_t ones, uint32_t b,
+                              const uint64_t* d_l1, const uint16_t* d_l2, const uint64_t* d_s0,
+                              const uint64_t* d_s1, uint32_t sample_k, const uint64_t* d_j, uint64_t* d_out,
+                              uint64_t q, uint32_t* d_status, wt_stream stream);
+
+/*
  * wt_selftest_lookback_timeout — diagnostic for the bounded device waits.
  * Runs the build's decoupled look-back for a tile whose predecessor never
  * publishes its count, with at most spin_cap polls (1 <= spin_cap <= 2^22;

@@ -221,3 +221,21 @@ class O2Tree:
         out = np.empty(j.size, np.uint64)
         lib().orc_o2_select(self._h, _p(c, _u32p), _p(j, _u64p), j.size, _p(out, _u64p))
         return out
+
+
+# --------------------------------------------------------------------------
+# standalone bitvectors: binary rank and select by definition
+# --------------------------------------------------------------------------
+
+def bv_rank(bits, i):
+    """rank_1(B, i) (Section 4.1): ones in B[0, i), for each i in [0, len(B)].
+    bits: 0/1 array.  Prefix sums of the bits, a library primitive."""
+    pre = np.concatenate([[0], np.cumsum(np.asarray(bits, dtype=np.int64))])
+    return pre[np.asarray(i, dtype=np.int64)].astype(np.uint64)
+
+
+def bv_select(bits, b, j):
+    """select_b(B, j) (Section 4.2): position of the j-th (1-based) bit equal to
+    b, for each j in [1, count_b]."""
+    pos = np.flatnonzero(np.asarray(bits) == b)
+    return pos[np.asarray(j, dtype=np.int64) - 1].astype(np.uint64)

@@ -86,3 +86,26 @@ def counters(bits, K, l1=65536, l2=512):
             if zeros % K == 0:
                 s0.append(p)
     return L1, L2, s0, s1
+
+
+# --------------------------------------------------------------------------
+# binary rank and select, one position at a time (Sections 4.1 and 4.2)
+# --------------------------------------------------------------------------
+
+def bv_rank(bits, i):
+    """Section 4.1: the number of ones among the first i bits."""
+    c = 0
+    for k in range(i):
+        c += 1 if bits[k] else 0
+    return c
+
+
+def bv_select(bits, b, j):
+    """Section 4.2: the position of the j-th (1-based) bit equal to b."""
+    seen = 0
+    for k, x in enumerate(bits):
+        if int(x) == b:
+            seen += 1
+            if seen == j:
+                return k
+    raise ValueError("fewer than j bits equal to b")

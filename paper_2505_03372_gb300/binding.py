@@ -29,7 +29,8 @@ EXPORTED = (
     "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
     "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
     "wt_mlp_gradient", "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync",
-    "wt_batch_tree", "wt_batch_bytes", "wt_batch_destroy", "wt_selftest_lookback_timeout",
+    "wt_batch_tree", "wt_batch_bytes", "wt_batch_destroy", "wt_selftest_lookback_timeout", "wt_bitvector_rank",
+    "wt_bitvector_select",
 )
 
 
@@ -110,6 +111,10 @@ def lib():
         L.wt_profile_report.restype = ctypes.c_size_t
         L.wt_bitvector_support_static.argtypes = [vp, u64, u32, vp, vp, vp, vp, u64, vp, vp]
         L.wt_bitvector_support_static.restype = ctypes.c_int
+        L.wt_bitvector_rank.argtypes = [vp, u64, vp, vp, vp, vp, u64, vp, vp]
+        L.wt_bitvector_rank.restype = ctypes.c_int
+        L.wt_bitvector_select.argtypes = [vp, u64, u64, u32, vp, vp, vp, vp, u32, vp, vp, u64, vp, vp]
+        L.wt_bitvector_select.restype = ctypes.c_int
         L.wt_train_select.argtypes = [vp, u32, ctypes.POINTER(TrainOptions), vp]
         L.wt_select_learned.argtypes = [vp, vp, vp, vp, u64, vp]
         L.wt_learned_info.argtypes = [vp, ctypes.POINTER(LearnedInfo)]
@@ -429,6 +434,82 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Bitvector:
+    """A device bitvector (uint64 words, LSB-first) with its rank/select support,
+    built by wt_bitvector_support_static; rank and select by wt_bitvector_rank /
+    wt_bitvector_select.  The words are copied into an allocation padded to
+    whole 512-bit blocks plus one."""
+
+    def __init__(self, words, nbits: int, sample_k: int = 4096, stream=None):
+        import torch
+
+        if not isinstance(words, torch.Tensor) or not words.is_cuda or words.dtype != torch.int64:
+            raise TypeError("words must be a CUDA int64 tensor")
+        nw = (nbits + 63) // 64
+        if words.numel() < nw:
+            raise ValueError("words holds fewer than nbits bits")
+        dev = words.device
+        self.nbits, self.sample_k = nbits, sample_k
+        self.words = torch.zeros((nbits // 512 + 1) * 8, dtype=torch.int64, device=dev)
+        self.words[:nw] = words[:nw]
+        if nbits % 64:
+            self.words[nw - 1] &= (1 << (nbits % 64)) - 1
+        self.l1 = torch.empty(nbits // 65536 + 1, dtype=torch.int64, device=dev)
+        self.l2 = torch.empty(nbits // 512 + 1, dtype=torch.int16, device=dev)
+        cap = nbits // sample_k + 2
+        self.s0 = torch.empty(cap, dtype=torch.int64, device=dev)
+        self.s1 = torch.empty(cap, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        _check(lib().wt_bitvector_support_static(self.words.data_ptr(), nbits, sample_k, self.l1.data_ptr(),
+                                                 self.l2.data_ptr(), self.s0.data_ptr(), self.s1.data_ptr(), cap,
+                                                 self.status.data_ptr(), _stream(stream)),
+               "wt_bitvector_support_static")
+        nwb = self.words.view(torch.uint8)[: (nbits + 7) // 8]
+        self.ones = int(self._popcount(nwb))
+
+    @staticmethod
+    def _popcount(b):
+        import torch
+
+        t = torch.tensor([bin(x).count("1") for x in range(256)], dtype=torch.int64, device=b.device)
+        return t[b.long()].sum().item()
+
+    def rank(self, i, out=None, stream=None):
+        import torch
+
+        q = i.numel()
+        if out is None:
+            out = torch.empty(q, dtype=torch.int64, device=i.device)
+        _check(lib().wt_bitvector_rank(self.words.data_ptr(), self.nbits, self.l1.data_ptr(), self.l2.data_ptr(),
+                                       _as_u64(i, "i"), _dptr(out, "out"), q, self.status.data_ptr(),
+                                       _stream(stream)), "wt_bitvector_rank")
+        return out
+
+    def select(self, b: int, j, out=None, stream=None):
+        import torch
+
+        q = j.numel()
+        if out is None:
+            out = torch.empty(q, dtype=torch.int64, device=j.device)
+        _check(lib().wt_bitvector_select(self.words.data_ptr(), self.nbits, self.ones, b, self.l1.data_ptr(),
+                                         self.l2.data_ptr(), self.s0.data_ptr(), self.s1.data_ptr(), self.sample_k,
+                                         _as_u64(j, "j"), _dptr(out, "out"), q, self.status.data_ptr(),
+                                         _stream(stream)), "wt_bitvector_select")
+        return out
+
+    def status_sync(self) -> int:
+        """Synchronise the device, return and clear the sticky status word."""
+        import torch
+
+        torch.cuda.synchronize()
+        v = int(self.status.item())
+        self.status.zero_()
+        for code in (WT_ETIMEOUT, WT_EQUERY):
+            if v & (1 << code):
+                return code
+        return WT_OK
 
 
 def mlp_gradient(params, u, t):

@@ -235,3 +235,46 @@ def make_batch(ntrees: int = 4096, seed: int = SEED_BASE + 3, device="cuda", log
         qa.append(torch.where(kind == 2, j, pos))
     queries = {"tree": torch.cat(qt), "kind": torch.cat(qk), "c": torch.cat(qc), "arg": torch.cat(qa)}
     return buf, views, sg, queries
+
+
+# --------------------------------------------------------------------------
+# standalone bitvectors (the paper's binary rank/select experiments, whose
+# bitvectors follow Kurpicz's generator: a fill of 10, 50 or 90 %, ones either
+# uniform or concentrated at the end)
+# --------------------------------------------------------------------------
+
+BITVECTOR_FILLS = (0.1, 0.5, 0.9)
+
+
+def make_bitvector(nbits: int, fill: float, layout: str = "uniform", seed: int = SEED_BASE + 5,
+                   device="cuda", chunk: int = 1 << 28) -> torch.Tensor:
+    """int64 words (LSB-first) of an nbits-bit vector.  "uniform": every bit is 1
+    with probability `fill`.  "adversarial": 99 % of the ones fall in the last
+    k·nbits positions, k = min(1, 0.99·fill / 0.95) (95 % ones there); the
+    remaining 1 % of the ones are spread uniformly over the rest.  Bits are drawn
+    chunk by chunk (a byte per bit) and packed 8 at a time."""
+    g = generator(seed, device)
+    nw = (nbits + 63) // 64
+    out = torch.zeros(nw * 8, dtype=torch.uint8, device=device)
+    weights = torch.tensor([1, 2, 4, 8, 16, 32, 64, 128], dtype=torch.int16, device=device)
+    tail0 = nbits
+    p_head = p_tail = fill
+    if layout == "adversarial":
+        k = min(1.0, 0.99 * fill / 0.95)
+        tail0 = int(nbits * (1.0 - k))
+        p_tail = min(1.0, 0.99 * fill / k) if k > 0 else 0.0
+        p_head = (0.01 * fill * nbits) / max(tail0, 1)
+    elif layout != "uniform":
+        raise ValueError(layout)
+    for s in range(0, nbits, chunk):
+        e = min(nbits, s + chunk)
+        pos = torch.arange(s, e, device=device)
+        thr = torch.where(pos < tail0, torch.full_like(pos, int(p_head * 65536)), torch.full_like(pos, int(p_tail * 65536)))
+        r = torch.randint(0, 65536, (e - s,), generator=g, device=device, dtype=torch.int64)
+        bits = (r < thr).to(torch.int16)
+        pad = (-bits.numel()) % 8
+        if pad:
+            bits = torch.cat([bits, torch.zeros(pad, dtype=torch.int16, device=device)])
+        packed = (bits.view(-1, 8) * weights).sum(1).to(torch.uint8)
+        out[s // 8: s // 8 + packed.numel()] = packed
+    return out.view(torch.int64)

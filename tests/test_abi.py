@@ -61,6 +61,10 @@ def test_host_argument_validation(libwt):
     assert libwt.wt_build(None, 0, 0, 1, ctypes.byref(opt), None, ctypes.byref(h)) == binding.WT_EINVAL
     assert libwt.wt_build(None, 0, 257, 1, ctypes.byref(opt), None, ctypes.byref(h)) == binding.WT_EINVAL
     assert libwt.wt_build(None, 0, (1 << 26) + 1, 4, ctypes.byref(opt), None, ctypes.byref(h)) == binding.WT_EINVAL
+    # the standalone bitvector queries reject an empty bitvector and null pointers
+    assert libwt.wt_bitvector_rank(None, 0, None, None, None, None, 1, None, None) == binding.WT_EINVAL
+    assert libwt.wt_bitvector_select(None, 0, 0, 1, None, None, None, None, 4096, None, None, 1, None,
+                                     None) == binding.WT_EINVAL
     # the host query pipeline rejects a null tree before touching anything
     assert libwt.wt_query_host(None, 0, None, None, None, None, 1, 0, None) == binding.WT_EINVAL
     bad_k = binding.Options(sample_k=1000)

@@ -359,3 +359,26 @@ def test_vectorised_predictors_equal_the_scalar_ones():
         assert (int(k0[idx]), int(k1[idx]), int(x0[idx]), int(x1[idx])) == kn
         assert int(pla[idx]) == mlp.predict_pla(kn, int(k[idx]))
         assert int(net[idx]) == mlp.predict_mlp_f32(kn, int(k[idx]), P)
+
+
+def test_bitvector_rank_select_by_brute_force():
+    """The oracle's binary rank/select against one-position-at-a-time loops, plus
+    the invariants rank_1(select_1(j)) = j - 1, B[select_b(j)] = b and
+    rank_1(i) + rank_0(i) = i."""
+    from oracle import brute
+
+    rng = np.random.default_rng(31)
+    for n, p in ((1, 0.5), (7, 0.0), (9, 1.0), (64, 0.3), (513, 0.5), (1000, 0.9)):
+        bits = (rng.random(n) < p).astype(np.uint8)
+        i = np.arange(n + 1)
+        want = np.array([brute.bv_rank(bits, k) for k in i], dtype=np.uint64)
+        assert np.array_equal(oracle.bv_rank(bits, i), want)
+        for b in (0, 1):
+            cnt = int((bits == b).sum())
+            j = np.arange(1, cnt + 1)
+            sel = oracle.bv_select(bits, b, j)
+            assert sel.tolist() == [brute.bv_select(bits, b, int(x)) for x in j]
+            assert np.all(bits[sel.astype(np.int64)] == b)
+            if b == 1 and cnt:
+                assert np.array_equal(oracle.bv_rank(bits, sel.astype(np.int64)), (j - 1).astype(np.uint64))
+        assert np.array_equal(oracle.bv_rank(bits, i) + oracle.bv_rank(1 - bits, i), i.astype(np.uint64))
