@@ -378,6 +378,25 @@ wt_status wt_bitvector_select(const uint64_t* d_words, uint64_t nbits, uint64_t 
                               uint64_t q, uint32_t* d_status, wt_stream stream);
 
 /*
+ * wt_alphabet — minimal-alphabet extraction (Section 6.2: a text's symbols
+ * mapped to [0, sigma) before the build when sigma is not known): sigma = the
+ * number of distinct values in d_symbols; d_out[k] = the rank of d_symbols[k]
+ * among those values, in the input's width (d_out == d_symbols is allowed);
+ * d_values (optional, device, room for min(n, 2^(8 w)) uint32) receives the
+ * distinct values in increasing order, so d_values[d_out[k]] == d_symbols[k].
+ * *h_sigma receives sigma; the call synchronises `stream` to read it.
+ * Method: a presence bitmap of 2^(8 w) bits, its rank/select support
+ * (wt_bitvector_support_static), rank for the mapping, select for d_values.
+ * Device memory from the stream-ordered pool: the bitmap and its support
+ * (about 32 B, 8 KiB or 560 MiB for w = 1, 2, 4), returned before the call ends.
+ *  d_symbols  device, n symbols of symbol_bytes (1, 2 or 4) bytes.
+ * n == 0 gives sigma = 0.  Null pointers, a width other than 1, 2, 4 or host
+ * memory return WT_EINVAL.
+ */
+wt_status wt_alphabet(const void* d_symbols, uint64_t n, uint32_t symbol_bytes, void* d_out, uint32_t* d_values,
+                      uint32_t* h_sigma, wt_stream stream);
+
+/*
  * wt_selftest_lookback_timeout — diagnostic for the bounded device waits.
  * Runs the build's decoupled look-back for a tile whose predecessor never
  * publishes its count, with at most spin_cap polls (1 <= spin_cap <= 2^22;

@@ -239,3 +239,10 @@ def bv_select(bits, b, j):
     b, for each j in [1, count_b]."""
     pos = np.flatnonzero(np.asarray(bits) == b)
     return pos[np.asarray(j, dtype=np.int64) - 1].astype(np.uint64)
+
+
+def alphabet_map(S):
+    """Minimal alphabet (Section 6.2): the distinct values of S in increasing
+    order and each symbol's rank among them (sorting, a library primitive)."""
+    values, inv = np.unique(np.asarray(S), return_inverse=True)
+    return inv.astype(np.int64), values

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwt.so")
-SOURCES = ["wt_build.cu", "wt_query.cu", "wt_api.cu", "wt_learned.cu", "wt_batch.cu", "wt_noalloc.cu", "wt_bitvec.cu"]
+SOURCES = ["wt_build.cu", "wt_query.cu", "wt_api.cu", "wt_learned.cu", "wt_batch.cu", "wt_noalloc.cu", "wt_bitvec.cu", "wt_alphabet.cu"]
 HEADERS = ["wt_common.cuh", "wt_internal.hpp", "wt_walk.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

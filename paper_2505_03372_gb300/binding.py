@@ -30,7 +30,7 @@ EXPORTED = (
     "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
     "wt_mlp_gradient", "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync",
     "wt_batch_tree", "wt_batch_bytes", "wt_batch_destroy", "wt_selftest_lookback_timeout", "wt_bitvector_rank",
-    "wt_bitvector_select",
+    "wt_bitvector_select", "wt_alphabet",
 )
 
 
@@ -115,6 +115,8 @@ def lib():
         L.wt_bitvector_rank.restype = ctypes.c_int
         L.wt_bitvector_select.argtypes = [vp, u64, u64, u32, vp, vp, vp, vp, u32, vp, vp, u64, vp, vp]
         L.wt_bitvector_select.restype = ctypes.c_int
+        L.wt_alphabet.argtypes = [vp, u64, u32, vp, vp, ctypes.POINTER(u32), vp]
+        L.wt_alphabet.restype = ctypes.c_int
         L.wt_train_select.argtypes = [vp, u32, ctypes.POINTER(TrainOptions), vp]
         L.wt_select_learned.argtypes = [vp, vp, vp, vp, u64, vp]
         L.wt_learned_info.argtypes = [vp, ctypes.POINTER(LearnedInfo)]
@@ -434,6 +436,25 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def alphabet(symbols, out=None, values: bool = True, stream=None):
+    """wt_alphabet: (symbols mapped to [0, sigma) in the input's width, the
+    distinct values in increasing order (uint32, or None), sigma)."""
+    import torch
+
+    w = {torch.uint8: 1, torch.int16: 2, torch.int32: 4}.get(symbols.dtype)
+    if w is None:
+        raise TypeError("symbols must be uint8, int16 or int32 (the bit patterns of u8/u16/u32 symbols)")
+    n = symbols.numel()
+    if out is None:
+        out = torch.empty_like(symbols)
+    vals = torch.empty(min(n, 1 << (8 * w)), dtype=torch.int32, device=symbols.device) if values and n else None
+    sigma = ctypes.c_uint32(0)
+    _check(lib().wt_alphabet(_dptr(symbols, "symbols") if n else None, n, w, _dptr(out, "out") if n else None,
+                             vals.data_ptr() if vals is not None else None, ctypes.byref(sigma), _stream(stream)),
+           "wt_alphabet")
+    return out, (vals[: sigma.value] if vals is not None else None), sigma.value
 
 
 class Bitvector:

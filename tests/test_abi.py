@@ -65,6 +65,11 @@ def test_host_argument_validation(libwt):
     assert libwt.wt_bitvector_rank(None, 0, None, None, None, None, 1, None, None) == binding.WT_EINVAL
     assert libwt.wt_bitvector_select(None, 0, 0, 1, None, None, None, None, 4096, None, None, 1, None,
                                      None) == binding.WT_EINVAL
+    # the alphabet extraction rejects a null sigma pointer and a bad width
+    assert libwt.wt_alphabet(None, 0, 1, None, None, None, None) == binding.WT_EINVAL
+    sig = ctypes.c_uint32(7)
+    assert libwt.wt_alphabet(None, 0, 3, None, None, ctypes.byref(sig), None) == binding.WT_EINVAL
+    assert libwt.wt_alphabet(None, 0, 1, None, None, ctypes.byref(sig), None) == binding.WT_OK and sig.value == 0
     # the host query pipeline rejects a null tree before touching anything
     assert libwt.wt_query_host(None, 0, None, None, None, None, 1, 0, None) == binding.WT_EINVAL
     bad_k = binding.Options(sample_k=1000)

@@ -382,3 +382,15 @@ def test_bitvector_rank_select_by_brute_force():
             if b == 1 and cnt:
                 assert np.array_equal(oracle.bv_rank(bits, sel.astype(np.int64)), (j - 1).astype(np.uint64))
         assert np.array_equal(oracle.bv_rank(bits, i) + oracle.bv_rank(1 - bits, i), i.astype(np.uint64))
+
+
+def test_alphabet_map_by_brute_force():
+    """The oracle's minimal-alphabet map against a set/sort over Python ints."""
+    rng = np.random.default_rng(5)
+    for n, hi in ((1, 10), (50, 7), (1000, 1 << 20), (300, 256)):
+        S = rng.integers(0, hi, n)
+        codes, values = oracle.alphabet_map(S)
+        want_vals = sorted(set(int(x) for x in S))
+        assert values.tolist() == want_vals
+        rank = {v: k for k, v in enumerate(want_vals)}
+        assert codes.tolist() == [rank[int(x)] for x in S]
