@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-sampled select comparison")
     ap.add_argument("--n", type=int, default=None, help="override the workload's n (small profiling cases)")
     ap.add_argument("--query-scale", type=float, default=1.0, help="scale the query counts (small profiling cases)")
+    ap.add_argument("--layout", default="tree", choices=["tree", "matrix"],
+                    help="level-wise wavelet tree (the paper's) or the wavelet matrix variant")
     return ap.parse_args()
 
 
@@ -239,8 +241,10 @@ def run_ours(args):
             outs[k.split("_")[0]] = torch.empty(v.numel(), dtype=torch.int64, device=dev)
     Q = sum(v.numel() for k, v in q.items() if k in ("access_i", "rank_i", "select_j", "mixed_arg"))
 
+    layout = wt.LAYOUT_MATRIX if args.layout == "matrix" else wt.LAYOUT_TREE
+
     def step(sym_dev, qd, od):
-        t = wt.build(sym_dev, wl.sigma, sample_k=wl.sample_k)
+        t = wt.build(sym_dev, wl.sigma, sample_k=wl.sample_k, layout=layout)
         if "access_i" in qd:
             t.access(qd["access_i"], out=od["access"])
         if "rank_i" in qd:
@@ -356,7 +360,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8" if w == 1 else f"u{8 * w}",
         "data": "synthetic", "impl": "ours",
-        "config": {"workload": wl.describe(), "queries_per_step_per_gpu": Q, "sample_k": wl.sample_k,
+        "config": {"workload": wl.describe() + ("; wavelet matrix layout" if args.layout == "matrix" else ""),
+                   "queries_per_step_per_gpu": Q, "sample_k": wl.sample_k,
                    "l2_flush": "inputs larger than L2 (1 GiB symbols, ~0.9 GiB tree, 0.5 GiB queries)",
                    "parallelism": "replicated build, sharded queries" if world > 1 else "1 GPU"},
         "phases": phases, "roofline": roof, "kernels": kern, "gpu_launches": launches, "clocks": clk,
@@ -502,7 +507,8 @@ def _e2e(args, wl, sym, q, outs, step, barrier, dist, world, Q):
             main.wait_event(ev_in[b])
             if k + 1 < nsteps:
                 copy_in(k + 1)
-            t = wt.build(d_sym[b], wl.sigma, sample_k=wl.sample_k)
+            t = wt.build(d_sym[b], wl.sigma, sample_k=wl.sample_k,
+                         layout=wt.LAYOUT_MATRIX if args.layout == "matrix" else wt.LAYOUT_TREE)
             ev_used[b].record(main)
             # queries and answers: the host query pipeline (wt_query_host), whose
             # copies overlap the build and the other batches' walks

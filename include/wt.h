@@ -58,8 +58,18 @@ typedef struct {
     uint32_t sample_k; /* select sample interval K: the position of every K-th one and every K-th
                           zero is stored (Section 4.2).  Power of two in [256, 2^20]; default 4096,
                           the value of the paper's wavelet-tree experiments (Section 6.3). */
-    uint32_t reserved[7];
+    uint32_t layout;   /* WT_LAYOUT_TREE (0, default): the level-wise wavelet tree with reduced
+                          codes (Sections 5.1-5.4).  WT_LAYOUT_MATRIX (1): the wavelet matrix the
+                          paper names as future work (Section 7): plain L-bit codes, every level
+                          one stable partition of the whole level by its bit (zeros first); the
+                          same queries, answered by walking with the per-level zero counts.
+                          wt_train_select / wt_select_learned and WT_EXPORT_NODES / LENS are
+                          WT_EUNSUPPORTED on a matrix. */
+    uint32_t reserved[6];
 } wt_options;
+
+#define WT_LAYOUT_TREE 0u
+#define WT_LAYOUT_MATRIX 1u
 
 /* Size of the rank blocks (Section 4.1): L1 blocks of 65536 bits with a 64-bit
  * count of ones before the block; L2 blocks of 512 bits with a 16-bit count of
@@ -176,6 +186,8 @@ typedef struct {
     uint64_t level_size[WT_MAX_LEVELS]; /* bits in level l = #symbols whose code is longer than l */
     uint64_t level_ones[WT_MAX_LEVELS];
     uint64_t tree_bytes;   /* device bytes held by the tree */
+    uint32_t layout;       /* WT_LAYOUT_TREE or WT_LAYOUT_MATRIX */
+    uint32_t reserved;
 } wt_info_t;
 
 /* Host-side metadata; no device work. */

@@ -246,3 +246,47 @@ def alphabet_map(S):
     order and each symbol's rank among them (sorting, a library primitive)."""
     values, inv = np.unique(np.asarray(S), return_inverse=True)
     return inv.astype(np.int64), values
+
+
+# --------------------------------------------------------------------------
+# the wavelet matrix (the variant named as future work in Section 7)
+# --------------------------------------------------------------------------
+
+class OMatrix:
+    """Wavelet matrix by definition: plain L-bit codes (L = ceil(lg sigma));
+    level 0 holds S, B_l[i] = bit L-1-l of the level's i-th symbol, and level
+    l+1 is level l stably partitioned by that bit, zeros first (a stable sort
+    on one bit, a library primitive).  Rank counters and select samples follow
+    Sections 4.1 and 4.2, computed from prefix sums."""
+
+    def __init__(self, S: np.ndarray, sigma: int, K: int = 4096):
+        self.L = int(sigma - 1).bit_length() if sigma > 1 else 0
+        self.K = K
+        seq = np.asarray(S).astype(np.int64)
+        self.levels = []
+        for l in range(self.L):
+            bits = ((seq >> (self.L - 1 - l)) & 1).astype(np.uint8)
+            self.levels.append(bits)
+            seq = seq[np.argsort(bits, kind="stable")]
+
+    def zeros(self, l):
+        return int((self.levels[l] == 0).sum())
+
+    def export(self, what: int, level: int = 0) -> np.ndarray:
+        bits = self.levels[level]
+        n = bits.size
+        pre = np.concatenate([[0], np.cumsum(bits.astype(np.int64))])
+        if what == 0:  # bits as LSB-first uint64 words
+            pad = np.zeros((n + 63) // 64 * 64, np.uint8)
+            pad[:n] = bits
+            return np.packbits(pad, bitorder="little").view(np.uint64)
+        if what == 1:  # L1: ones in B[0, 65536 k)
+            return pre[np.arange(n // 65536 + 1) * 65536].astype(np.uint64)
+        if what == 2:  # L2: ones from the enclosing L1 block's start to 512 m
+            m = np.arange(n // 512 + 1) * 512
+            return (pre[m] - pre[(m // 65536) * 65536]).astype(np.uint16)
+        if what in (3, 4):  # S0 / S1: [0] = 0, [m] = position of the (m K)-th b-bit
+            pos = np.flatnonzero(bits == (what - 3))
+            m = np.arange(1, pos.size // self.K + 1)
+            return np.concatenate([[0], pos[m * self.K - 1]]).astype(np.uint64)
+        raise ValueError(what)

@@ -109,3 +109,16 @@ def bv_select(bits, b, j):
             if seen == j:
                 return k
     raise ValueError("fewer than j bits equal to b")
+
+
+def matrix_levels(S, sigma):
+    """Wavelet matrix levels by list manipulation: level l's bit of every
+    symbol, then the symbols with bit 0 in order followed by those with bit 1."""
+    L = (sigma - 1).bit_length() if sigma > 1 else 0
+    seq = [int(x) for x in S]
+    levels = []
+    for l in range(L):
+        sh = L - 1 - l
+        levels.append([(x >> sh) & 1 for x in seq])
+        seq = [x for x in seq if not (x >> sh) & 1] + [x for x in seq if (x >> sh) & 1]
+    return levels

@@ -40,8 +40,11 @@ class WTError(RuntimeError):
         super().__init__(f"{what}: {status_str(status)}" if what else status_str(status))
 
 
+LAYOUT_TREE, LAYOUT_MATRIX = 0, 1
+
+
 class Options(ctypes.Structure):
-    _fields_ = [("sample_k", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+    _fields_ = [("sample_k", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
 
 
 class Info(ctypes.Structure):
@@ -54,6 +57,8 @@ class Info(ctypes.Structure):
         ("level_size", ctypes.c_uint64 * MAX_LEVELS),
         ("level_ones", ctypes.c_uint64 * MAX_LEVELS),
         ("tree_bytes", ctypes.c_uint64),
+        ("layout", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -198,7 +203,7 @@ class Tree:
         t.levels = t.info().levels
         return t
 
-    def __init__(self, symbols, sigma: int, sample_k: int = 4096, stream=None):
+    def __init__(self, symbols, sigma: int, sample_k: int = 4096, stream=None, layout: int = 0):
         import torch
 
         if not symbols.is_cuda or symbols.dim() != 1:
@@ -211,7 +216,7 @@ class Tree:
         self.sigma = int(sigma)
         self.symbol_bytes = w
         self._stream = stream
-        opt = Options(sample_k=sample_k)
+        opt = Options(sample_k=sample_k, layout=layout)
         h = ctypes.c_void_p()
         ptr = self._keep.data_ptr() if self.n else None
         st = lib().wt_build(ptr, self.n, self.sigma, w, ctypes.byref(opt), _stream(stream), ctypes.byref(h))
@@ -367,9 +372,10 @@ class Tree:
         return out.reshape(-1, 4) if what == EXPORT_NODES else out
 
 
-def build(symbols, sigma: int, sample_k: int = 4096, stream=None) -> Tree:
-    """wt_build: construct the tree of a 1-D CUDA tensor of symbols in [0, sigma)."""
-    return Tree(symbols, sigma, sample_k=sample_k, stream=stream)
+def build(symbols, sigma: int, sample_k: int = 4096, stream=None, layout: int = LAYOUT_TREE) -> Tree:
+    """wt_build: construct the tree (or, with layout=LAYOUT_MATRIX, the wavelet
+    matrix) of a 1-D CUDA tensor of symbols in [0, sigma)."""
+    return Tree(symbols, sigma, sample_k=sample_k, stream=stream, layout=layout)
 
 
 class Batch:

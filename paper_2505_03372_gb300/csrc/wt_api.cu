@@ -170,13 +170,15 @@ wt_status wt_build(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t s
     }
     uint32_t K = (opt && opt->sample_k) ? opt->sample_k : 4096u;
     if (K < 256 || K > (1u << 20) || (K & (K - 1))) return WT_EINVAL;
+    const uint32_t layout = opt ? opt->layout : WT_LAYOUT_TREE;
+    if (layout != WT_LAYOUT_TREE && layout != WT_LAYOUT_MATRIX) return WT_EINVAL;
 
     wt_tree_s* t = new wt_tree_s();
     memset(&t->desc, 0, sizeof(t->desc));
     cudaGetDevice(&t->device);
     t->stream = stream;
     t->magic = kTreeMagic;
-    wt_status st = build_tree(d_symbols, n, sigma, symbol_bytes, K, stream, t);
+    wt_status st = build_tree(d_symbols, n, sigma, symbol_bytes, K, stream, t, layout);
     if (st != WT_OK) {
         dev_free(t->hdr_mem, stream);
         dev_free(t->lvl_mem, stream);
@@ -382,6 +384,7 @@ wt_status wt_info(wt_tree tree, wt_info_t* out) {
         out->level_ones[l] = tree->level_ones[l];
     }
     out->tree_bytes = tree->hdr_bytes + tree->lvl_bytes;
+    out->layout = tree->desc.layout;
     return WT_OK;
 }
 
@@ -396,6 +399,7 @@ wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, ui
         cnt = sigma + 1ull;
         src = d.C;
     } else if (what == WT_EXPORT_CODES || what == WT_EXPORT_LENS) {
+        if (d.layout == WT_LAYOUT_MATRIX && what == WT_EXPORT_LENS) return WT_EUNSUPPORTED;
         cnt = sigma;
         *count = cnt;
         if (h_dst) {
@@ -408,6 +412,7 @@ wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, ui
         }
         return WT_OK;
     } else if (what == WT_EXPORT_NODES) {
+        if (d.layout == WT_LAYOUT_MATRIX) return WT_EUNSUPPORTED;
         cnt = L ? ((1ull << L) - 1) : 0;
         *count = cnt;
         if (h_dst && cnt) {

@@ -1085,10 +1085,47 @@ static cudaError_t launch_hist(const void* S, uint64_t n, uint32_t sigma, unsign
 
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
+// Wavelet matrix: the zeros of every level from C (symbols whose bit L-1-l is 0
+// form runs [k 2^(b+1), k 2^(b+1) + 2^b) of the alphabet), one block per level;
+// meta as for the tree (size n, zeros) and a one-entry "node" per level whose
+// partition offsets send the zeros to [0, Z_l) and the ones to [Z_l, n).
+__global__ void __launch_bounds__(256) matrix_meta_kernel(const uint64_t* __restrict__ C, uint32_t sigma, uint32_t L,
+                                                          uint64_t n, uint64_t* __restrict__ meta,
+                                                          NodeEntry* __restrict__ mnodes) {
+    const uint32_t l = blockIdx.x, b = L - 1 - l;
+    const uint64_t run = 1ull << b, period = run << 1;
+    uint64_t z = 0;
+    for (uint64_t k = threadIdx.x; k * period < sigma; k += blockDim.x) {
+        const uint64_t a = k * period;
+        z += C[umin64(sigma, a + run)] - C[a];
+    }
+    __shared__ uint64_t ws[8];
+    z = warp_sum_u64(z);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = z;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t zz = 0;
+        for (int k = 0; k < 8; k++) zz += ws[k];
+        meta[2 * l] = n;
+        meta[2 * l + 1] = zz;
+        NodeEntry e = {0, 0, 0, zz};
+        mnodes[l] = e;
+    }
+}
+
 wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t w, uint32_t sample_k, cudaStream_t s,
-                     wt_tree_s* t) {
-    const CodeParams cp = make_code_params(sigma);
+                     wt_tree_s* t, uint32_t layout) {
+    const bool matrix = layout == WT_LAYOUT_MATRIX;
+    CodeParams cp = make_code_params(sigma);
+    if (matrix) {  // plain L-bit codes: encode gives code = symbol, length L
+        cp.pow2 = true;
+        cp.r = 1;
+        cp.e[0] = cp.L;
+        cp.P[0] = 0;
+        cp.P[1] = 1ull << cp.L;
+    }
     const uint32_t L = cp.L;
+    t->desc.layout = layout;
     uint32_t k_log2 = 0;
     while ((1u << k_log2) < sample_k) k_log2++;
 
@@ -1099,7 +1136,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     t->sample_k = sample_k;
 
     // ---- header memory: status, C, node table, meta ----
-    const uint64_t nslots = L ? ((1ull << L) - 1) : 0;
+    const uint64_t nslots = matrix ? L : (L ? ((1ull << L) - 1) : 0);  // the matrix: one entry per level
     size_t off_status = 0;
     size_t off_C = 256;
     size_t off_nodes = align_up(off_C + (sigma + 1ull) * 8, 256);
@@ -1164,7 +1201,10 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     // 2. C
     device_exclusive_scan(hist, C, sigma, tmp, s);
     // 3. nodes + meta
-    if (L) {
+    if (L && matrix) {
+        ProfScope ps("meta", s);
+        matrix_meta_kernel<<<L, 256, 0, s>>>(C, sigma, L, n, meta, nodes);
+    } else if (L) {
         {
             ProfScope ps("node_start", s);
             node_start_kernel<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(cp, C, nodes, left, nslots);
@@ -1282,13 +1322,13 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.s1 = reinterpret_cast<uint64_t*>(M + lay[l].s1);
             a.n_s0 = ((size - t->level_ones[l]) >> k_log2) + 1;
             a.n_s1 = (t->level_ones[l] >> k_log2) + 1;
-            a.nodes = nodes + ((1ull << l) - 1);
+            a.nodes = matrix ? nodes + l : nodes + ((1ull << l) - 1);
             a.state = state;
             a.counter = counters + l;
             a.status = t->desc.status;
             a.level = l;
             a.shift_bit = L - 1 - l;
-            a.pshift = L - l;
+            a.pshift = matrix ? 32 : L - l;  // the matrix: every tile lies in the level's one node
             a.k_log2 = k_log2;
             a.cp = cp;
             a.ctab_n = w == 1 ? 256u : ((uint64_t)sigma * w <= kCodeTableBytes) ? sigma : 0;

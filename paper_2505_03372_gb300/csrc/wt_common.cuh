@@ -180,7 +180,7 @@ struct TreeDesc {
     CodeParams cp;
     uint64_t n;
     uint32_t k_log2;  // select sample interval K = 2^k_log2
-    uint32_t pad;
+    uint32_t layout;  // 0: level-wise tree; 1: wavelet matrix (zeros of level l = lv[l].size - lv[l].ones)
     const NodeEntry* nodes;
     const uint64_t* C;  // sigma + 1
     uint32_t* status;

@@ -537,6 +537,7 @@ extern "C" {
 
 wt_status wt_train_select(wt_tree tree, uint32_t mode, const wt_train_options* opt, wt_stream stream) {
     if (!tree_valid(tree) || mode > kLearnMlp) return WT_EINVAL;
+    if (tree->desc.layout == WT_LAYOUT_MATRIX) return WT_EUNSUPPORTED;
     const uint32_t steps = (opt && opt->steps) ? opt->steps : 300;
     const float lr = (opt && opt->lr > 0.f) ? opt->lr : 1e-2f;
     const uint32_t pairs = (opt && opt->pairs) ? opt->pairs : 8192;

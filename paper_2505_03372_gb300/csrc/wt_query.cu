@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kQThreads) access_kernel(const __grid_constant
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < q; k += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i = __ldg(qi + k);
         const bool bad = i >= t.n;
-        out[ORD ? __ldg(idx + k) : k] = bad ? UINT32_MAX : do_access(t, nc, i);
+        out[ORD ? __ldg(idx + k) : k] = bad ? UINT32_MAX : (t.layout ? do_access_m(t, i) : do_access(t, nc, i));
         flag_query_error(t, bad);
     }
 }
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kQThreads) rank_kernel(const __grid_constant__
         const uint32_t c = __ldg(qc + k);
         const uint64_t i = __ldg(qi + k);
         const bool bad = c >= t.cp.sigma || i > t.n;
-        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : do_rank(t, nc, c, i);
+        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : (t.layout ? do_rank_m(t, c, i) : do_rank(t, nc, c, i));
         flag_query_error(t, bad);
     }
 }
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kQThreads) select_kernel(const __grid_constant
         const uint32_t c = __ldg(qc + k);
         const uint64_t j = __ldg(qj + k);
         const bool bad = !select_valid(t, c, j);
-        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : do_select(t, nc, c, j);
+        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : (t.layout ? do_select_m(t, c, j) : do_select(t, nc, c, j));
         flag_query_error(t, bad);
     }
 }
@@ -96,15 +96,15 @@ __global__ void __launch_bounds__(kQThreads) mixed_kernel(const __grid_constant_
         bool bad;
         if (kd == 0) {
             bad = x >= t.n;
-            if (!bad) r = do_access(t, nc, x);
+            if (!bad) r = (t.layout ? do_access_m(t, x) : do_access(t, nc, x));
         } else if (kd == 1) {
             const uint32_t c = __ldg(qc + k);
             bad = c >= t.cp.sigma || x > t.n;
-            if (!bad) r = do_rank(t, nc, c, x);
+            if (!bad) r = (t.layout ? do_rank_m(t, c, x) : do_rank(t, nc, c, x));
         } else if (kd == 2) {
             const uint32_t c = __ldg(qc + k);
             bad = !select_valid(t, c, x);
-            if (!bad) r = do_select(t, nc, c, x);
+            if (!bad) r = (t.layout ? do_select_m(t, c, x) : do_select(t, nc, c, x));
         } else {
             bad = true;
         }
@@ -337,6 +337,7 @@ wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_k
 constexpr uint32_t kNodeCacheSlots = 2048;  // levels 0..10: 32 KB of {start, r0}
 
 static uint32_t cache_slots(const wt_tree_s* t) {
+    if (t->desc.layout != 0) return 0;  // a wavelet matrix has no node table to cache
     const uint32_t L = t->desc.cp.L;
     const uint64_t nslots = L ? (1ull << L) - 1 : 0;
     return (uint32_t)(nslots < kNodeCacheSlots ? nslots : kNodeCacheSlots);

@@ -85,6 +85,62 @@ __device__ __forceinline__ uint64_t do_select(const TreeDesc& t, const NodeCache
     return j - 1;
 }
 
+// ---------------------------------------------------------------------------
+// Wavelet matrix (layout 1): plain L-bit codes; level l+1 holds level l's
+// zeros first (in order) and its ones after them, so a position moves down by
+// rank_0, or by Z_l + rank_1 (Z_l = zeros of level l), and up by select.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t do_access_m(const TreeDesc& t, uint64_t i) {
+    uint32_t code = 0;
+    for (uint32_t l = 0; l < t.cp.L; l++) {
+        const LevelDesc& lv = t.lv[l];
+        uint32_t b;
+        const uint64_t r1 = rank1_bit(lv, i, b);
+        code = (code << 1) | b;
+        i = b ? (lv.size - lv.ones) + r1 : i - r1;
+    }
+    return code;
+}
+
+// rank_c(i): the range [s, e) of level-l positions above [0, i) of c's run
+__device__ __forceinline__ uint64_t do_rank_m(const TreeDesc& t, uint32_t c, uint64_t i) {
+    uint64_t s = 0, e = i;
+    for (uint32_t l = 0; l < t.cp.L; l++) {
+        const LevelDesc& lv = t.lv[l];
+        const uint32_t b = (c >> (t.cp.L - 1 - l)) & 1u;
+        const uint64_t r1s = rank1(lv, s), r1e = rank1(lv, e);
+        if (b) {
+            const uint64_t z = lv.size - lv.ones;
+            s = z + r1s;
+            e = z + r1e;
+        } else {
+            s -= r1s;
+            e -= r1e;
+        }
+    }
+    return e - s;
+}
+
+// select_c(j): down to the start of c's run below the last level, then up
+__device__ __forceinline__ uint64_t do_select_m(const TreeDesc& t, uint32_t c, uint64_t j) {
+    const uint32_t L = t.cp.L;
+    uint64_t s = 0;
+    for (uint32_t l = 0; l < L; l++) {
+        const LevelDesc& lv = t.lv[l];
+        const uint32_t b = (c >> (L - 1 - l)) & 1u;
+        const uint64_t r1 = rank1(lv, s);
+        s = b ? (lv.size - lv.ones) + r1 : s - r1;
+    }
+    uint64_t p = s + j - 1;
+    for (int l = (int)L - 1; l >= 0; l--) {
+        const LevelDesc& lv = t.lv[l];
+        const uint32_t b = (c >> (L - 1 - (uint32_t)l)) & 1u;
+        p = b ? select_b(lv, 1, p - (lv.size - lv.ones) + 1, t.k_log2) : select_b(lv, 0, p + 1, t.k_log2);
+    }
+    return p;
+}
+
 // Copy the first `slots` {start, r0} pairs of the node table into shared memory
 // (every thread of the CTA calls this; it ends with a barrier).
 __device__ __forceinline__ NodeCache load_node_cache(const TreeDesc& t, ulonglong2* s, uint32_t slots) {

@@ -394,3 +394,25 @@ def test_alphabet_map_by_brute_force():
         assert values.tolist() == want_vals
         rank = {v: k for k, v in enumerate(want_vals)}
         assert codes.tolist() == [rank[int(x)] for x in S]
+
+
+def test_wavelet_matrix_oracle_by_brute_force():
+    """The oracle's wavelet matrix levels against list-based stable partitions,
+    its counters and samples against counting, and the matrix identity that
+    level l+1 is level l's zeros followed by its ones."""
+    rng = np.random.default_rng(12)
+    for n, sigma, K in ((1, 2, 256), (37, 5, 256), (2000, 96, 256), (5000, 1000, 256), (70000, 3, 256)):
+        S = rng.integers(0, sigma, n)
+        om = oracle.OMatrix(S, sigma, K)
+        bl = brute.matrix_levels(S, sigma)
+        assert len(om.levels) == len(bl)
+        for l, bits in enumerate(bl):
+            assert om.levels[l].tolist() == bits
+            L1, L2, s0, s1 = brute.counters(bits, K)
+            assert om.export(1, l).tolist() == L1
+            assert om.export(2, l).tolist() == L2
+            assert om.export(3, l).tolist() == s0
+            assert om.export(4, l).tolist() == s1
+            words = om.export(0, l)
+            assert np.unpackbits(words.view(np.uint8), bitorder="little")[:n].tolist() == bits
+            assert om.zeros(l) == bits.count(0)
