@@ -113,6 +113,21 @@ wt_status wt_build(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t s
 void wt_destroy(wt_tree tree);
 
 /*
+ * wt_build_host — wt_build from symbols in host memory (pinned or pageable),
+ * the chunked construction the paper proposes (Section 7): the symbols are
+ * copied to the device in 64 MiB chunks on an internal copy stream that does
+ * not wait for work already queued on `stream`, and the histogram counts each
+ * chunk on `stream` as it arrives, so the copy overlaps earlier work on the
+ * stream and the histogram; the level passes then run as in wt_build.  The
+ * device copy of the symbols comes from the stream-ordered pool and is returned
+ * after the build; h_symbols must stay valid until the call returns (it
+ * synchronises once, as wt_build does).  Arguments and results as wt_build;
+ * a device pointer as h_symbols returns WT_EINVAL.
+ */
+wt_status wt_build_host(const void* h_symbols, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                        const wt_options* opt, wt_stream stream, wt_tree* out);
+
+/*
  * wt_access — Algorithm 5: d_out[k] = S[d_i[k]] for k < q.
  *  d_i    device, q positions; a position >= n yields UINT32_MAX and WT_EQUERY.
  *  d_out  device, q symbols (uint32).

@@ -25,7 +25,7 @@ MAX_LEVELS = 26
 
 # every symbol include/wt.h declares (checked by the ABI test)
 EXPORTED = (
-    "wt_build", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_query_host", "wt_status_sync",
+    "wt_build", "wt_build_host", "wt_destroy", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_query_host", "wt_status_sync",
     "wt_info", "wt_export", "wt_status_str", "wt_profile_enable", "wt_profile_reset", "wt_profile_launches",
     "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
     "wt_mlp_gradient", "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync",
@@ -94,6 +94,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
         L.wt_build.argtypes = [vp, u64, u32, u32, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+        L.wt_build_host.argtypes = [vp, u64, u32, u32, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
         L.wt_destroy.argtypes = [vp]
         L.wt_destroy.restype = None
         L.wt_access.argtypes = [vp, vp, vp, u64, vp]
@@ -139,7 +140,7 @@ def lib():
         L.wt_batch_destroy.restype = None
         L.wt_selftest_lookback_timeout.argtypes = [u32, vp]
         L.wt_selftest_lookback_timeout.restype = ctypes.c_int
-        for f in ("wt_build", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_query_host", "wt_status_sync",
+        for f in ("wt_build", "wt_build_host", "wt_access", "wt_rank", "wt_select", "wt_query_mixed", "wt_query_host", "wt_status_sync",
                   "wt_info",
                   "wt_export", "wt_train_select", "wt_select_learned", "wt_learned_info", "wt_mlp_gradient",
                   "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync", "wt_batch_tree"):
@@ -206,8 +207,8 @@ class Tree:
     def __init__(self, symbols, sigma: int, sample_k: int = 4096, stream=None, layout: int = 0):
         import torch
 
-        if not symbols.is_cuda or symbols.dim() != 1:
-            raise TypeError("symbols must be a 1-D CUDA tensor")
+        if symbols.dim() != 1:
+            raise TypeError("symbols must be a 1-D tensor")
         w = symbols.element_size()
         if w not in (1, 2, 4) or symbols.dtype.is_floating_point:
             raise TypeError("symbols must be an integer tensor of 1, 2 or 4 bytes per element")
@@ -219,7 +220,9 @@ class Tree:
         opt = Options(sample_k=sample_k, layout=layout)
         h = ctypes.c_void_p()
         ptr = self._keep.data_ptr() if self.n else None
-        st = lib().wt_build(ptr, self.n, self.sigma, w, ctypes.byref(opt), _stream(stream), ctypes.byref(h))
+        # a CPU tensor (pinned or pageable) goes through wt_build_host: chunked copy overlapping the histogram
+        build_fn = lib().wt_build if symbols.is_cuda else lib().wt_build_host
+        st = build_fn(ptr, self.n, self.sigma, w, ctypes.byref(opt), _stream(stream), ctypes.byref(h))
         self._keep = None  # the input is not retained after the call (it has synchronised once)
         _check(st, "wt_build")
         self._h = h

@@ -136,6 +136,17 @@ static bool is_device_ptr(const void* p) {
 
 static bool tree_ok(const wt_tree_s* t) { return t && t->magic == kTreeMagic; }
 
+// True if p is host memory (pinned or pageable), not device or managed memory.
+static bool is_host_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // unknown to CUDA: ordinary pageable memory
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
 }  // namespace wt
 
 using namespace wt;
@@ -179,6 +190,60 @@ wt_status wt_build(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t s
     t->stream = stream;
     t->magic = kTreeMagic;
     wt_status st = build_tree(d_symbols, n, sigma, symbol_bytes, K, stream, t, layout);
+    if (st != WT_OK) {
+        dev_free(t->hdr_mem, stream);
+        dev_free(t->lvl_mem, stream);
+        t->magic = 0;
+        delete t;
+        return st;
+    }
+    *out = t;
+    return WT_OK;
+}
+
+wt_status wt_build_host(const void* h_symbols, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                        const wt_options* opt, wt_stream stream, wt_tree* out) {
+    if (!out) return WT_EINVAL;
+    *out = nullptr;
+    if (symbol_bytes != 1 && symbol_bytes != 2 && symbol_bytes != 4) return WT_EINVAL;
+    if (sigma == 0 || sigma > (1u << kMaxSigmaLog)) return WT_EINVAL;
+    if (symbol_bytes < 4 && (uint64_t)sigma > (1ull << (8 * symbol_bytes))) return WT_EINVAL;
+    if (n >= (1ull << 40)) return WT_EINVAL;
+    if (n && !is_host_ptr(h_symbols)) return WT_EINVAL;
+    uint32_t K = (opt && opt->sample_k) ? opt->sample_k : 4096u;
+    if (K < 256 || K > (1u << 20) || (K & (K - 1))) return WT_EINVAL;
+    const uint32_t layout = opt ? opt->layout : WT_LAYOUT_TREE;
+    if (layout != WT_LAYOUT_TREE && layout != WT_LAYOUT_MATRIX) return WT_EINVAL;
+    // The device copy is allocated on the copy stream (stream-ordered: usable
+    // there at once, and by `stream` after the per-chunk events), so the copies
+    // need not wait for the work already queued on `stream`.
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return WT_ECUDA;
+    void* d_buf = nullptr;
+    if (n && dev_alloc(&d_buf, n * symbol_bytes, cs) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return WT_ENOMEM;
+    }
+    wt_tree_s* t = new wt_tree_s();
+    memset(&t->desc, 0, sizeof(t->desc));
+    cudaGetDevice(&t->device);
+    t->stream = stream;
+    t->magic = kTreeMagic;
+    wt_status st = build_tree(d_buf, n, sigma, symbol_bytes, K, stream, t, layout, h_symbols, cs);
+    if (n) {
+        // `stream` has waited for every chunk (or the build failed before the
+        // copies: then order the free after the copy stream's work too)
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, cs);
+            cudaStreamWaitEvent(stream, ev, 0);
+            cudaEventDestroy(ev);
+        } else {
+            cudaStreamSynchronize(cs);
+        }
+    }
+    dev_free(d_buf, stream);  // stream-ordered: after the level passes that read it
+    cudaStreamDestroy(cs);
     if (st != WT_OK) {
         dev_free(t->hdr_mem, stream);
         dev_free(t->lvl_mem, stream);
@@ -236,17 +301,6 @@ wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_
 // ---------------------------------------------------------------------------
 
 namespace {
-
-// True if p is host memory (pinned or pageable), not device or managed memory.
-bool is_host_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return true;  // unknown to CUDA: ordinary pageable memory
-    }
-    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
-}
 
 struct HostPipe {
     cudaStream_t h2d = nullptr, d2h = nullptr;

@@ -1114,7 +1114,7 @@ __global__ void __launch_bounds__(256) matrix_meta_kernel(const uint64_t* __rest
 }
 
 wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t w, uint32_t sample_k, cudaStream_t s,
-                     wt_tree_s* t, uint32_t layout) {
+                     wt_tree_s* t, uint32_t layout, const void* h_src, cudaStream_t cs) {
     const bool matrix = layout == WT_LAYOUT_MATRIX;
     CodeParams cp = make_code_params(sigma);
     if (matrix) {  // plain L-bit codes: encode gives code = symbol, length L
@@ -1189,13 +1189,36 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     WT_CUDA_TRY(cudaMemsetAsync(hist, 0, (uint64_t)sigma * 8, s));
     WT_CUDA_TRY(cudaMemsetAsync(tcnt0, 0, std::max<uint64_t>(tiles0, 1) * 8, s));
 
-    // 1. histogram
+    // 1. histogram (with a host source: chunk by chunk as the chunks arrive, the
+    // copy of chunk k+1 on a copy stream overlapping the histogram of chunk k)
     if (n) {
         unsigned long long* hh = (unsigned long long*)hist;
-        unsigned long long* tc = L ? tcnt0 : nullptr;
-        cudaError_t e = w == 1   ? launch_hist<uint8_t>(d_symbols, n, sigma, hh, t->desc.status, m0, tc, s)
-                        : w == 2 ? launch_hist<uint16_t>(d_symbols, n, sigma, hh, t->desc.status, m0, tc, s)
-                                 : launch_hist<uint32_t>(d_symbols, n, sigma, hh, t->desc.status, m0, tc, s);
+        auto hist_part = [&](uint64_t off, uint64_t len) {
+            const void* src = static_cast<const uint8_t*>(d_symbols) + off * w;
+            unsigned long long* tc = L ? tcnt0 + off * w / kTileBytes : nullptr;  // off is a whole number of tiles
+            return w == 1   ? launch_hist<uint8_t>(src, len, sigma, hh, t->desc.status, m0, tc, s)
+                   : w == 2 ? launch_hist<uint16_t>(src, len, sigma, hh, t->desc.status, m0, tc, s)
+                            : launch_hist<uint32_t>(src, len, sigma, hh, t->desc.status, m0, tc, s);
+        };
+        cudaError_t e = cudaSuccess;
+        if (h_src) {
+            const uint64_t chunk = (64ull << 20) / w;  // 64 MiB: a whole number of 32 KiB tiles
+            for (uint64_t off = 0; off < n && e == cudaSuccess; off += chunk) {
+                const uint64_t len = std::min(chunk, n - off);
+                cudaEvent_t ev = nullptr;
+                e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(static_cast<uint8_t*>(const_cast<void*>(d_symbols)) + off * w,
+                                        static_cast<const uint8_t*>(h_src) + off * w, len * w,
+                                        cudaMemcpyHostToDevice, cs);
+                if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+                if (ev) cudaEventDestroy(ev);
+                if (e == cudaSuccess) e = hist_part(off, len);
+            }
+        } else {
+            e = hist_part(0, n);
+        }
         if (e != cudaSuccess) { dev_free(scratch, s); return WT_ECUDA; }
     }
     // 2. C

@@ -48,9 +48,12 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);
 
 // ---- build (wt_build.cu) ----
-// layout: WT_LAYOUT_TREE or WT_LAYOUT_MATRIX
+// layout: WT_LAYOUT_TREE or WT_LAYOUT_MATRIX.  h_src (optional): host symbols to
+// copy into d_symbols (a device buffer of n symbols, allocated on the copy
+// stream cs) chunk by chunk on cs during the histogram.
 wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t w, uint32_t sample_k,
-                     cudaStream_t s, wt_tree_s* t, uint32_t layout = 0);
+                     cudaStream_t s, wt_tree_s* t, uint32_t layout = 0, const void* h_src = nullptr,
+                     cudaStream_t cs = nullptr);
 
 // out[k] = sum of in[0..k) for k <= count (count + 1 entries); tmp holds
 // 2 * (ceil(count / 8192) + 1) entries

@@ -70,6 +70,9 @@ def test_host_argument_validation(libwt):
     sig = ctypes.c_uint32(7)
     assert libwt.wt_alphabet(None, 0, 3, None, None, ctypes.byref(sig), None) == binding.WT_EINVAL
     assert libwt.wt_alphabet(None, 0, 1, None, None, ctypes.byref(sig), None) == binding.WT_OK and sig.value == 0
+    # the host-input build rejects a null out-pointer and a bad width
+    assert libwt.wt_build_host(None, 0, 4, 1, ctypes.byref(opt), None, None) == binding.WT_EINVAL
+    assert libwt.wt_build_host(None, 0, 4, 3, ctypes.byref(opt), None, ctypes.byref(h)) == binding.WT_EINVAL
     # the host query pipeline rejects a null tree before touching anything
     assert libwt.wt_query_host(None, 0, None, None, None, None, 1, 0, None) == binding.WT_EINVAL
     bad_k = binding.Options(sample_k=1000)

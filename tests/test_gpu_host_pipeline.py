@@ -140,3 +140,24 @@ def test_query_host_rejects_device_memory():
         torch.cuda.synchronize()
         assert h_out.numpy().view(np.uint32)[0] == sym[0].item()
         assert t.status_sync() == wt.WT_OK
+
+
+@pytest.mark.parametrize("w,n,sigma,pinned", [(1, (1 << 27) + 12345, 96, True), (2, (1 << 25) + 7, 65536, False),
+                                              (4, 300001, 70000, True), (1, 1, 2, False)])
+def test_build_from_host_memory_equals_device_build(w, n, sigma, pinned):
+    """wt_build_host (64 MiB chunks copied while the histogram runs) builds the
+    same tree as wt_build on the same symbols, level by level."""
+    sym = workloads.make_symbols(n, sigma, w, "zipf" if sigma < 1000 else "uniform", 1.0, seed=n % 1000 + w,
+                                 device="cuda")
+    h = sym.cpu()
+    if pinned:
+        h = h.pin_memory()
+    with wt.build(sym, sigma) as td, wt.build(h, sigma) as th:
+        a, b = td.info(), th.info()
+        assert a.levels == b.levels
+        for l in range(a.levels):
+            assert a.level_size[l] == b.level_size[l] and a.level_ones[l] == b.level_ones[l]
+            for what in (wt.EXPORT_BITS, wt.EXPORT_L1, wt.EXPORT_L2, wt.EXPORT_S0, wt.EXPORT_S1):
+                assert np.array_equal(td.export(what, l), th.export(what, l)), (l, what)
+        assert np.array_equal(td.export(wt.EXPORT_C), th.export(wt.EXPORT_C))
+        assert th.status_sync() == wt.WT_OK
