@@ -3,7 +3,8 @@
 //
 // Pipeline (all on the device, one stream):
 //   1. histogram of S with symbol validation (Section 5.1.1: shared-memory
-//      sub-histograms, persistent grid);
+//      sub-histograms, persistent grid), which also counts the level-0 ones of
+//      every 32 KiB tile;
 //   2. C = exclusive prefix sum of the histogram;
 //   3. node table: for every node (depth l, code prefix p) its start C[a],
 //      the precomputed rank_0 at the start (Section 5.2.1) and the two
@@ -15,9 +16,12 @@
 //      rank counters (Section 4.1) and its select samples (Section 4.2), and
 //      stably partition T_l by the level bit into T_{l+1} -- the radix-sort step
 //      of Algorithm 4 done as a one-bit split per level.  The global prefix of
-//      ones that the counters and the partition need comes from a decoupled
-//      look-back over tiles, so every level reads T_l once and writes T_{l+1}
-//      once.
+//      ones each tile needs for the counters and the partition is an exclusive
+//      scan of per-tile counts that the pass before gathered while writing T_l
+//      (the histogram for level 0), so every level reads T_l once and writes
+//      T_{l+1} once.  Batches of trees (wt_batch.cu) find the prefix by a
+//      decoupled look-back over tiles instead.
+//   The wavelet matrix layout uses the same passes with one node per level.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
