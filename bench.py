@@ -36,6 +36,34 @@ UNIT = "Mqueries/s"
 PEAK_FALLBACK_GBS = 6800.0
 
 
+# --------------------------------------------------------------------------
+# multi-rank bookkeeping (torchrun, one process per GPU): every rank builds the
+# same tree from the same seed and answers its own query batch; the step time
+# is the slowest rank's, the value counts every rank's queries
+# --------------------------------------------------------------------------
+
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of a rank's own query batch (rank 0 keeps the single-GPU seed)."""
+    return base + 7919 * rank
+
+
+def job_ms(ms: float, dist) -> float:
+    """The step time of the job: the maximum over ranks (all ranks return it)."""
+    if dist is None:
+        return ms
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world: int, q_per_rank: int, ms: float) -> float:
+    """Whole-job throughput in Mqueries/s: every rank's queries over the job's step time."""
+    return world * q_per_rank / (ms * 1e-3) / 1e6
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,7 +259,7 @@ def run_ours(args):
     sym = workloads.make_symbols(wl.n, wl.sigma, wl.symbol_bytes, wl.dist, wl.zipf_s,
                                  seed=workloads.SEED_BASE + wl.index, device="cuda")
     counts = workloads.symbol_counts(sym, wl.sigma)
-    q = workloads.make_queries(wl, sym, seed=workloads.SEED_BASE + 0x100 + wl.index + 7919 * rank, counts=counts)
+    q = workloads.make_queries(wl, sym, seed=rank_seed(workloads.SEED_BASE + 0x100 + wl.index, rank), counts=counts)
     dev = torch.device("cuda", local)
     outs = {}
     for k, v in q.items():
@@ -289,12 +317,8 @@ def run_ours(args):
     launches = wt.profile_launches()
     rep = wt.profile_report()
     wt.profile_enable(False)
-    ms_step = ms_total / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
-    value = world * Q / (ms_step * 1e-3) / 1e6
+    ms_step = job_ms(ms_total / args.steps, dist)
+    value = job_value(world, Q, ms_step)
 
     # ---- phases and roofline of the dominant kernel ----
     peak, peak_kind = peaks()
@@ -513,16 +537,12 @@ def _e2e(args, wl, sym, q, outs, step, barrier, dist, world, Q):
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = job_ms(e0.elapsed_time(e1) / args.steps, dist)
     # the answers of the last step, checked against the device-resident run
     for k in h_out:
         if not torch.equal(h_out[k], outs[k].cpu()):
             raise RuntimeError(f"e2e answers differ from the device-resident run ({k})")
-    return {"value": world * Q / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+    return {"value": job_value(world, Q, ms), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h,
             "path": "pinned host symbols -> wt_build_host (64 MiB chunks copied while the histogram runs; the "
                     "next step's copy overlaps this step's passes) ; pinned host queries -> wt_query_host (chunked "
@@ -552,7 +572,7 @@ def run_batched(args):
     from paper_2505_03372_gb300 import autotune, binding as wt, workloads
 
     ntrees = int(args.n) if args.n else 4096
-    buf, views, sigmas, q = workloads.make_batch(ntrees=ntrees, seed=workloads.SEED_BASE + 3 + 7919 * rank)
+    buf, views, sigmas, q = workloads.make_batch(ntrees=ntrees, seed=rank_seed(workloads.SEED_BASE + 3, rank))
     t0 = time.perf_counter()
     opts = autotune.tune_batch(views, sigmas, q)
     tune_s = time.perf_counter() - t0
@@ -580,11 +600,7 @@ def run_batched(args):
             dist.barrier()
         clk = clocks.stop() if clocks else None
         launches = wt.profile_launches() - launches0
-        ms = e0.elapsed_time(e1) / args.steps
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = job_ms(e0.elapsed_time(e1) / args.steps, dist)
         # algorithmic bytes of one step: every tree's level-wise build plus the query sectors
         K = opts["sample_k"]
         bbytes = 0
@@ -621,7 +637,7 @@ def run_batched(args):
         nbytes = b.nbytes()
     h2d = h_buf.numel() * h_buf.element_size() + sum(v.numel() * v.element_size() for v in h_q.values())
     line = {
-        "metric": METRIC, "value": world * Q / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": job_value(world, Q, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u16", "data": "synthetic", "impl": "ours",
         "config": {"workload": f"{ntrees} trees, n log-uniform [2^10, 2^24] uint16 (total {nsym}), sigma from "
