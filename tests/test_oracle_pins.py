@@ -416,3 +416,24 @@ def test_wavelet_matrix_oracle_by_brute_force():
             words = om.export(0, l)
             assert np.unpackbits(words.view(np.uint8), bitorder="little")[:n].tolist() == bits
             assert om.zeros(l) == bits.count(0)
+
+
+def test_bitvector_generator_layouts():
+    """The bitvector inputs have the stated fills and layouts: uniform ones at the
+    fill rate; adversarial ones 99 % within the last min(1, 0.99 fill / 0.95) of
+    the positions.  (Sampling only; checked on the CPU with a small vector.)"""
+    torch = pytest.importorskip("torch")
+    from paper_2505_03372_gb300 import workloads
+
+    n = 400_003
+    for fill in workloads.BITVECTOR_FILLS:
+        u = workloads.make_bitvector(n, fill, "uniform", seed=7, device="cpu")
+        bits = np.unpackbits(u.numpy().view(np.uint8), bitorder="little")
+        assert bits[n:].sum() == 0
+        assert abs(bits[:n].mean() - fill) < 0.01
+        a = workloads.make_bitvector(n, fill, "adversarial", seed=7, device="cpu")
+        bits = np.unpackbits(a.numpy().view(np.uint8), bitorder="little")[:n]
+        k = min(1.0, 0.99 * fill / 0.95)
+        tail = bits[int(n * (1 - k)):]
+        assert abs(bits.mean() - fill) < 0.01
+        assert tail.sum() >= 0.985 * bits.sum()
