@@ -561,6 +561,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
     __shared__ uint64_t s_E, s_EL1, s_p;
     __shared__ uint32_t s_single;
     __shared__ uint32_t s_nc[4];  // ones of T_{l+1} written by this tile: per run, in its first / second tile
+    __shared__ uint32_t s_wpre[kTileBytes / 8 / W / 8];  // per 64-bit word of level bits: ones before it in its group
     __shared__ uint32_t s_gcnt[64];
     __shared__ uint32_t s_gnext;
 
@@ -756,6 +757,16 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
                 if (lane >= o) inc += t;
             }
             const uint32_t ex = inc - c;
+            {
+                // the lane that starts a 64-bit word of level bits records the
+                // ones before that word in its group (for the sample search)
+                constexpr uint32_t LPW = 64 / VEPL;  // lanes per word
+                constexpr uint32_t WPG = GE / 64;    // words per group
+                if ((lane % LPW) == 0) {
+                    s_wpre[g * WPG + lane / LPW] = ex & 0xFFFFu;
+                    s_wpre[(g + 1) * WPG + lane / LPW] = ex >> 16;
+                }
+            }
             const uint32_t ga = __shfl_sync(0xffffffffu, rp0, g >> 1), gb = __shfl_sync(0xffffffffu, rp1, g >> 1);
             const uint32_t oba = ga + (ex & 0xFFFFu), obb = gb + (ex >> 16);
             const uint32_t ja = g * GE + lane * VEPL, jb = ja + GE;
@@ -837,7 +848,11 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             const uint64_t x = w64[t];
             const uint32_t g = t / WPG;
             uint32_t pre = rpre[g];  // ones of the tile before word t
-            for (uint32_t k = g * WPG; k < t; k++) pre += __popcll(w64[k]);
+            if (a.dst != nullptr && a.tile_excl != nullptr) {
+                pre += s_wpre[t];  // recorded by the partition
+            } else {
+                for (uint32_t k = g * WPG; k < t; k++) pre += __popcll(w64[k]);
+            }
             const uint32_t nv = count - t * 64;
             const uint64_t valid = nv >= 64 ? ~0ull : ((1ull << nv) - 1ull);
             const uint64_t z = ~x & valid;
