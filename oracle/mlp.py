@@ -6,6 +6,12 @@ packed as {w1[32], b1[32], w2[32], b2}.  The loss is the mean squared error of
 u + g(u) against the position fraction t.  Forward and backward passes are
 written out by hand; the backward pass is pinned by central finite
 differences in tests/test_oracle_pins.py.
+
+The FP32 predictor (``predict_mlp_f32`` and its array form) repeats the
+kernel's chain of correctly rounded operations; its fused multiply-add
+(``fma_f32``) rounds once, and it is pinned by exact rational arithmetic, by
+the FP64 forward pass within the FP32 error bound, and by hand-computed
+values of a one-unit network (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 
@@ -74,17 +80,55 @@ def predict_pla(kn, k):
     return x0 + ((k - k0) * (x1 - x0)) // (k1 - k0)
 
 
+def fma_f32(a, b, c):
+    """Fused multiply-add of float32 values rounded once to float32 (round to
+    nearest, ties to even), as CUDA's __fmaf_rn computes it; elementwise.
+
+    The product a*b of two float32 values is exact in float64 (at most 48
+    significant bits).  The sum p + c is formed in float64 with round-to-odd:
+    the round-to-nearest sum s and its exact error e (Knuth's TwoSum) give the
+    exact value s + e; when e != 0 and s's last significand bit is even, s is
+    replaced by its float64 neighbour towards e.  Rounding a round-to-odd value
+    with at least two more significand bits (53 >= 24 + 2) to float32 equals
+    rounding the exact value once (Boldo and Melquiond, "Emulation of FMA and
+    correctly rounded sums: proved algorithms using rounding to odd", IEEE
+    Trans. Computers 57(4), 2008).
+    """
+    a = np.asarray(a, np.float32).astype(np.float64)
+    b = np.asarray(b, np.float32).astype(np.float64)
+    c = np.asarray(c, np.float32).astype(np.float64)
+    p = a * b
+    s = p + c
+    pv = s - c
+    cv = s - pv
+    e = (p - pv) + (c - cv)
+    even = (s.view(np.int64) & 1) == 0
+    fix = (e != 0) & even
+    s_odd = np.where(fix, np.nextafter(s, np.where(e > 0, np.inf, -np.inf)), s)
+    return s_odd.astype(np.float32)
+
+
+def _mlp_h_f32(u, P):
+    """u + g(u) in the kernel's FP32 operation order: a_j = fma(w1_j, u, b1_j),
+    y = fma(w2_j, max(a_j, 0), y) for j = 0..31 starting at y = b2, then u + y."""
+    P = np.asarray(P, np.float32)
+    u = np.asarray(u, np.float32)
+    y = np.full(u.shape, P[3 * H], np.float32)
+    for j in range(H):
+        a = fma_f32(P[j], u, P[H + j])
+        y = fma_f32(P[2 * H + j], np.maximum(a, np.float32(0)), y)
+    return (u + y).astype(np.float32)
+
+
 def predict_mlp_f32(kn, k, P):
-    """The same prediction in emulated FP32 (products and sums rounded to float32 at each step)."""
+    """Position predicted by the network for rank k in segment kn, in the
+    kernel's FP32 arithmetic: u = (k - k0) / (k1 - k0) rounded to float32,
+    h = clamp(u + g(u), 0, 1), offset = trunc(float32(x1 - x0) * h), capped
+    at x1 - x0."""
     k0, k1, x0, x1 = kn
     f = np.float32
-    P = np.asarray(P, np.float32)
     u = f(f(k - k0) / f(k1 - k0))
-    y = P[3 * H]
-    for j in range(H):
-        a = f(np.float64(P[j]) * np.float64(u) + np.float64(P[H + j]))
-        y = f(np.float64(P[2 * H + j]) * np.float64(max(a, f(0))) + np.float64(y))
-    hh = f(min(max(f(u + y), f(0)), f(1)))
+    hh = f(min(max(_mlp_h_f32(u, P)[()], f(0)), f(1)))
     span = x1 - x0
     off = int(f(f(span) * hh))
     return x0 + min(off, span)
@@ -111,15 +155,8 @@ def predict_pla_all(k, k0, k1, x0, x1):
 def predict_mlp_f32_all(k, k0, k1, x0, x1, P):
     """``predict_mlp_f32`` for arrays of ranks (same rounding steps, elementwise)."""
     f = np.float32
-    P = np.asarray(P, np.float32)
-    u = (f(1) * (k - k0).astype(np.float32)) / (k1 - k0).astype(np.float32)
-    u = u.astype(np.float32)
-    u64 = u.astype(np.float64)
-    y = np.full(u.shape, P[3 * H], np.float32)
-    for j in range(H):
-        a = (np.float64(P[j]) * u64 + np.float64(P[H + j])).astype(np.float32)
-        y = (np.float64(P[2 * H + j]) * np.maximum(a, f(0)).astype(np.float64) + y.astype(np.float64)).astype(np.float32)
-    hh = np.clip((u + y).astype(np.float32), f(0), f(1)).astype(np.float32)
+    u = ((k - k0).astype(np.float32) / (k1 - k0).astype(np.float32)).astype(np.float32)
+    hh = np.clip(_mlp_h_f32(u, P), f(0), f(1)).astype(np.float32)
     span = x1 - x0
     off = (span.astype(np.float32) * hh).astype(np.float32).astype(np.int64)
     return x0 + np.minimum(off, span)

@@ -361,6 +361,125 @@ def test_vectorised_predictors_equal_the_scalar_ones():
         assert int(net[idx]) == mlp.predict_mlp_f32(kn, int(k[idx]), P)
 
 
+def _round_f32_exact(x):
+    """Round the rational x to float32 (round to nearest, ties to even), from
+    the definition of the format: 24 significant bits, exponents down to -126,
+    subnormals spaced 2^-149 apart."""
+    from fractions import Fraction
+
+    if x == 0:
+        return 0.0
+    sgn = -1 if x < 0 else 1
+    ax = abs(Fraction(x))
+    e = ax.numerator.bit_length() - ax.denominator.bit_length()
+    while Fraction(2) ** e > ax:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= ax:
+        e += 1
+    ulp = Fraction(2) ** (max(e, -126) - 23)
+    q, r = divmod(ax, ulp)
+    if r * 2 > ulp or (r * 2 == ulp and q % 2 == 1):
+        q += 1
+    return sgn * float(q * ulp)
+
+
+def test_fma_f32_rounds_once():
+    """fma_f32 against exact rational arithmetic: random operands, and
+    constructed sums that sit just below or above a float32 rounding midpoint
+    (where rounding in float64 first, then to float32, goes the wrong way)."""
+    from fractions import Fraction
+
+    from oracle import mlp
+
+    rng = np.random.default_rng(21)
+    a = rng.normal(size=3000).astype(np.float32)
+    b = (rng.normal(size=3000) * 10.0 ** rng.integers(-8, 8, 3000)).astype(np.float32)
+    c = (rng.normal(size=3000) * 10.0 ** rng.integers(-8, 8, 3000)).astype(np.float32)
+    f = np.float32
+    one_p = f(1 + 2 ** -23)
+    below_mid = f(2 ** -24 * (1 - 2 ** -23))  # (1 + 2^-23) * this = 2^-24 - 2^-70
+    a = np.concatenate([a, [one_p, one_p, -one_p, one_p]]).astype(np.float32)
+    b = np.concatenate([b, [below_mid, below_mid, below_mid, f(2 ** -24)]]).astype(np.float32)
+    c = np.concatenate([c, [one_p, f(1.0), -one_p, one_p]]).astype(np.float32)
+    got = mlp.fma_f32(a, b, c)
+    for i in range(a.size):
+        exact = Fraction(float(a[i])) * Fraction(float(b[i])) + Fraction(float(c[i]))
+        assert float(got[i]) == _round_f32_exact(exact), (i, a[i], b[i], c[i])
+    # the constructed case: exact value 1 + 2^-23 + 2^-24 - 2^-70 rounds down to
+    # 1 + 2^-23, while float64 first gives the midpoint and then 1 + 2^-22
+    assert float(got[3000]) == 1 + 2 ** -23
+    naive = (a[3000].astype(np.float64) * b[3000].astype(np.float64) + c[3000].astype(np.float64)).astype(np.float32)
+    assert float(naive) == 1 + 2 ** -22
+
+
+def test_mlp_forward_of_a_one_unit_network():
+    """g(u) = b2 + sum_j w2_j relu(w1_j u + b1_j) with the packing {w1, b1, w2, b2},
+    by hand for one active unit: w1 = 2, b1 = -0.5, w2 = 3, b2 = 0.25."""
+    from oracle import mlp
+
+    P = np.zeros(mlp.NPARAM)
+    P[0], P[mlp.H], P[2 * mlp.H], P[3 * mlp.H] = 2.0, -0.5, 3.0, 0.25
+    y, _, _ = mlp.forward(P, np.array([0.1, 0.25, 0.5, 1.0]))
+    assert np.allclose(y, [0.25, 0.25, 1.75, 4.75], rtol=0, atol=1e-15)
+
+
+def test_mlp_predictor_hand_values_and_edges():
+    """predict_mlp_f32 for w1 = 1, b1 = 0, w2 = 0.5, b2 = 0 (h = 1.5 u, all
+    values exact in float32), the clamp of h to [0, 1] on both sides, and the
+    cap of the offset at the span when float32(span) rounds up."""
+    from oracle import mlp
+
+    P = np.zeros(mlp.NPARAM, np.float32)
+    P[0], P[2 * mlp.H] = 1.0, 0.5
+    kn = (0, 8, 100, 164)
+    assert mlp.predict_mlp_f32(kn, 0, P) == 100
+    assert mlp.predict_mlp_f32(kn, 2, P) == 124  # u = 0.25, h = 0.375, 64 * 0.375 = 24
+    assert mlp.predict_mlp_f32(kn, 4, P) == 148  # u = 0.5, h = 0.75
+    assert mlp.predict_mlp_f32(kn, 6, P) == 164  # u = 0.75, h = 1.125 -> 1
+    P2 = P.copy()
+    P2[3 * mlp.H] = -0.5  # h = 1.5 u - 0.5 < 0 below u = 1/3
+    assert mlp.predict_mlp_f32(kn, 2, P2) == 100
+    assert mlp.predict_mlp_f32(kn, 4, P2) == 116  # h = 0.25
+    span = (1 << 25) - 1  # float32(span) = 2^25 > span
+    assert mlp.predict_mlp_f32((0, 8, 7, 7 + span), 7, P) == 7 + span
+    # the array form agrees on the same points
+    k = np.array([0, 2, 4, 6], np.int64)
+    z = np.zeros(4, np.int64)
+    got = mlp.predict_mlp_f32_all(k, z, z + 8, z + 100, z + 164, P)
+    assert got.tolist() == [100, 124, 148, 164]
+
+
+def test_mlp_predictor_within_fp32_bound_of_fp64_forward():
+    """The FP32 chain against the FP64 network on random parameters: |h32 - h64|
+    stays within the forward error bound of 2 (H + 2) ulps of the magnitudes
+    involved, and the position within span * that bound + 2."""
+    from oracle import mlp
+
+    rng = np.random.default_rng(33)
+    u_max = 0.0
+    for trial in range(20):
+        P = (rng.normal(size=mlp.NPARAM) * 0.5).astype(np.float32)
+        k0, span_k = 4096 * trial, int(rng.integers(2, 9000))
+        x0, span_x = int(rng.integers(0, 1 << 30)), int(rng.integers(1, 1 << 24))
+        kn = (k0, k0 + span_k, x0, x0 + span_x)
+        for k in rng.integers(k0, k0 + span_k, 40):
+            k = int(k)
+            u32 = np.float32(np.float32(k - k0) / np.float32(span_k))
+            u = float(u32)
+            h32 = float(mlp._mlp_h_f32(u32, P))
+            y64, _, _ = mlp.forward(P.astype(np.float64), np.array([u]))
+            h64 = u + float(y64[0])
+            w1, b1, w2, b2 = mlp.unpack(P.astype(np.float64))
+            mag = abs(u) + abs(b2) + float(np.sum(np.abs(w2) * (np.abs(w1) * abs(u) + np.abs(b1))))
+            bound = 2.0 * (mlp.H + 2) * 2.0 ** -24 * mag
+            assert abs(h32 - h64) <= bound, (trial, k, h32, h64, bound)
+            pos = mlp.predict_mlp_f32(kn, k, P)
+            ref = x0 + min(span_x, int(np.floor(span_x * min(max(h64, 0.0), 1.0))))
+            assert abs(pos - ref) <= span_x * bound + 2 * span_x * 2.0 ** -24 + 2, (trial, k, pos, ref)
+            u_max = max(u_max, u)
+    assert u_max > 0.9
+
+
 def test_bitvector_rank_select_by_brute_force():
     """The oracle's binary rank/select against one-position-at-a-time loops, plus
     the invariants rank_1(select_1(j)) = j - 1, B[select_b(j)] = b and
