@@ -8,9 +8,11 @@
  *
  * Conventions shared by every entry point
  *  - Pointers named d_* are device pointers (cudaMalloc / cudaMallocAsync /
- *    PyTorch CUDA tensors); h_* are host pointers.  The caller owns them; the
- *    library never frees or retains them past the call (or, for asynchronous
- *    calls, past the completion of the work it enqueued on `stream`).
+ *    PyTorch CUDA tensors) of the current device, or managed memory; h_* are
+ *    host pointers.  Device memory of another GPU is refused (WT_EINVAL).
+ *    The caller owns them; the library never frees or retains them past
+ *    the call (or, for asynchronous calls, past the completion of the work
+ *    it enqueued on `stream`).
  *  - `stream` is a CUDA stream (the same type as cudaStream_t); NULL means the
  *    legacy default stream.  Work is enqueued on it; calls return before the
  *    GPU finishes unless stated otherwise.
@@ -53,6 +55,32 @@ typedef enum {
     WT_EUNSUPPORTED = 7 /* operation not available for this tree (e.g. no trained select model) */
 } wt_status;
 
+/*
+ * Device memory supplied by the caller (for example PyTorch's caching
+ * allocator), so that the tree and every scratch buffer live in the caller's
+ * pool.  Not part of the paper; an interface convention of this library.
+ *  alloc(bytes, stream, ctx)  returns device memory of at least `bytes` bytes on
+ *        the current device, 256-byte aligned, that work enqueued on `stream`
+ *        after the call may use; NULL when it cannot (the call that asked then
+ *        returns WT_ENOMEM after releasing what it had allocated).
+ *  free(ptr, stream, ctx)  returns a block: the library has enqueued its last use
+ *        of it on `stream`, the stream it was allocated on, so it may be handed
+ *        out again to work ordered after that point on that stream.
+ * Every block is released on the stream it was taken on: the caller's
+ * `stream`, or, for the staging buffers of wt_build_host and wt_query_host,
+ * the library's own copy stream of the device (taken there so that the
+ * copies overlap work already queued on `stream`; released there after that
+ * stream has waited for the buffer's last use).
+ * The struct is copied; ctx and the functions must stay valid until the last
+ * handle built with them is destroyed.  The callbacks run on the calling
+ * thread, inside the library call.
+ */
+typedef struct {
+    void* (*alloc)(size_t bytes, wt_stream stream, void* ctx);
+    void (*free)(void* ptr, wt_stream stream, void* ctx);
+    void* ctx;
+} wt_allocator;
+
 /* Build options.  Zero-initialised fields take the default. */
 typedef struct {
     uint32_t sample_k; /* select sample interval K: the position of every K-th one and every K-th
@@ -65,7 +93,10 @@ typedef struct {
                           same queries, answered by walking with the per-level zero counts.
                           wt_train_select / wt_select_learned and WT_EXPORT_NODES / LENS are
                           WT_EUNSUPPORTED on a matrix. */
-    uint32_t reserved[6];
+    const wt_allocator* allocator; /* NULL: the device's stream-ordered pool (cudaMallocAsync).  Else the
+                          tree, the build's scratch, the query ordering's scratch, the host pipeline's
+                          buffers and the learned-select tables all come from it. */
+    uint32_t reserved[4];
 } wt_options;
 
 #define WT_LAYOUT_TREE 0u
@@ -119,8 +150,9 @@ void wt_destroy(wt_tree tree);
  * not wait for work already queued on `stream`, and the histogram counts each
  * chunk on `stream` as it arrives, so the copy overlaps earlier work on the
  * stream and the histogram; the level passes then run as in wt_build.  The
- * device copy of the symbols comes from the stream-ordered pool and is returned
- * after the build; h_symbols must stay valid until the call returns (it
+ * device copy of the symbols comes from the allocator in opt (or the
+ * stream-ordered pool), taken and returned on the library's copy stream after
+ * the build; h_symbols must stay valid until the call returns (it
  * synchronises once, as wt_build does).  Arguments and results as wt_build;
  * a device pointer as h_symbols returns WT_EINVAL.
  */
@@ -182,8 +214,9 @@ wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_
  * copy overlaps it.  The call returns once everything is queued; h_out holds
  * the answers after `stream` has been synchronised, and the host buffers must
  * stay valid until then.  Data errors are reported as for the device calls.
- * Device memory: two chunks of arguments and answers, from the stream-ordered
- * pool, returned when the last copy-out completes.
+ * Device memory: two chunks of arguments and answers, from the tree's allocator
+ * (or the stream-ordered pool), taken and returned on the library's copy
+ * stream, after the last copy-out.
  */
 wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, const uint32_t* h_c,
                         const uint64_t* h_arg, void* h_out, uint64_t q, uint64_t chunk, wt_stream stream);
@@ -302,7 +335,8 @@ wt_status wt_learned_info(wt_tree tree, wt_learned_info_t* out);
  *             tree's symbols; the buffers must stay valid while the batch runs.
  *  h_n, h_sigma  host arrays of sizes and alphabet sizes (limits as wt_build).
  *  opt        sample_k as in wt_options; query_threads 128, 256 or 512 threads
- *             per CTA of the query kernel (default 256); NULL for defaults.
+ *             per CTA of the query kernel (default 256); lp_ctas_per_sm the
+ *             level pass's persistent grid; NULL for defaults.
  * Queries: d_tree[k] < ntrees selects the tree, then d_kind / d_c / d_arg /
  * d_out as in wt_query_mixed.  A tree index >= ntrees yields UINT64_MAX.
  * wt_batch_status_sync reports the OR of every tree's sticky status.
@@ -314,7 +348,11 @@ wt_status wt_learned_info(wt_tree tree, wt_learned_info_t* out);
 typedef struct {
     uint32_t sample_k;
     uint32_t query_threads;
-    uint32_t reserved[6];
+    const wt_allocator* allocator; /* NULL: cudaMalloc; else the batch's one allocation comes from it
+                                      (allocated and released on the legacy default stream) */
+    uint32_t lp_ctas_per_sm;       /* CTAs per SM of the persistent batched level pass: 1, 2 or 3
+                                      (0: 3, the most that fit) */
+    uint32_t reserved[3];
 } wt_batch_options;
 
 wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const uint64_t* h_n, const uint32_t* h_sigma,
@@ -360,14 +398,19 @@ wt_status wt_mlp_gradient(const float* h_params, const float* h_u, const float* 
  *  sample_capacity  at least floor(nbits / sample_k) + 2
  *  d_status  optional device word; WT_ETIMEOUT's bit (1 << WT_ETIMEOUT) is OR-ed
  *         into it if a bounded device wait gave up.
+ *  d_ones optional device word; receives the number of ones of the bitvector
+ *         (the count wt_bitvector_select takes).
  * Limits: 1 <= nbits <= 2^32 (the size of the static scratch); larger or
  * empty inputs, a sample_k that is not a power of two in [256, 2^20], a too
- * small sample_capacity or a pointer that is not device memory return
- * WT_EINVAL before any work is enqueued.  No cudaMalloc, cudaFree or other
- * allocating call is made.
+ * small sample_capacity or a pointer that is not device memory of the current
+ * device return WT_EINVAL before any work is enqueued; so does a CUDA error
+ * left pending on the calling thread by earlier work (WT_ECUDA).  No
+ * cudaMalloc, cudaFree or other allocating call is made.
  * The first call on a device looks up the device address of the static
  * scratch (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  Every call on a device shares the scratch,
+ * call before any stream capture.  The address is kept per device together
+ * with the identity of the context it belongs to; after a device reset the
+ * next call sees a new context and looks the address up again.  Every call on a device shares the scratch,
  * which keeps the last call's contents; each call clears what must start at
  * zero.  Calls whose work overlaps on the GPU (different streams, or a call
  * issued while another is still running) race on the scratch and give wrong
@@ -376,7 +419,7 @@ wt_status wt_mlp_gradient(const float* h_params, const float* h_u, const float* 
  */
 wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64_t nbits, uint32_t sample_k, uint64_t* d_l1,
                                       uint16_t* d_l2, uint64_t* d_s0, uint64_t* d_s1, uint64_t sample_capacity,
-                                      uint32_t* d_status, wt_stream stream);
+                                      uint32_t* d_status, uint64_t* d_ones, wt_stream stream);
 
 /*
  * wt_bitvector_rank / wt_bitvector_select — binary rank (Section 4.1,

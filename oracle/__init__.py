@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     """Compile the C oracle into ``oracle/liboracle.so`` with gcc."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -52,6 +52,12 @@ def lib():
         L.orc_o1_select.argtypes = [_u64p, _u64p, ctypes.c_uint32, _u32p, _u64p, ctypes.c_uint64, _u64p]
         L.orc_o2_build.argtypes = [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
         L.orc_o2_build.restype = _vp
+        L.orc_o2_build_mt.argtypes = [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]
+        L.orc_o2_build_mt.restype = _vp
+        L.orc_o2_query_mt.argtypes = [_vp, ctypes.c_int, _u32p, _u64p, ctypes.c_uint64, _vp, ctypes.c_int]
+        L.orc_o2_query_mt.restype = None
+        L.orc_default_threads.argtypes = []
+        L.orc_default_threads.restype = ctypes.c_int
         L.orc_o2_free.argtypes = [_vp]
         L.orc_o2_levels.argtypes = [_vp]
         L.orc_o2_levels.restype = ctypes.c_uint32
@@ -154,14 +160,23 @@ _EXPORT_DTYPE = {0: np.uint64, 1: np.uint64, 2: np.uint16, 3: np.uint64, 4: np.u
                  5: np.uint64, 6: np.uint64, 7: np.uint8, 8: np.uint64}
 
 
-class O2Tree:
-    """Naive level-wise wavelet tree (reduced codes, |L1| = 65536, |L2| = 512)."""
+def default_threads() -> int:
+    """Host threads the O2 build and the threaded query loops use by default
+    (the online CPUs)."""
+    return int(lib().orc_default_threads())
 
-    def __init__(self, S: np.ndarray, sigma: int, K: int = 4096):
+
+class O2Tree:
+    """Naive level-wise wavelet tree (reduced codes, |L1| = 65536, |L2| = 512).
+
+    ``threads``: host threads for the build's counting sorts (0: all online
+    CPUs; inputs below 2^16 symbols use one).  The tree does not depend on it."""
+
+    def __init__(self, S: np.ndarray, sigma: int, K: int = 4096, threads: int = 0):
         S, w = _sym(S)
         self._S = S
         self.n, self.sigma, self.K = S.size, sigma, K
-        self._h = lib().orc_o2_build(S.ctypes.data, w, S.size, sigma, K)
+        self._h = lib().orc_o2_build_mt(S.ctypes.data, w, S.size, sigma, K, threads)
         if not self._h:
             raise ValueError("symbol >= sigma in input (or sigma == 0)")
         self.L = int(lib().orc_o2_levels(self._h))
@@ -222,6 +237,15 @@ class O2Tree:
         lib().orc_o2_select(self._h, _p(c, _u32p), _p(j, _u64p), j.size, _p(out, _u64p))
         return out
 
+    def query_mt(self, kind: int, arg, c=None, threads: int = 0):
+        """access (kind 0), rank (1) or select (2) over a batch split across
+        host threads (0: all online CPUs); the same answers as the methods above."""
+        arg = np.ascontiguousarray(arg, np.uint64)
+        cc = np.ascontiguousarray(c if c is not None else np.zeros(arg.size), np.uint32)
+        out = np.empty(arg.size, np.uint32 if kind == 0 else np.uint64)
+        lib().orc_o2_query_mt(self._h, kind, _p(cc, _u32p), _p(arg, _u64p), arg.size, out.ctypes.data, threads)
+        return out
+
 
 # --------------------------------------------------------------------------
 # standalone bitvectors: binary rank and select by definition
@@ -239,6 +263,27 @@ def bv_select(bits, b, j):
     b, for each j in [1, count_b]."""
     pos = np.flatnonzero(np.asarray(bits) == b)
     return pos[np.asarray(j, dtype=np.int64) - 1].astype(np.uint64)
+
+
+def bitvector_support(bits, K):
+    """Rank counters and select samples of a bitvector by definition (Sections
+    4.1 and 4.2), from its prefix sums (a library primitive): L1[k] = ones in
+    B[0, 65536 k) for k <= n / 65536; L2[m] = ones in B[65536 floor(512 m /
+    65536), 512 m) for m <= n / 512; S_b[0] = 0 and S_b[m] = position of the
+    (m K)-th bit equal to b.  Returns (L1, L2, S0, S1) as uint64, uint16,
+    uint64, uint64 arrays."""
+    bits = np.asarray(bits).astype(np.uint8)
+    n = bits.size
+    pre = np.concatenate([[0], np.cumsum(bits, dtype=np.int64)])
+    l1 = pre[np.arange(n // 65536 + 1) * 65536].astype(np.uint64)
+    m = np.arange(n // 512 + 1) * 512
+    l2 = (pre[m] - pre[(m // 65536) * 65536]).astype(np.uint16)
+    out = [l1, l2]
+    for b in (0, 1):
+        pos = np.flatnonzero(bits == b)
+        k = np.arange(1, pos.size // K + 1)
+        out.append(np.concatenate([[0], pos[k * K - 1]]).astype(np.uint64))
+    return tuple(out)
 
 
 def alphabet_map(S):
@@ -275,18 +320,10 @@ class OMatrix:
     def export(self, what: int, level: int = 0) -> np.ndarray:
         bits = self.levels[level]
         n = bits.size
-        pre = np.concatenate([[0], np.cumsum(bits.astype(np.int64))])
         if what == 0:  # bits as LSB-first uint64 words
             pad = np.zeros((n + 63) // 64 * 64, np.uint8)
             pad[:n] = bits
             return np.packbits(pad, bitorder="little").view(np.uint64)
-        if what == 1:  # L1: ones in B[0, 65536 k)
-            return pre[np.arange(n // 65536 + 1) * 65536].astype(np.uint64)
-        if what == 2:  # L2: ones from the enclosing L1 block's start to 512 m
-            m = np.arange(n // 512 + 1) * 512
-            return (pre[m] - pre[(m // 65536) * 65536]).astype(np.uint16)
-        if what in (3, 4):  # S0 / S1: [0] = 0, [m] = position of the (m K)-th b-bit
-            pos = np.flatnonzero(bits == (what - 3))
-            m = np.arange(1, pos.size // self.K + 1)
-            return np.concatenate([[0], pos[m * self.K - 1]]).astype(np.uint64)
+        if what in (1, 2, 3, 4):  # L1, L2, S0, S1
+            return bitvector_support(bits, self.K)[what - 1]
         raise ValueError(what)

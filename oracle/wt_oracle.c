@@ -29,9 +29,11 @@
  * (brute force on tiny inputs, the worked example of Section 5, closed forms
  * and invariants); none is "parity unpinned".
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #define ORC_L1_BITS 65536u /* Section 4.1: L1-block size */
 #define ORC_L2_BITS 512u   /* Section 6.2/6.3: |L2| = 512 in every experiment */
@@ -63,6 +65,41 @@ static uint32_t ceil_lg(uint64_t x) {
 }
 
 static int popc64(uint64_t x) { return __builtin_popcountll(x); }
+
+/* ------------------------------------------------------------------------- */
+/* threads: the O2 build, its sample export and the query loops split their   */
+/* index ranges over host threads; results do not depend on the thread count  */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_MAX_THREADS 256
+
+/* Threads to use: requested > 0, else the online CPUs; 1 for small work. */
+static int orc_threads(int requested, uint64_t work) {
+    long nt = requested > 0 ? requested : sysconf(_SC_NPROCESSORS_ONLN);
+    if (requested <= 0 && work < ((uint64_t)1 << 16)) nt = 1;
+    if (nt < 1) nt = 1;
+    if (nt > ORC_MAX_THREADS) nt = ORC_MAX_THREADS;
+    return (int)nt;
+}
+
+/* Run fn on jobs[0..nt) (each job_size bytes), job 0 on the calling thread.
+ * A job whose thread cannot be started runs on the calling thread too.     */
+static void orc_run(void* (*fn)(void*), void* jobs, size_t job_size, int nt) {
+    pthread_t th[ORC_MAX_THREADS];
+    int ok[ORC_MAX_THREADS];
+    for (int i = 1; i < nt; i++) ok[i] = pthread_create(&th[i], NULL, fn, (char*)jobs + (size_t)i * job_size) == 0;
+    fn(jobs);
+    for (int i = 1; i < nt; i++) {
+        if (ok[i]) pthread_join(th[i], NULL);
+        else fn((char*)jobs + (size_t)i * job_size);
+    }
+}
+
+/* [lo, hi) of part i of nt equal parts of [0, n) */
+static void orc_split(uint64_t n, int nt, int i, uint64_t* lo, uint64_t* hi) {
+    *lo = n / (uint64_t)nt * (uint64_t)i + (n % (uint64_t)nt < (uint64_t)i ? n % (uint64_t)nt : (uint64_t)i);
+    *hi = *lo + n / (uint64_t)nt + ((uint64_t)i < n % (uint64_t)nt ? 1 : 0);
+}
 
 /* ------------------------------------------------------------------------- */
 /* Codes                                                                      */
@@ -255,7 +292,57 @@ static uint64_t lv_select(const orc_level* v, int b, uint64_t k) {
     }
 }
 
-orc_tree* orc_o2_build(const void* S, int w, uint64_t n, uint32_t sigma, uint32_t K) {
+/* One thread's share of a level: positions [a, b) of S (count and scatter)
+ * and words [w0, w1) of the level (packing).                                 */
+typedef struct {
+    const orc_tree* t;
+    const void* S;
+    int w;
+    uint32_t l;
+    uint64_t a, b;
+    uint64_t* cnt;  /* bucket counts of this share, then its first slot per bucket */
+    uint64_t size;  /* symbols of the share whose code is longer than l */
+    uint8_t* tmp;   /* one byte per position of the level: its bit */
+    orc_level* v;
+    uint64_t w0, w1;
+} orc_lvl_job;
+
+static void* orc_lvl_count(void* p) {
+    orc_lvl_job* j = (orc_lvl_job*)p;
+    const orc_tree* t = j->t;
+    for (uint64_t i = j->a; i < j->b; i++) {
+        uint64_t s = sym_at(j->S, j->w, i);
+        j->cnt[t->code[s] >> (t->L - j->l)]++;
+        if (t->len[s] > j->l) j->size++;
+    }
+    return NULL;
+}
+
+static void* orc_lvl_scatter(void* p) {
+    orc_lvl_job* j = (orc_lvl_job*)p;
+    const orc_tree* t = j->t;
+    const uint64_t size = j->v->size;
+    for (uint64_t i = j->a; i < j->b; i++) {
+        uint64_t s = sym_at(j->S, j->w, i);
+        uint64_t pos = j->cnt[t->code[s] >> (t->L - j->l)]++;
+        if (t->len[s] > j->l && pos < size) j->tmp[pos] = (uint8_t)((t->code[s] >> (t->L - 1 - j->l)) & 1u);
+    }
+    return NULL;
+}
+
+static void* orc_lvl_pack(void* p) {
+    orc_lvl_job* j = (orc_lvl_job*)p;
+    const uint64_t size = j->v->size;
+    for (uint64_t k = j->w0; k < j->w1; k++) {
+        uint64_t x = 0;
+        for (uint64_t b = 0; b < 64 && k * 64 + b < size; b++)
+            if (j->tmp[k * 64 + b]) x |= ((uint64_t)1) << b;
+        j->v->bits[k] = x;
+    }
+    return NULL;
+}
+
+orc_tree* orc_o2_build_mt(const void* S, int w, uint64_t n, uint32_t sigma, uint32_t K, int threads) {
     if (sigma == 0 || K == 0) return NULL;
     orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
     t->n = n;
@@ -279,35 +366,58 @@ orc_tree* orc_o2_build(const void* S, int w, uint64_t n, uint32_t sigma, uint32_
     for (uint32_t c = 0; c < sigma; c++) t->C[c + 1] += t->C[c];
     uint32_t L = t->L;
     t->lv = (orc_level*)calloc(L ? L : 1, sizeof(orc_level));
+    const int nt_all = orc_threads(threads, n);
+    uint8_t* tmp = (uint8_t*)malloc(n ? n : 1);
+    orc_lvl_job jobs[ORC_MAX_THREADS];
     for (uint32_t l = 0; l < L; l++) {
         orc_level* v = &t->lv[l];
         /* stable counting sort of S by the first l code bits (Algorithm 4);
          * finished codes sort behind all unfinished ones because code lengths
-         * never increase with the symbol.                                     */
+         * never increase with the symbol.  Each thread counts its range of
+         * positions per bucket; slots are handed out bucket by bucket and,
+         * within a bucket, range by range, which keeps the order stable.     */
         uint64_t nb = (uint64_t)1 << l;
-        uint64_t* cnt = (uint64_t*)calloc(nb + 1, sizeof(uint64_t));
-        uint64_t size = 0;
-        for (uint64_t j = 0; j < n; j++) {
-            uint64_t s = sym_at(S, w, j);
-            cnt[(t->code[s] >> (L - l)) + 1]++;
-            if (t->len[s] > l) size++;
+        int nt = nt_all;
+        while (nt > 1 && nb * (uint64_t)nt > ((uint64_t)1 << 26)) nt--;  /* bounded count arrays */
+        uint64_t* cnt = (uint64_t*)calloc(nb * (uint64_t)nt, sizeof(uint64_t));
+        for (int i = 0; i < nt; i++) {
+            memset(&jobs[i], 0, sizeof(jobs[i]));
+            jobs[i].t = t;
+            jobs[i].S = S;
+            jobs[i].w = w;
+            jobs[i].l = l;
+            jobs[i].cnt = cnt + nb * (uint64_t)i;
+            jobs[i].tmp = tmp;
+            jobs[i].v = v;
+            orc_split(n, nt, i, &jobs[i].a, &jobs[i].b);
         }
-        for (uint64_t k = 0; k < nb; k++) cnt[k + 1] += cnt[k];
+        orc_run(orc_lvl_count, jobs, sizeof(jobs[0]), nt);
+        uint64_t size = 0, run = 0;
+        for (int i = 0; i < nt; i++) size += jobs[i].size;
+        for (uint64_t k = 0; k < nb; k++)
+            for (int i = 0; i < nt; i++) {
+                uint64_t c = jobs[i].cnt[k];
+                jobs[i].cnt[k] = run;
+                run += c;
+            }
         v->size = size;
         v->nwords = (size + 63) / 64;
         v->bits = (uint64_t*)calloc(v->nwords + 1, sizeof(uint64_t));
-        for (uint64_t j = 0; j < n; j++) {
-            uint64_t s = sym_at(S, w, j);
-            uint64_t pos = cnt[t->code[s] >> (L - l)]++;
-            if (t->len[s] > l && ((t->code[s] >> (L - 1 - l)) & 1u)) v->bits[pos >> 6] |= ((uint64_t)1) << (pos & 63);
-        }
+        orc_run(orc_lvl_scatter, jobs, sizeof(jobs[0]), nt);
+        for (int i = 0; i < nt; i++) orc_split(v->nwords, nt, i, &jobs[i].w0, &jobs[i].w1);
+        orc_run(orc_lvl_pack, jobs, sizeof(jobs[0]), nt);
         free(cnt);
         v->pc = (uint64_t*)malloc(sizeof(uint64_t) * (v->nwords + 2));
         v->pc[0] = 0;
         for (uint64_t k = 0; k <= v->nwords; k++) v->pc[k + 1] = v->pc[k] + (uint64_t)popc64(v->bits[k]);
         v->ones = v->pc[v->nwords];
     }
+    free(tmp);
     return t;
+}
+
+orc_tree* orc_o2_build(const void* S, int w, uint64_t n, uint32_t sigma, uint32_t K) {
+    return orc_o2_build_mt(S, w, n, sigma, K, 0);
 }
 
 void orc_o2_free(orc_tree* t) {
@@ -352,6 +462,26 @@ static void nodes_rec(const orc_tree* t, uint64_t a, uint64_t b, uint32_t d, uin
     uint64_t m = a + prev_pow2(b - a);
     nodes_rec(t, a, m, d + 1, p << 1, out);
     nodes_rec(t, m, b, d + 1, (p << 1) | 1u, out);
+}
+
+/* One thread's range of a level for the sample export. */
+typedef struct {
+    const orc_level* v;
+    int b;
+    uint64_t K, p0, p1, before, cnt;
+    uint64_t* out;
+} orc_smp_job;
+
+static void* orc_smp_scan(void* p) {
+    orc_smp_job* j = (orc_smp_job*)p;
+    uint64_t seen = j->before;
+    for (uint64_t q = j->p0; q < j->p1; q++) {
+        if (bit_at(j->v, q) == j->b) {
+            seen++;
+            if (seen % j->K == 0 && seen / j->K < j->cnt) j->out[seen / j->K] = q;
+        }
+    }
+    return NULL;
 }
 
 /* Logical contents for comparison with the GPU export.
@@ -420,14 +550,30 @@ uint64_t orc_o2_export(const orc_tree* t, uint32_t l, uint32_t what, void* dst) 
         if (dst) {
             uint64_t* o = (uint64_t*)dst;
             o[0] = 0;
-            /* direct count: walk every bit once */
-            uint64_t seen = 0, m = 1;
-            for (uint64_t p = 0; p < v->size && m < cnt; p++) {
-                if (bit_at(v, p) == b) {
-                    seen++;
-                    if (seen == m * t->K) o[m++] = p;
-                }
+            /* direct count: walk every bit once, each thread over its own
+             * range of positions after counting the b-bits before it        */
+            orc_smp_job jobs[ORC_MAX_THREADS];
+            const int nt = orc_threads(0, v->size);
+            for (int i = 0; i < nt; i++) {
+                uint64_t w0, w1;
+                orc_split(v->nwords, nt, i, &w0, &w1);
+                jobs[i].v = v;
+                jobs[i].b = b;
+                jobs[i].K = t->K;
+                jobs[i].p0 = w0 * 64;
+                jobs[i].p1 = w1 * 64 < v->size ? w1 * 64 : v->size;
+                jobs[i].before = 0;
+                jobs[i].out = o;
+                jobs[i].cnt = cnt;
             }
+            uint64_t run = 0;
+            for (int i = 0; i < nt; i++) {
+                jobs[i].before = run;
+                uint64_t ones = v->pc[jobs[i].p1 / 64] - v->pc[jobs[i].p0 / 64];
+                if (jobs[i].p1 % 64) ones += (uint64_t)popc64(v->bits[jobs[i].p1 / 64] & ((((uint64_t)1) << (jobs[i].p1 % 64)) - 1));
+                run += b ? ones : (jobs[i].p1 - jobs[i].p0) - ones;
+            }
+            orc_run(orc_smp_scan, jobs, sizeof(jobs[0]), nt);
         }
         return cnt;
     }
@@ -547,3 +693,41 @@ void orc_o2_select(const orc_tree* t, const uint32_t* c, const uint64_t* j, uint
         else out[k] = o2_select1(t, c[k], j[k]);
     }
 }
+
+/* The query loops above over nt threads, each taking a contiguous range of
+ * the batch: kind 0 access (out uint32), 1 rank, 2 select (out uint64).     */
+typedef struct {
+    const orc_tree* t;
+    int kind;
+    const uint32_t* c;
+    const uint64_t* arg;
+    uint64_t a, b;
+    void* out;
+} orc_q_job;
+
+static void* orc_q_run(void* p) {
+    orc_q_job* j = (orc_q_job*)p;
+    uint64_t q = j->b - j->a;
+    if (j->kind == 0) orc_o2_access(j->t, j->arg + j->a, q, (uint32_t*)j->out + j->a);
+    else if (j->kind == 1) orc_o2_rank(j->t, j->c + j->a, j->arg + j->a, q, (uint64_t*)j->out + j->a);
+    else orc_o2_select(j->t, j->c + j->a, j->arg + j->a, q, (uint64_t*)j->out + j->a);
+    return NULL;
+}
+
+void orc_o2_query_mt(const orc_tree* t, int kind, const uint32_t* c, const uint64_t* arg, uint64_t q, void* out,
+                     int threads) {
+    orc_q_job jobs[ORC_MAX_THREADS];
+    const int nt = orc_threads(threads, q * 64);
+    for (int i = 0; i < nt; i++) {
+        jobs[i].t = t;
+        jobs[i].kind = kind;
+        jobs[i].c = c;
+        jobs[i].arg = arg;
+        jobs[i].out = out;
+        orc_split(q, nt, i, &jobs[i].a, &jobs[i].b);
+    }
+    orc_run(orc_q_run, jobs, sizeof(jobs[0]), nt);
+}
+
+/* Number of threads orc_o2_build_mt and orc_o2_query_mt use by default. */
+int orc_default_threads(void) { return orc_threads(0, (uint64_t)1 << 40); }

@@ -43,8 +43,57 @@ class WTError(RuntimeError):
 LAYOUT_TREE, LAYOUT_MATRIX = 0, 1
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    """wt_allocator: alloc(bytes, stream, ctx) / free(ptr, stream, ctx) callbacks."""
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
 class Options(ctypes.Structure):
-    _fields_ = [("sample_k", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+    _fields_ = [("sample_k", ctypes.c_uint32), ("layout", ctypes.c_uint32),
+                ("allocator", ctypes.POINTER(Allocator)), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class TorchAllocator:
+    """A wt_allocator backed by PyTorch's CUDA caching allocator, so trees and
+    scratch buffers live in torch's memory pool.  libwt asks for memory on the
+    caller's stream and returns it on the same stream, which is how the
+    caching allocator orders reuse.  A failed allocation returns NULL (libwt
+    then reports WT_ENOMEM).  Keep the object alive as long as any tree built
+    with it."""
+
+    def __init__(self, device=None):
+        import torch
+
+        self.device = torch.cuda.current_device() if device is None else int(device)
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._fa, self._ff = _ALLOC_FN(_alloc), _FREE_FN(_free)
+        self.struct = Allocator(self._fa, self._ff, None)
+
+
+_torch_allocators = {}
+
+
+def torch_allocator(device=None) -> TorchAllocator:
+    """The shared TorchAllocator of a device (created on first use)."""
+    import torch
+
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _torch_allocators:
+        _torch_allocators[d] = TorchAllocator(d)
+    return _torch_allocators[d]
 
 
 class Info(ctypes.Structure):
@@ -79,7 +128,9 @@ class LearnedInfo(ctypes.Structure):
 
 
 class BatchOptions(ctypes.Structure):
-    _fields_ = [("sample_k", ctypes.c_uint32), ("query_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+    _fields_ = [("sample_k", ctypes.c_uint32), ("query_threads", ctypes.c_uint32),
+                ("allocator", ctypes.POINTER(Allocator)), ("lp_ctas_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 _lib = None
@@ -115,7 +166,7 @@ def lib():
         L.wt_profile_launches.restype = u64
         L.wt_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         L.wt_profile_report.restype = ctypes.c_size_t
-        L.wt_bitvector_support_static.argtypes = [vp, u64, u32, vp, vp, vp, vp, u64, vp, vp]
+        L.wt_bitvector_support_static.argtypes = [vp, u64, u32, vp, vp, vp, vp, u64, vp, vp, vp]
         L.wt_bitvector_support_static.restype = ctypes.c_int
         L.wt_bitvector_rank.argtypes = [vp, u64, vp, vp, vp, vp, u64, vp, vp]
         L.wt_bitvector_rank.restype = ctypes.c_int
@@ -204,7 +255,8 @@ class Tree:
         t.levels = t.info().levels
         return t
 
-    def __init__(self, symbols, sigma: int, sample_k: int = 4096, stream=None, layout: int = 0):
+    def __init__(self, symbols, sigma: int, sample_k: int = 4096, stream=None, layout: int = 0,
+                 allocator="torch"):
         import torch
 
         if symbols.dim() != 1:
@@ -218,6 +270,14 @@ class Tree:
         self.symbol_bytes = w
         self._stream = stream
         opt = Options(sample_k=sample_k, layout=layout)
+        # tree memory from torch's caching allocator (default), a given
+        # TorchAllocator / Allocator, or None for libwt's stream-ordered pool
+        if isinstance(allocator, str) and allocator == "torch":
+            allocator = torch_allocator()
+        self._allocator = allocator
+        if allocator is not None:
+            st_ = allocator.struct if isinstance(allocator, TorchAllocator) else allocator
+            opt.allocator = ctypes.pointer(st_)
         h = ctypes.c_void_p()
         ptr = self._keep.data_ptr() if self.n else None
         # a CPU tensor (pinned or pageable) goes through wt_build_host: chunked copy overlapping the histogram
@@ -375,10 +435,13 @@ class Tree:
         return out.reshape(-1, 4) if what == EXPORT_NODES else out
 
 
-def build(symbols, sigma: int, sample_k: int = 4096, stream=None, layout: int = LAYOUT_TREE) -> Tree:
+def build(symbols, sigma: int, sample_k: int = 4096, stream=None, layout: int = LAYOUT_TREE,
+          allocator="torch") -> Tree:
     """wt_build: construct the tree (or, with layout=LAYOUT_MATRIX, the wavelet
-    matrix) of a 1-D CUDA tensor of symbols in [0, sigma)."""
-    return Tree(symbols, sigma, sample_k=sample_k, stream=stream, layout=layout)
+    matrix) of a 1-D CUDA tensor of symbols in [0, sigma); a CPU tensor goes
+    through wt_build_host.  Device memory comes from torch's caching allocator
+    unless ``allocator`` is None (libwt's pool) or another allocator."""
+    return Tree(symbols, sigma, sample_k=sample_k, stream=stream, layout=layout, allocator=allocator)
 
 
 class Batch:
@@ -387,7 +450,8 @@ class Batch:
     symbols: list of 1-D CUDA tensors (16-byte aligned, same element size); they
     must stay alive and unchanged in size while the batch exists."""
 
-    def __init__(self, symbols, sigmas, sample_k: int = 4096, query_threads: int = 256):
+    def __init__(self, symbols, sigmas, sample_k: int = 4096, query_threads: int = 256, allocator=None,
+                 lp_ctas_per_sm: int = 0):
         self._syms = list(symbols)
         nt = len(self._syms)
         w = self._syms[0].element_size()
@@ -397,7 +461,12 @@ class Batch:
         self.n = [t.numel() for t in self._syms]
         self.sigma = [int(x) for x in sigmas]
         self.symbol_bytes = w
-        opt = BatchOptions(sample_k=sample_k, query_threads=query_threads)
+        opt = BatchOptions(sample_k=sample_k, query_threads=query_threads, lp_ctas_per_sm=lp_ctas_per_sm)
+        if isinstance(allocator, str) and allocator == "torch":
+            allocator = torch_allocator()
+        self._allocator = allocator
+        if allocator is not None:
+            opt.allocator = ctypes.pointer(allocator.struct if isinstance(allocator, TorchAllocator) else allocator)
         h = ctypes.c_void_p()
         _check(lib().wt_batch_create(nt, ptrs, ns, sg, w, ctypes.byref(opt), ctypes.byref(h)), "wt_batch_create")
         self._h = h
@@ -492,19 +561,18 @@ class Bitvector:
         self.s0 = torch.empty(cap, dtype=torch.int64, device=dev)
         self.s1 = torch.empty(cap, dtype=torch.int64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
-        _check(lib().wt_bitvector_support_static(self.words.data_ptr(), nbits, sample_k, self.l1.data_ptr(),
-                                                 self.l2.data_ptr(), self.s0.data_ptr(), self.s1.data_ptr(), cap,
-                                                 self.status.data_ptr(), _stream(stream)),
+        self._ones = torch.zeros(1, dtype=torch.int64, device=dev)
+        self._cap = cap
+        self.support(stream)
+        self.ones = int(self._ones.item())  # counted by the support kernel
+
+    def support(self, stream=None):
+        """wt_bitvector_support_static: (re)build the counters, samples and ones count."""
+        _check(lib().wt_bitvector_support_static(self.words.data_ptr(), self.nbits, self.sample_k, self.l1.data_ptr(),
+                                                 self.l2.data_ptr(), self.s0.data_ptr(), self.s1.data_ptr(),
+                                                 self._cap, self.status.data_ptr(), self._ones.data_ptr(),
+                                                 _stream(stream)),
                "wt_bitvector_support_static")
-        nwb = self.words.view(torch.uint8)[: (nbits + 7) // 8]
-        self.ones = int(self._popcount(nwb))
-
-    @staticmethod
-    def _popcount(b):
-        import torch
-
-        t = torch.tensor([bin(x).count("1") for x in range(256)], dtype=torch.int64, device=b.device)
-        return t[b.long()].sum().item()
 
     def rank(self, i, out=None, stream=None):
         import torch

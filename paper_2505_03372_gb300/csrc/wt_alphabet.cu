@@ -8,7 +8,8 @@
 
 extern "C" wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64_t nbits, uint32_t sample_k,
                                                  uint64_t* d_l1, uint16_t* d_l2, uint64_t* d_s0, uint64_t* d_s1,
-                                                 uint64_t sample_capacity, uint32_t* d_status, wt_stream stream);
+                                                 uint64_t sample_capacity, uint32_t* d_status, uint64_t* d_ones,
+                                                 wt_stream stream);
 
 namespace wt {
 namespace {
@@ -44,10 +45,6 @@ __global__ void __launch_bounds__(kAlThreads) presence_kernel(const T* __restric
 }
 
 // the number of present values: rank_1 at the end of the bitmap
-__global__ void sigma_kernel(const LevelDesc lv, uint64_t* __restrict__ sigma) {
-    if (threadIdx.x == 0) *sigma = rank1(lv, lv.size);
-}
-
 // (S and out may be the same array: each thread reads its symbol before writing it)
 template <typename T>
 __global__ void __launch_bounds__(kAlThreads) remap_kernel(const LevelDesc lv, const T* S, T* out, uint64_t n) {
@@ -62,15 +59,7 @@ __global__ void __launch_bounds__(kAlThreads) values_kernel(const LevelDesc lv, 
         values[c] = (uint32_t)select_b(lv, 1, c + 1, 12);  // kAlSampleK = 2^12
 }
 
-bool al_dev(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+bool al_dev(const void* p) { return device_ptr_ok(p); }
 
 template <typename T>
 wt_status run_alphabet(const void* d_symbols, uint64_t n, void* d_out, uint32_t* d_values, uint32_t* h_sigma,
@@ -104,11 +93,11 @@ wt_status run_alphabet(const void* d_symbols, uint64_t n, void* d_out, uint32_t*
             ProfScope ps("alphabet_presence", s);
             presence_kernel<T><<<grid, kAlThreads, 0, s>>>(S, n, reinterpret_cast<unsigned long long*>(words));
         }
+        // sigma = the ones of the presence bitmap, counted by the support kernel
+        uint64_t* d_sigma = reinterpret_cast<uint64_t*>(M + o_sig);
         st = wt_bitvector_support_static(words, nbits, kAlSampleK, const_cast<uint64_t*>(lv.l1),
                                          const_cast<uint16_t*>(lv.l2), const_cast<uint64_t*>(lv.s0),
-                                         const_cast<uint64_t*>(lv.s1), cap, status, s);
-        uint64_t* d_sigma = reinterpret_cast<uint64_t*>(M + o_sig);
-        if (st == WT_OK) sigma_kernel<<<1, 32, 0, s>>>(lv, d_sigma);
+                                         const_cast<uint64_t*>(lv.s1), cap, status, d_sigma, s);
         if (st == WT_OK && cudaMemcpyAsync(&sigma, d_sigma, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             st = WT_ECUDA;
         if (st == WT_OK && cudaStreamSynchronize(s) != cudaSuccess) st = WT_ECUDA;

@@ -22,7 +22,12 @@ namespace wt {
 
 static std::once_flag g_pool_once;
 
-cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s, const wt_allocator* a) {
+    if (bytes == 0) bytes = 256;
+    if (a) {
+        *p = a->alloc(bytes, s, a->ctx);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
     std::call_once(g_pool_once, [] {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -32,12 +37,26 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
     });
-    if (bytes == 0) bytes = 256;
     return cudaMallocAsync(p, bytes, s);
 }
 
-void dev_free(void* p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+void dev_free(void* p, cudaStream_t s, const wt_allocator* a) {
+    if (!p) return;
+    if (a) a->free(p, s, a->ctx);
+    else cudaFreeAsync(p, s);
+}
+
+bool device_ptr_ok(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error this query left
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess && at.device == dev;
 }
 
 int sm_count() {
@@ -123,16 +142,7 @@ static void collect_pending() {
 // argument checks
 // ---------------------------------------------------------------------------
 
-// True if p is memory a kernel on this device may dereference.
-static bool is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+static bool is_device_ptr(const void* p) { return device_ptr_ok(p); }
 
 static bool tree_ok(const wt_tree_s* t) { return t && t->magic == kTreeMagic; }
 
@@ -145,6 +155,45 @@ static bool is_host_ptr(const void* p) {
         return true;  // unknown to CUDA: ordinary pageable memory
     }
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+// The library's two copy streams of the current device (host-to-device and
+// device-to-host staging of wt_build_host and wt_query_host), created on first
+// use and kept for the life of the process.  A device reset destroys them: the
+// next call on that device after a reset fails with WT_ECUDA.
+static bool copy_streams(cudaStream_t* h2d, cudaStream_t* d2h) {
+    static std::mutex mu;
+    static cudaStream_t st[256][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    for (int k = 0; k < 2; k++)
+        if (!st[dev][k] && cudaStreamCreateWithFlags(&st[dev][k], cudaStreamNonBlocking) != cudaSuccess) {
+            st[dev][k] = nullptr;
+            return false;
+        }
+    *h2d = st[dev][0];
+    *d2h = st[dev][1];
+    return true;
+}
+
+static wt_tree_s* new_tree(cudaStream_t stream, const wt_allocator* alloc) {
+    wt_tree_s* t = new wt_tree_s();
+    memset(&t->desc, 0, sizeof(t->desc));
+    cudaGetDevice(&t->device);
+    t->stream = stream;
+    t->has_alloc = alloc != nullptr;
+    if (alloc) t->alloc = *alloc;
+    t->magic = kTreeMagic;
+    return t;
+}
+
+static void release_tree(wt_tree_s* t) {
+    free_learned(t, t->stream);
+    dev_free(t->hdr_mem, t->stream, tree_alloc(t));
+    dev_free(t->lvl_mem, t->stream, tree_alloc(t));
+    t->magic = 0;
+    delete t;
 }
 
 }  // namespace wt
@@ -184,17 +233,13 @@ wt_status wt_build(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t s
     const uint32_t layout = opt ? opt->layout : WT_LAYOUT_TREE;
     if (layout != WT_LAYOUT_TREE && layout != WT_LAYOUT_MATRIX) return WT_EINVAL;
 
-    wt_tree_s* t = new wt_tree_s();
-    memset(&t->desc, 0, sizeof(t->desc));
-    cudaGetDevice(&t->device);
-    t->stream = stream;
-    t->magic = kTreeMagic;
+    const wt_allocator* alloc = opt ? opt->allocator : nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free)) return WT_EINVAL;
+
+    wt_tree_s* t = new_tree(stream, alloc);
     wt_status st = build_tree(d_symbols, n, sigma, symbol_bytes, K, stream, t, layout);
     if (st != WT_OK) {
-        dev_free(t->hdr_mem, stream);
-        dev_free(t->lvl_mem, stream);
-        t->magic = 0;
-        delete t;
+        release_tree(t);
         return st;
     }
     *out = t;
@@ -214,41 +259,32 @@ wt_status wt_build_host(const void* h_symbols, uint64_t n, uint32_t sigma, uint3
     if (K < 256 || K > (1u << 20) || (K & (K - 1))) return WT_EINVAL;
     const uint32_t layout = opt ? opt->layout : WT_LAYOUT_TREE;
     if (layout != WT_LAYOUT_TREE && layout != WT_LAYOUT_MATRIX) return WT_EINVAL;
-    // The device copy is allocated on the copy stream (stream-ordered: usable
-    // there at once, and by `stream` after the per-chunk events), so the copies
-    // need not wait for the work already queued on `stream`.
-    cudaStream_t cs = nullptr;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return WT_ECUDA;
+    const wt_allocator* alloc = opt ? opt->allocator : nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free)) return WT_EINVAL;
+    // The device copy lives on the library's copy stream: allocated there,
+    // filled there chunk by chunk (`stream` waits per chunk), and returned there
+    // once that stream has waited for its last use on `stream`.  The copies do
+    // not wait for the work already queued on `stream`, and a caller's
+    // allocator sees the block taken and returned on one stream.
+    cudaStream_t cs = nullptr, unused = nullptr;
+    if (!copy_streams(&cs, &unused)) return WT_ECUDA;
     void* d_buf = nullptr;
-    if (n && dev_alloc(&d_buf, n * symbol_bytes, cs) != cudaSuccess) {
-        cudaStreamDestroy(cs);
-        return WT_ENOMEM;
-    }
-    wt_tree_s* t = new wt_tree_s();
-    memset(&t->desc, 0, sizeof(t->desc));
-    cudaGetDevice(&t->device);
-    t->stream = stream;
-    t->magic = kTreeMagic;
+    if (n && dev_alloc(&d_buf, n * symbol_bytes, cs, alloc) != cudaSuccess) return WT_ENOMEM;
+    wt_tree_s* t = new_tree(stream, alloc);
     wt_status st = build_tree(d_buf, n, sigma, symbol_bytes, K, stream, t, layout, h_symbols, cs);
     if (n) {
-        // `stream` has waited for every chunk (or the build failed before the
-        // copies: then order the free after the copy stream's work too)
         cudaEvent_t ev = nullptr;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
-            cudaEventRecord(ev, cs);
-            cudaStreamWaitEvent(stream, ev, 0);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ev, stream) ==
+                cudaSuccess && cudaStreamWaitEvent(cs, ev, 0) == cudaSuccess) {
             cudaEventDestroy(ev);
         } else {
-            cudaStreamSynchronize(cs);
+            if (ev) cudaEventDestroy(ev);
+            cudaStreamSynchronize(stream);
         }
+        dev_free(d_buf, cs, alloc);  // stream-ordered on the copy stream: after the level passes that read it
     }
-    dev_free(d_buf, stream);  // stream-ordered: after the level passes that read it
-    cudaStreamDestroy(cs);
     if (st != WT_OK) {
-        dev_free(t->hdr_mem, stream);
-        dev_free(t->lvl_mem, stream);
-        t->magic = 0;
-        delete t;
+        release_tree(t);
         return st;
     }
     *out = t;
@@ -257,11 +293,7 @@ wt_status wt_build_host(const void* h_symbols, uint64_t n, uint32_t sigma, uint3
 
 void wt_destroy(wt_tree tree) {
     if (!tree_ok(tree)) return;
-    free_learned(tree, tree->stream);
-    dev_free(tree->hdr_mem, tree->stream);
-    dev_free(tree->lvl_mem, tree->stream);
-    tree->magic = 0;
-    delete tree;
+    release_tree(tree);  // a tree of a batch holds no level or header memory of its own
 }
 
 wt_status wt_access(wt_tree tree, const uint64_t* d_i, uint32_t* d_out, uint64_t q, wt_stream stream) {
@@ -303,12 +335,11 @@ wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_
 namespace {
 
 struct HostPipe {
-    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr;  // the library's copy streams of this device
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_walk[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     bool ok = true;
     HostPipe() {
-        ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess;
+        ok = copy_streams(&h2d, &d2h);
         for (int b = 0; b < 2 && ok; b++)
             ok = cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&ev_walk[b], cudaEventDisableTiming) == cudaSuccess &&
@@ -320,8 +351,6 @@ struct HostPipe {
             if (ev_walk[b]) cudaEventDestroy(ev_walk[b]);
             if (ev_out[b]) cudaEventDestroy(ev_out[b]);
         }
-        if (h2d) cudaStreamDestroy(h2d);
-        if (d2h) cudaStreamDestroy(d2h);
     }
 };
 
@@ -346,8 +375,11 @@ wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, cons
     const int nbuf = nch > 1 ? 2 : 1;
     HostPipe hp;
     if (!hp.ok) return WT_ECUDA;
+    // the buffers are taken on the copy-in stream (no wait for the work queued
+    // on `stream`) and returned on it after the last copy-out
+    const wt_allocator* alloc = tree_alloc(tree);
     void* mem = nullptr;
-    if (dev_alloc(&mem, per * nbuf, hp.h2d) != cudaSuccess) return WT_ENOMEM;
+    if (dev_alloc(&mem, per * nbuf, hp.h2d, alloc) != cudaSuccess) return WT_ENOMEM;
     uint8_t* M = static_cast<uint8_t*>(mem);
     cudaStream_t s = stream;
     wt_status st = WT_OK;
@@ -397,7 +429,7 @@ wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, cons
         cudaStreamSynchronize(s);  // no events: order by waiting on the host instead
         cudaStreamSynchronize(hp.d2h);
         cudaStreamSynchronize(hp.h2d);
-        dev_free(mem, s);
+        dev_free(mem, hp.h2d, alloc);
         if (walked) cudaEventDestroy(walked);
         return WT_ECUDA;
     }
@@ -405,7 +437,8 @@ wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, cons
     cudaStreamWaitEvent(hp.d2h, walked, 0);
     cudaEventRecord(done, hp.d2h);
     cudaStreamWaitEvent(s, done, 0);
-    dev_free(mem, hp.d2h);
+    cudaStreamWaitEvent(hp.h2d, done, 0);
+    dev_free(mem, hp.h2d, alloc);  // after the last copy-out
     cudaEventDestroy(walked);
     cudaEventDestroy(done);
     return st;

@@ -33,6 +33,8 @@ struct wt_batch_s {
     uint64_t q;
     // captured graph
     cudaStream_t cap_stream;
+    uint32_t has_alloc;  // the one allocation came from `alloc` (wt_batch_options.allocator)
+    wt_allocator alloc;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     uint32_t graph_kernels;
@@ -83,15 +85,7 @@ __global__ void __launch_bounds__(kBqMaxThreads) batch_query_kernel(const TreeDe
 
 static uint64_t al(uint64_t x, uint64_t a = 256) { return (x + a - 1) / a * a; }
 
-static bool is_dev(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+static bool is_dev(const void* p) { return device_ptr_ok(p); }
 
 static wt_status capture(wt_batch_s* b) {
     if (b->exec) {
@@ -140,7 +134,13 @@ static void batch_free(wt_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->mem) cudaFree(b->mem);
+    if (b->mem) {
+        if (b->has_alloc) {
+            b->alloc.free(b->mem, nullptr, b->alloc.ctx);
+        } else {
+            cudaFree(b->mem);
+        }
+    }
     b->magic = 0;
     delete b;
 }
@@ -156,6 +156,10 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     const uint32_t K = (opt && opt->sample_k) ? opt->sample_k : 4096u;
     if (K < 256 || K > (1u << 20) || (K & (K - 1))) return WT_EINVAL;
     const uint32_t qthreads = (opt && opt->query_threads) ? opt->query_threads : 256u;
+    const wt_allocator* alloc = opt ? opt->allocator : nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free)) return WT_EINVAL;
+    const uint32_t lp_ctas = (opt && opt->lp_ctas_per_sm) ? opt->lp_ctas_per_sm : 3u;
+    if (lp_ctas > 3) return WT_EINVAL;
     if (qthreads != 128 && qthreads != 256 && qthreads != 512) return WT_EINVAL;
     for (uint32_t i = 0; i < ntrees; i++) {
         const uint32_t sg = h_sigma[i];
@@ -236,7 +240,18 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
             t.s1.push_back(take(((n >> kl) + 2) * 8));
         }
     }
-    if (cudaMalloc(&b->mem, off) != cudaSuccess) {
+    if (alloc) {
+        b->has_alloc = 1;
+        b->alloc = *alloc;
+        b->mem = alloc->alloc(off, nullptr, alloc->ctx);  // legacy default stream, synchronised below
+        if (b->mem && cudaStreamSynchronize(nullptr) != cudaSuccess) {
+            batch_free(b);
+            return WT_ECUDA;
+        }
+    } else if (cudaMalloc(&b->mem, off) != cudaSuccess) {
+        b->mem = nullptr;
+    }
+    if (!b->mem) {
         cudaGetLastError();
         delete b;
         return WT_ENOMEM;
@@ -328,6 +343,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     bd.w = w;
     bd.maxL = maxL;
     bd.k_log2 = kl;
+    bd.lp_ctas = lp_ctas;
     bd.total_chunks = cpre[ntrees];
     bd.total_slots = spre[ntrees];
     bd.info = reinterpret_cast<BatchTreeInfo*>(M + o_info);

@@ -40,15 +40,7 @@ __global__ void __launch_bounds__(kBvThreads) bv_select_kernel(const LevelDesc l
     if (status && __any_sync(__activemask(), bad_any) && bad_any) atomicOr(status, kStQuery);
 }
 
-bool bv_dev(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+bool bv_dev(const void* p) { return device_ptr_ok(p); }
 
 template <typename K>
 int bv_grid(K kernel, uint64_t q) {

@@ -1160,7 +1160,8 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     size_t off_C = 256;
     size_t off_nodes = align_up(off_C + (sigma + 1ull) * 8, 256);
     size_t hdr = align_up(off_nodes + std::max<uint64_t>(nslots, 1) * sizeof(NodeEntry), 256);
-    WT_CUDA_TRY(dev_alloc(&t->hdr_mem, hdr, s));
+    const wt_allocator* A = tree_alloc(t);
+    WT_CUDA_TRY(dev_alloc(&t->hdr_mem, hdr, s, A));
     t->hdr_bytes = hdr;
     uint8_t* H = reinterpret_cast<uint8_t*>(t->hdr_mem);
     t->desc.status = reinterpret_cast<uint32_t*>(H + off_status);
@@ -1182,7 +1183,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     size_t s_tcnt = align_up(s_meta + 2 * kMaxLevels * 8, 256);
     size_t s_end = align_up(s_tcnt + std::max<uint64_t>(tiles0, 1) * 8, 256);
     void* scratch = nullptr;
-    WT_CUDA_TRY(dev_alloc(&scratch, s_end, s));
+    WT_CUDA_TRY(dev_alloc(&scratch, s_end, s, A));
     uint8_t* X = reinterpret_cast<uint8_t*>(scratch);
     uint64_t* hist = reinterpret_cast<uint64_t*>(X + s_hist);
     uint64_t* left = reinterpret_cast<uint64_t*>(X + s_left);
@@ -1238,7 +1239,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         } else {
             e = hist_part(0, n);
         }
-        if (e != cudaSuccess) { dev_free(scratch, s); return WT_ECUDA; }
+        if (e != cudaSuccess) { dev_free(scratch, s, A); return WT_ECUDA; }
     }
     // 2. C
     device_exclusive_scan(hist, C, sigma, tmp, s);
@@ -1276,7 +1277,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     WT_CUDA_TRY(cudaMemcpyAsync(&hstatus, t->desc.status, 4, cudaMemcpyDeviceToHost, s));
     WT_CUDA_TRY(cudaStreamSynchronize(s));
     if (hstatus & kStSymbol) {
-        dev_free(scratch, s);
+        dev_free(scratch, s, A);
         return WT_ESYMBOL;
     }
 
@@ -1302,8 +1303,8 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         off = align_up(off + ((ones >> k_log2) + 1) * 8, 256);
     }
     t->lvl_bytes = std::max<size_t>(off, 256);
-    if (dev_alloc(&t->lvl_mem, t->lvl_bytes, s) != cudaSuccess) {
-        dev_free(scratch, s);
+    if (dev_alloc(&t->lvl_mem, t->lvl_bytes, s, A) != cudaSuccess) {
+        dev_free(scratch, s, A);
         return WT_ENOMEM;
     }
     uint8_t* M = reinterpret_cast<uint8_t*>(t->lvl_mem);
@@ -1329,8 +1330,8 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         const size_t b_stmp = align_up(2 * ((max_tiles + kScanChunk - 1) / kScanChunk + 2) * 8, 256);
         void* work = nullptr;
         const size_t work_bytes = 2 * tbytes + b_state + 256 + 2 * b_cnt + b_excl + b_stmp;
-        if (dev_alloc(&work, work_bytes, s) != cudaSuccess) {
-            dev_free(scratch, s);
+        if (dev_alloc(&work, work_bytes, s, A) != cudaSuccess) {
+            dev_free(scratch, s, A);
             return WT_ENOMEM;
         }
         uint8_t* Wm = reinterpret_cast<uint8_t*>(work);
@@ -1388,8 +1389,8 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             else if (w == 2) e = enc ? launch_level_pass<uint16_t, true>(a, s) : launch_level_pass<uint16_t, false>(a, s);
             else e = enc ? launch_level_pass<uint32_t, true>(a, s) : launch_level_pass<uint32_t, false>(a, s);
             if (e != cudaSuccess) {
-                dev_free(work, s);
-                dev_free(scratch, s);
+                dev_free(work, s, A);
+                dev_free(scratch, s, A);
                 return WT_ECUDA;
             }
             have_excl = a.next_cnt != nullptr;
@@ -1397,7 +1398,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
                 device_exclusive_scan(reinterpret_cast<const uint64_t*>(a.next_cnt), texcl, ntiles_next, stmp, s,
                                       "tile_scan");
         }
-        dev_free(work, s);
+        dev_free(work, s, A);
     } else {
         // empty levels still need their first counter / sample entries
         for (uint32_t l = 0; l < L; l++) {
@@ -1408,7 +1409,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             WT_CUDA_TRY(cudaMemsetAsync(M + lay[l].s1, 0, 8, s));
         }
     }
-    dev_free(scratch, s);
+    dev_free(scratch, s, A);
     return WT_OK;
 }
 
@@ -1580,7 +1581,8 @@ static cudaError_t launch_level_pass_batched(const BatchDev& b, uint32_t l, cuda
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int grid = sm_count() * kLpBlocksPerSM;
+    const int grid = sm_count() * (int)((b.lp_ctas >= 1 && b.lp_ctas <= (uint32_t)kLpBlocksPerSM) ? b.lp_ctas
+                                                                                                 : kLpBlocksPerSM);
     level_pass_batched_kernel<T, ENC><<<grid, kLpThreads, sm, s>>>(b.lpa + (uint64_t)l * b.ntrees,
                                                                    b.tile_prefix + (uint64_t)l * (b.ntrees + 1),
                                                                    b.ntrees, b.counters + l);

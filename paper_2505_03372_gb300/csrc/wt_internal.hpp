@@ -24,6 +24,8 @@ struct wt_tree_s {
     void* learned_mem;
     size_t learned_bytes;
     uint32_t is_view;         // a tree of a batch (wt_batch_tree): memory belongs to the batch
+    uint32_t has_alloc;       // 1: memory comes from `alloc` (wt_options.allocator), else the device's pool
+    wt_allocator alloc;
     uint64_t magic;
 };
 
@@ -44,8 +46,16 @@ struct ProfScope {
 };
 
 // ---- memory (wt_api.cu) ----
-cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
-void dev_free(void* p, cudaStream_t s);
+// Device memory comes from the caller's allocator when one is given (null:
+// the device's stream-ordered pool).  A failed allocation returns
+// cudaErrorMemoryAllocation.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s, const wt_allocator* a = nullptr);
+void dev_free(void* p, cudaStream_t s, const wt_allocator* a = nullptr);
+inline const wt_allocator* tree_alloc(const wt_tree_s* t) { return t->has_alloc ? &t->alloc : nullptr; }
+
+// True if p is memory a kernel on the current device may dereference: device
+// memory of this device, or managed memory.
+bool device_ptr_ok(const void* p);
 
 // ---- build (wt_build.cu) ----
 // layout: WT_LAYOUT_TREE or WT_LAYOUT_MATRIX.  h_src (optional): host symbols to
@@ -84,6 +94,7 @@ struct BatchTreeInfo {
 
 struct BatchDev {
     uint32_t ntrees, w, maxL, k_log2;
+    uint32_t lp_ctas;                // CTAs per SM of the persistent level pass
     uint64_t total_chunks, total_slots;
     BatchTreeInfo* info;
     TreeDesc* desc;

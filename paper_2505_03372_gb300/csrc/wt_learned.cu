@@ -393,7 +393,7 @@ static void init_mlp(float* P) {
 }
 
 void free_learned(wt_tree_s* t, cudaStream_t s) {
-    if (t->learned_mem) dev_free(t->learned_mem, s);
+    if (t->learned_mem) dev_free(t->learned_mem, s, tree_alloc(t));
     t->learned_mem = nullptr;
     t->learned_bytes = 0;
     memset(&t->learned, 0, sizeof(t->learned));
@@ -414,7 +414,7 @@ wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, ui
         }
     }
     void* mem = nullptr;
-    if (dev_alloc(&mem, off, s) != cudaSuccess) return WT_ENOMEM;
+    if (dev_alloc(&mem, off, s, tree_alloc(t)) != cudaSuccess) return WT_ENOMEM;
     t->learned_mem = mem;
     t->learned_bytes = off;
     uint8_t* M = static_cast<uint8_t*>(mem);
@@ -437,7 +437,10 @@ wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, ui
         // training pairs from the built levels, then Adam on every model at once
         void* scratch = nullptr;
         const size_t pbytes = (size_t)2 * L * pairs_cap * sizeof(float2);
-        if (dev_alloc(&scratch, pbytes + 2 * L * 4 + 256, s) != cudaSuccess) return WT_ENOMEM;
+        if (dev_alloc(&scratch, pbytes + 2 * L * 4 + 256, s, tree_alloc(t)) != cudaSuccess) {
+            free_learned(t, s);  // no half-trained model stays behind
+            return WT_ENOMEM;
+        }
         float2* pairs = static_cast<float2*>(scratch);
         uint32_t* npairs = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(scratch) + pbytes);
         WT_CUDA_TRY(cudaMemsetAsync(npairs, 0, 2 * L * 4, s));
@@ -468,7 +471,7 @@ wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, ui
             ProfScope ps("mlp_train", s);
             mlp_train_kernel<<<2 * L, kTrainThreads, sm, s>>>(pairs, npairs, pairs_cap, mlp, steps, lr, nullptr);
         }
-        dev_free(scratch, s);
+        dev_free(scratch, s, tree_alloc(t));
     }
     for (uint32_t l = 0; l < L; l++) {
         if (!t->level_size[l]) continue;
@@ -509,7 +512,7 @@ wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const u
             select_learned_kernel<true><<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, o.c, o.a, o.idx, d_out, q);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
-        if (o.mem) dev_free(o.mem, s);
+        if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps(name, s);
@@ -523,15 +526,7 @@ using namespace wt;
 
 static bool tree_valid(const wt_tree_s* t) { return t && t->magic == kTreeMagic; }
 
-static bool dev_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+static bool dev_ptr(const void* p) { return device_ptr_ok(p); }
 
 extern "C" {
 

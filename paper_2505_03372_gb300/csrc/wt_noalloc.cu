@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(kNaThreads) bv_support_kernel(const uint64_t* 
                                                                 uint16_t* __restrict__ l2, uint64_t* __restrict__ s0,
                                                                 uint64_t* __restrict__ s1, uint64_t s_cap,
                                                                 uint64_t ntiles, uint64_t* __restrict__ scratch,
-                                                                uint32_t* __restrict__ status) {
+                                                                uint32_t* __restrict__ status,
+                                                                uint64_t* __restrict__ total_ones) {
     __shared__ uint32_t s_wpre[kNaTileWords + 1];  // ones before each word of the tile
     __shared__ uint32_t s_wsum[kNaThreads / 32];
     __shared__ uint64_t s_tile, s_E;
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(kNaThreads) bv_support_kernel(const uint64_t* 
         s0[0] = 0;
         s1[0] = 0;
     }
+    if (tid == 0 && tile == ntiles - 1 && total_ones) *total_ones = E + ones;
     // select samples: position of every K-th one and every K-th zero
     const uint64_t m1lo = (E >> k_log2) + 1, m1hi = (E + ones) >> k_log2;
     const uint64_t m0lo = (R0 >> k_log2) + 1, m0hi = (R0 + zeros) >> k_log2;
@@ -178,18 +180,38 @@ __global__ void __launch_bounds__(kNaThreads) bv_support_kernel(const uint64_t* 
     }
 }
 
+// The scratch's device address per device, with the identity of the context it
+// was looked up in: a device reset makes a new context (a new identity), and the
+// next call looks the address up again instead of using a stale one.
 std::mutex g_na_mu;
 void* g_na_addr[256];
+unsigned long long g_na_ctx[256];
 bool g_na_ready[256];
 
-bool na_is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Identity of the current context (0 if the driver cannot tell).
+unsigned long long na_context_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
         cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur && get_id && get_cur(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
 }
 
 }  // namespace
@@ -199,14 +221,19 @@ using namespace wt;
 
 extern "C" wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64_t nbits, uint32_t sample_k,
                                                  uint64_t* d_l1, uint16_t* d_l2, uint64_t* d_s0, uint64_t* d_s1,
-                                                 uint64_t sample_capacity, uint32_t* d_status, wt_stream stream) {
+                                                 uint64_t sample_capacity, uint32_t* d_status, uint64_t* d_ones,
+                                                 wt_stream stream) {
     if (nbits == 0 || nbits > kNaMaxTiles * (uint64_t)kNaTileBits) return WT_EINVAL;  // beyond the static scratch
     if (sample_k < 256 || sample_k > (1u << 20) || (sample_k & (sample_k - 1))) return WT_EINVAL;
     if (sample_capacity < (nbits / sample_k) + 2) return WT_EINVAL;
-    if (!na_is_device_ptr(d_words) || !na_is_device_ptr(d_l1) || !na_is_device_ptr(d_l2) ||
-        !na_is_device_ptr(d_s0) || !na_is_device_ptr(d_s1))
+    if (!device_ptr_ok(d_words) || !device_ptr_ok(d_l1) || !device_ptr_ok(d_l2) || !device_ptr_ok(d_s0) ||
+        !device_ptr_ok(d_s1))
         return WT_EINVAL;
-    if (d_status && !na_is_device_ptr(d_status)) return WT_EINVAL;
+    if (d_status && !device_ptr_ok(d_status)) return WT_EINVAL;
+    if (d_ones && !device_ptr_ok(d_ones)) return WT_EINVAL;
+    // an error left pending by earlier work on this thread would otherwise be
+    // reported as this call's launch error
+    if (cudaPeekAtLastError() != cudaSuccess) return WT_ECUDA;
 
     // device address of the static scratch, looked up once per device with that device current
     int dev = 0;
@@ -214,10 +241,15 @@ extern "C" wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ready[dev]) {
+        const unsigned long long ctx = na_context_id();
+        if (!g_na_ready[dev] || g_na_ctx[dev] != ctx || ctx == 0) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_bv_scratch) != cudaSuccess) return WT_ECUDA;
+            if (cudaGetSymbolAddress(&p, g_bv_scratch) != cudaSuccess) {
+                g_na_ready[dev] = false;
+                return WT_ECUDA;
+            }
             g_na_addr[dev] = p;
+            g_na_ctx[dev] = ctx;
             g_na_ready[dev] = true;
         }
         scratch = g_na_addr[dev];
@@ -232,6 +264,6 @@ extern "C" wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64
         return WT_ECUDA;
     bv_support_kernel<<<(unsigned)ntiles, kNaThreads, 0, s>>>(d_words, nbits, k_log2, d_l1, d_l2, d_s0, d_s1,
                                                               sample_capacity, ntiles, static_cast<uint64_t*>(scratch),
-                                                              d_status);
+                                                              d_status, d_ones);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }

@@ -296,7 +296,7 @@ wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_k
     const uint64_t per_copy = al(q * 8) + al(q * 4) + al(d_c ? q * 4 : 8) + al(d_kind ? q : 8);
     const uint64_t o_hist = 0, o_offs = al(nh * 8), o_tmp = o_offs + al((nh + 1) * 8), o_copy = o_tmp + al(ntmp * 8);
     const uint64_t total = o_copy + 2 * per_copy;
-    if (dev_alloc(&o.mem, total, s) != cudaSuccess) return WT_ENOMEM;
+    if (dev_alloc(&o.mem, total, s, tree_alloc(t)) != cudaSuccess) return WT_ENOMEM;
     uint8_t* M = static_cast<uint8_t*>(o.mem);
     uint64_t* hist = reinterpret_cast<uint64_t*>(M + o_hist);
     uint64_t* offs = reinterpret_cast<uint64_t*>(M + o_offs);
@@ -371,7 +371,7 @@ wt_status launch_access(const wt_tree_s* t, const uint64_t* d_i, uint32_t* d_out
             WALK_LAUNCH(access_kernel<true>, t, q, s, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
-        if (o.mem) dev_free(o.mem, s);
+        if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps("access", s);
@@ -390,7 +390,7 @@ wt_status launch_rank(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d
             WALK_LAUNCH(rank_kernel<true>, t, q, s, o.c, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
-        if (o.mem) dev_free(o.mem, s);
+        if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps("rank", s);
@@ -409,7 +409,7 @@ wt_status launch_select(const wt_tree_s* t, const uint32_t* d_c, const uint64_t*
             WALK_LAUNCH(select_kernel<true>, t, q, s, o.c, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
-        if (o.mem) dev_free(o.mem, s);
+        if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps("select", s);
@@ -428,7 +428,7 @@ wt_status launch_mixed(const wt_tree_s* t, const uint8_t* d_kind, const uint32_t
             WALK_LAUNCH(mixed_kernel<true>, t, q, s, o.kind, o.c, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
-        if (o.mem) dev_free(o.mem, s);
+        if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps("mixed", s);

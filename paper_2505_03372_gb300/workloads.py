@@ -237,6 +237,29 @@ def make_batch(ntrees: int = 4096, seed: int = SEED_BASE + 3, device="cuda", log
     return buf, views, sg, queries
 
 
+def batch_subset(views, sigmas, q, lo: int, hi: int):
+    """Trees [lo, hi) of a batch with their queries (tree ids renumbered from
+    0), the symbols copied into a buffer of their own with every tree on a
+    16-byte boundary.  Returns (buffer, views, sigmas, queries) like make_batch."""
+    sel = list(views[lo:hi])
+    w = sel[0].element_size() if sel else 2
+    align = 16 // w
+    offs, tot = [], 0
+    for v in sel:
+        offs.append(tot)
+        tot += (v.numel() + align - 1) // align * align
+    device = q["tree"].device
+    dtype = sel[0].dtype if sel else torch.int16
+    buf = torch.zeros(max(tot, 1), dtype=dtype, device=device)
+    out_views = []
+    for v, o in zip(sel, offs):
+        buf[o:o + v.numel()] = v
+        out_views.append(buf[o:o + v.numel()])
+    m = (q["tree"] >= lo) & (q["tree"] < hi)
+    sub = {"tree": (q["tree"][m] - lo).to(torch.int32), "kind": q["kind"][m], "c": q["c"][m], "arg": q["arg"][m]}
+    return buf, out_views, list(sigmas[lo:hi]), sub
+
+
 # --------------------------------------------------------------------------
 # standalone bitvectors (the paper's binary rank/select experiments, whose
 # bitvectors follow Kurpicz's generator: a fill of 10, 50 or 90 %, ones either

@@ -143,21 +143,43 @@ def test_query_host_rejects_device_memory():
 
 
 @pytest.mark.parametrize("w,n,sigma,pinned", [(1, (1 << 27) + 12345, 96, True), (2, (1 << 25) + 7, 65536, False),
-                                              (4, 300001, 70000, True), (1, 1, 2, False)])
-def test_build_from_host_memory_equals_device_build(w, n, sigma, pinned):
-    """wt_build_host (64 MiB chunks copied while the histogram runs) builds the
-    same tree as wt_build on the same symbols, level by level."""
+                                              (4, 3 * (1 << 24) + 4321, 5000, True), (4, 300001, 70000, True),
+                                              (1, 1, 2, False)])
+def test_build_from_host_memory_matches_oracle(w, n, sigma, pinned):
+    """wt_build_host (64 MiB chunks copied while the histogram runs; the u32
+    case has three whole chunks and a ragged fourth) against the naive oracle
+    tree, every level's bits, counters and samples, C and the node table, and
+    its answers against the definitions; also equal to wt_build's tree."""
     sym = workloads.make_symbols(n, sigma, w, "zipf" if sigma < 1000 else "uniform", 1.0, seed=n % 1000 + w,
                                  device="cuda")
     h = sym.cpu()
     if pinned:
         h = h.pin_memory()
+    S = h.numpy().view({1: np.uint8, 2: np.uint16, 4: np.uint32}[w])
+    o2 = oracle.O2Tree(S, sigma, K=4096)
     with wt.build(sym, sigma) as td, wt.build(h, sigma) as th:
         a, b = td.info(), th.info()
-        assert a.levels == b.levels
-        for l in range(a.levels):
-            assert a.level_size[l] == b.level_size[l] and a.level_ones[l] == b.level_ones[l]
+        assert a.levels == b.levels == o2.L
+        for l in range(b.levels):
+            assert b.level_size[l] == o2.level_size(l) and b.level_ones[l] == o2.level_ones(l)
             for what in (wt.EXPORT_BITS, wt.EXPORT_L1, wt.EXPORT_L2, wt.EXPORT_S0, wt.EXPORT_S1):
-                assert np.array_equal(td.export(what, l), th.export(what, l)), (l, what)
-        assert np.array_equal(td.export(wt.EXPORT_C), th.export(wt.EXPORT_C))
+                g = th.export(what, l)
+                assert np.array_equal(g, o2.export(what, l)), (l, what)
+                assert np.array_equal(g, td.export(what, l)), (l, what)
+        assert np.array_equal(th.export(wt.EXPORT_C), o2.export(oracle.EXPORT_C))
+        if o2.L:
+            assert np.array_equal(th.export(wt.EXPORT_NODES), o2.export(oracle.EXPORT_NODES))
+        o1 = oracle.O1(S, sigma)
+        rng = np.random.default_rng(n)
+        q = 20000
+        i = rng.integers(0, n, q).astype(np.uint64)
+        cnt = np.diff(o1.C).astype(np.int64)
+        present = np.flatnonzero(cnt)
+        c = present[rng.integers(0, present.size, q)].astype(np.uint32)
+        j = (rng.random(q) * cnt[c]).astype(np.uint64) + 1
+        di = torch.from_numpy(i.view(np.int64)).cuda()
+        dc, dj = torch.from_numpy(c.view(np.int32)).cuda(), torch.from_numpy(j.view(np.int64)).cuda()
+        assert np.array_equal(th.access(di).cpu().numpy().view(np.uint32), o1.access(i))
+        assert np.array_equal(th.rank(dc, di).cpu().numpy().view(np.uint64), o1.rank(c, i))
+        assert np.array_equal(th.select(dc, dj).cpu().numpy().view(np.uint64), o1.select(c, j))
         assert th.status_sync() == wt.WT_OK

@@ -290,30 +290,32 @@ def test_repeated_builds_and_profile_counts():
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name", ["text", "large_alphabet", "learned"])
-def test_full_size_workloads_sampled(name):
-    """Full-size inputs, the bench's launch configuration; sampled queries against O1,
-    level 0 against its definition (top code bit of every symbol), sizes against C."""
+def test_full_size_workloads_match_oracle(name):
+    """Full-size inputs (2^30 u8 Zipf over 96, 2^28 u32 over 2^20, 2^30 u16
+    Zipf over 65536) in the bench's launch configuration: every level's bits,
+    L1/L2 counters and samples, C and the node table against the naive oracle
+    tree (built on the host cores, level by level), and sampled queries
+    against the definitions."""
     w, sym, q, counts = workloads.make_workload(name, device="cuda", scale_queries=0.002)
     t = wt.build(sym, w.sigma, sample_k=w.sample_k)
     S = _host(sym, w.symbol_bytes)
-    o1 = oracle.O1(S, w.sigma)
+    del sym
+    o2 = oracle.O2Tree(S, w.sigma, K=w.sample_k)
     inf = t.info()
-    code, ln, L = oracle.codes_split(w.sigma)
-    # level 0 bits: bit L-1 of the code of S[j]
-    top = ((code[: w.sigma] >> np.uint64(L - 1)) & np.uint64(1)).astype(np.uint8)
-    b0 = np.empty(S.size, np.uint8)
-    for a in range(0, S.size, 1 << 24):
-        b0[a:a + (1 << 24)] = top[S[a:a + (1 << 24)]]
-    words = np.packbits(b0, bitorder="little").view(np.uint64) if b0.size % 64 == 0 else None
-    g0 = t.export(wt.EXPORT_BITS, 0)
-    assert words is not None and np.array_equal(g0, words)
-    hist = np.diff(o1.C).astype(np.int64)
-    for l in range(L):
-        assert inf.level_size[l] == int(hist[ln[: w.sigma] > l].sum())
-    # L1 counters of every level against the level sizes: last entry <= ones
-    for l in range(L):
-        l1 = t.export(wt.EXPORT_L1, l)
-        assert l1[0] == 0 and np.all(np.diff(l1.astype(np.int64)) >= 0) and l1[-1] <= inf.level_ones[l]
+    assert inf.levels == o2.L
+    for l in range(o2.L):
+        assert inf.level_size[l] == o2.level_size(l) and inf.level_ones[l] == o2.level_ones(l), l
+        for what in (wt.EXPORT_BITS, wt.EXPORT_L1, wt.EXPORT_L2, wt.EXPORT_S0, wt.EXPORT_S1):
+            g = t.export(what, l)
+            r = o2.export(what, l)
+            if not np.array_equal(g, r):
+                bad = np.flatnonzero(g != r) if g.shape == r.shape else np.array([-1])
+                raise AssertionError(f"{name} level {l} export {what}: {bad.size} mismatches, first at {bad[:5]}")
+            del g, r
+    assert np.array_equal(t.export(wt.EXPORT_C), o2.export(oracle.EXPORT_C))
+    assert np.array_equal(t.export(wt.EXPORT_NODES), o2.export(oracle.EXPORT_NODES))
+    del o2
+    o1 = oracle.O1(S, w.sigma)
     for key, f in (("access_i", lambda: (_u32(t.access(q["access_i"])), o1.access(q["access_i"].cpu().numpy()))),
                    ("rank_c", lambda: (_u64(t.rank(q["rank_c"], q["rank_i"])), o1.rank(q["rank_c"].cpu().numpy(), q["rank_i"].cpu().numpy()))),
                    ("select_c", lambda: (_u64(t.select(q["select_c"], q["select_j"])), o1.select(q["select_c"].cpu().numpy(), q["select_j"].cpu().numpy())))):

@@ -54,3 +54,42 @@ def test_single_rank_is_unchanged():
     assert bench.job_ms(12.5, None) == 12.5
     assert bench.rank_seed(100, 0) == 100
     assert bench.job_value(1, 3_000_000, 10.0) == pytest.approx(300.0)
+
+
+def _tree_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_2505_03372_gb300 import workloads
+
+    buf, views, sigmas, q = workloads.make_batch(ntrees=37, seed=workloads.SEED_BASE + 3, device="cpu",
+                                                 log_n=(4, 12), log_q=(2, 6))
+    lo, hi = bench.shard_range(len(views), rank, world)
+    b2, v2, s2, q2 = workloads.batch_subset(views, sigmas, q, lo, hi)
+    # every tree of the share is the batch's tree, 16-byte aligned in the new buffer
+    same = all(torch.equal(a, views[lo + k]) for k, a in enumerate(v2))
+    aligned = all((v.data_ptr() - b2.data_ptr()) % 16 == 0 for v in v2)
+    # the share's queries are exactly the batch's queries of trees [lo, hi), renumbered
+    m = (q["tree"] >= lo) & (q["tree"] < hi)
+    qok = torch.equal(q2["tree"].long() + lo, q["tree"][m].long()) and torch.equal(q2["arg"], q["arg"][m])
+    counts = torch.tensor([hi - lo, q2["tree"].numel()], dtype=torch.int64)
+    dist.all_reduce(counts)
+    ranges = [torch.zeros(2, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(ranges, torch.tensor([lo, hi], dtype=torch.int64))
+    out[rank] = (same, aligned, qok, counts.tolist(), [r.tolist() for r in ranges], q["tree"].numel(), s2 == sigmas[lo:hi])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_split_the_batched_trees():
+    """The batched workload under torchrun: each rank takes a contiguous range
+    of the drawn trees (no collective on the data path); together the ranks
+    cover every tree and every query exactly once."""
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_tree_worker, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        same, aligned, qok, counts, ranges, total_q, sig_ok = out[r]
+        assert same and aligned and qok and sig_ok
+        assert counts == [37, total_q]
+        assert ranges == [[0, 19], [19, 37]]

@@ -262,6 +262,54 @@ def test_invariants_medium():
     assert sum(t.level_size(l) for l in range(t.L)) == int((hist * ln[:sigma].astype(np.int64)).sum())
 
 
+@pytest.mark.parametrize("sigma", [3, 96, 1000])
+def test_threaded_build_matches_pointer_tree(sigma):
+    """The O2 build split over several threads (more threads than the default
+    rule gives a small input) against the pointer-based tree, level by level,
+    and its counters and samples against the pure-Python counting."""
+    rng = np.random.default_rng(77 + sigma)
+    S = rng.integers(0, sigma, 3001).astype(np.uint16)
+    for threads in (1, 3, 7):
+        t = oracle.O2Tree(S, sigma, K=16, threads=threads)
+        levels = brute.pointer_tree_levels([int(x) for x in S], sigma)
+        assert t.L == len(levels)
+        for l, bits in enumerate(levels):
+            assert [int(x) for x in t.bits(l)] == bits, (threads, l)
+            L1, L2, s0, s1 = brute.counters(bits, 16)
+            assert t.export(oracle.EXPORT_L1, l).tolist() == L1
+            assert t.export(oracle.EXPORT_L2, l).tolist() == L2
+            assert t.export(oracle.EXPORT_S0, l).tolist() == s0
+            assert t.export(oracle.EXPORT_S1, l).tolist() == s1
+
+
+def test_threaded_build_and_queries_do_not_depend_on_threads():
+    """A level larger than 2^16 bits (so the sample export is threaded too):
+    one thread and several give the same tree; threaded query loops equal the
+    definitional oracle."""
+    rng = np.random.default_rng(5)
+    sigma, n = 1000, 300001
+    S = rng.integers(0, sigma, n).astype(np.uint16)
+    t1 = oracle.O2Tree(S, sigma, K=256, threads=1)
+    t5 = oracle.O2Tree(S, sigma, K=256, threads=5)
+    for l in range(t1.L):
+        for what in (oracle.EXPORT_BITS, oracle.EXPORT_L1, oracle.EXPORT_L2, oracle.EXPORT_S0, oracle.EXPORT_S1):
+            assert np.array_equal(t1.export(what, l), t5.export(what, l)), (l, what)
+    # samples of a large level against positions of the b-bits (numpy's flatnonzero)
+    bits = t5.bits(0)
+    for b, what in ((0, oracle.EXPORT_S0), (1, oracle.EXPORT_S1)):
+        pos = np.flatnonzero(bits == b)
+        want = np.concatenate([[0], pos[np.arange(256, pos.size + 1, 256) - 1]])
+        assert np.array_equal(t5.export(what, 0), want.astype(np.uint64))
+    o1 = oracle.O1(S, sigma)
+    i = rng.integers(0, n, 5000).astype(np.uint64)
+    c = rng.integers(0, sigma, 5000).astype(np.uint32)
+    assert np.array_equal(t5.query_mt(0, i, threads=4), o1.access(i))
+    assert np.array_equal(t5.query_mt(1, i, c, threads=3), o1.rank(c, i))
+    cnt = np.diff(o1.C).astype(np.int64)
+    j = (rng.random(5000) * cnt[c]).astype(np.uint64) + 1
+    assert np.array_equal(t5.query_mt(2, j, c, threads=6), o1.select(c, j))
+
+
 def test_node_start_alg8_matches_recursion():
     for sigma in list(range(2, 300)) + [1000, 4097, 5000]:
         t = oracle.O2Tree(np.zeros(1, np.uint16), sigma)
@@ -501,6 +549,18 @@ def test_bitvector_rank_select_by_brute_force():
             if b == 1 and cnt:
                 assert np.array_equal(oracle.bv_rank(bits, sel.astype(np.int64)), (j - 1).astype(np.uint64))
         assert np.array_equal(oracle.bv_rank(bits, i) + oracle.bv_rank(1 - bits, i), i.astype(np.uint64))
+
+
+def test_bitvector_support_by_brute_force():
+    """oracle.bitvector_support against the pure-Python counting, over sizes
+    around the 512- and 65536-bit blocks and all-zero / all-one vectors."""
+    rng = np.random.default_rng(17)
+    for n, fill, K in ((1, 0.5, 4), (511, 0.5, 8), (512, 1.0, 16), (513, 0.0, 16), (65536, 0.3, 256),
+                       (65536 * 2 + 700, 0.7, 512), (200003, 0.02, 64)):
+        bits = (rng.random(n) < fill).astype(np.uint8)
+        L1, L2, s0, s1 = brute.counters(bits.tolist(), K)
+        g = oracle.bitvector_support(bits, K)
+        assert g[0].tolist() == L1 and g[1].tolist() == L2 and g[2].tolist() == s0 and g[3].tolist() == s1, n
 
 
 def test_alphabet_map_by_brute_force():

@@ -8,9 +8,11 @@ scratch living in a static array inside libwt.
 
 The test compares its output with what wt_build stores for the same bits: a
 tree over the alphabet {0, 1} has a single level whose bits are the symbols,
-so wt_export of that level is the reference.  Each case calls the entry point
-twice in a row (the static scratch keeps the previous call's contents and must
-be cleared by the call itself).  This file is collected last on purpose.
+so wt_export of that level is the reference; and with the oracle's counters
+and samples, computed from prefix sums of the bits.  Each case calls the entry
+point twice in a row (the static scratch keeps the previous call's contents
+and must be cleared by the call itself).  This file is collected last on
+purpose.
 """
 import ctypes
 
@@ -19,6 +21,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_2505_03372_gb300 import binding as wt  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -48,14 +51,15 @@ def _call(words_dev, nbits, K, cap):
     s0 = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
     s1 = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ones = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     st = wt.lib().wt_bitvector_support_static(words_dev.data_ptr(), nbits, K, l1.data_ptr(), l2.data_ptr(),
-                                               s0.data_ptr(), s1.data_ptr(), cap, status.data_ptr(),
+                                               s0.data_ptr(), s1.data_ptr(), cap, status.data_ptr(), ones.data_ptr(),
                                                torch.cuda.current_stream().cuda_stream)
     assert st == wt.WT_OK, wt.status_str(st)
     torch.cuda.synchronize()
     assert status.item() == 0
     return (l1.cpu().numpy().view(np.uint64), l2.cpu().numpy().view(np.uint16), s0.cpu().numpy().view(np.uint64),
-            s1.cpu().numpy().view(np.uint64))
+            s1.cpu().numpy().view(np.uint64), int(ones.item()))
 
 
 @pytest.mark.parametrize("nbits,density,K", [
@@ -73,13 +77,18 @@ def test_matches_wt_build_twice(nbits, density, K):
     ref = _reference(bits, K)
     words = torch.from_numpy(ref[wt.EXPORT_BITS].view(np.int64).copy()).cuda()
     cap = nbits // K + 2
+    o_l1, o_l2, o_s0, o_s1 = oracle.bitvector_support(bits, K)
     for _ in range(2):
-        l1, l2, s0, s1 = _call(words, nbits, K, cap)
+        l1, l2, s0, s1, ones = _call(words, nbits, K, cap)
         assert np.array_equal(l1, ref[wt.EXPORT_L1])
         assert np.array_equal(l2, ref[wt.EXPORT_L2])
         n0, n1 = ref[wt.EXPORT_S0].size, ref[wt.EXPORT_S1].size
         assert np.array_equal(s0[:n0], ref[wt.EXPORT_S0])
         assert np.array_equal(s1[:n1], ref[wt.EXPORT_S1])
+        # and against the definition
+        assert np.array_equal(l1, o_l1) and np.array_equal(l2, o_l2)
+        assert np.array_equal(s0[:o_s0.size], o_s0) and np.array_equal(s1[:o_s1.size], o_s1)
+        assert ones == int(bits.sum())
 
 
 def test_rejects_inputs_beyond_the_static_scratch():
@@ -89,10 +98,13 @@ def test_rejects_inputs_beyond_the_static_scratch():
     s = torch.cuda.current_stream().cuda_stream
     too_big = (1 << 32) + 1
     st = wt.lib().wt_bitvector_support_static(words.data_ptr(), too_big, 4096, small.data_ptr(), l2.data_ptr(),
-                                               small.data_ptr(), small.data_ptr(), too_big // 4096 + 2, None, s)
+                                               small.data_ptr(), small.data_ptr(), too_big // 4096 + 2, None, None, s)
     assert st == wt.WT_EINVAL
     # a host buffer is refused before anything is enqueued
     host = np.zeros(16, np.uint64)
     st = wt.lib().wt_bitvector_support_static(host.ctypes.data, 64, 4096, small.data_ptr(), l2.data_ptr(),
-                                               small.data_ptr(), small.data_ptr(), 2, None, s)
+                                               small.data_ptr(), small.data_ptr(), 2, None, None, s)
+    assert st == wt.WT_EINVAL
+    st = wt.lib().wt_bitvector_support_static(words.data_ptr(), 64, 4096, small.data_ptr(), l2.data_ptr(),
+                                               small.data_ptr(), small.data_ptr(), 2, None, host.ctypes.data, s)
     assert st == wt.WT_EINVAL
