@@ -66,11 +66,11 @@ typedef enum {
  *  free(ptr, stream, ctx)  returns a block: the library has enqueued its last use
  *        of it on `stream`, the stream it was allocated on, so it may be handed
  *        out again to work ordered after that point on that stream.
- * Every block is released on the stream it was taken on: the caller's
- * `stream`, or, for the staging buffers of wt_build_host and wt_query_host,
- * the library's own copy stream of the device (taken there so that the
- * copies overlap work already queued on `stream`; released there after that
- * stream has waited for the buffer's last use).
+ * Every request is made on the caller's `stream` and every block is
+ * released on it, after its last use there.  (So the staging buffers of
+ * wt_build_host and wt_query_host are taken on `stream` too, and their copies
+ * wait for the work already queued on it; with the default pool those copies
+ * overlap that work instead.)
  * The struct is copied; ctx and the functions must stay valid until the last
  * handle built with them is destroyed.  The callbacks run on the calling
  * thread, inside the library call.
@@ -151,8 +151,7 @@ void wt_destroy(wt_tree tree);
  * chunk on `stream` as it arrives, so the copy overlaps earlier work on the
  * stream and the histogram; the level passes then run as in wt_build.  The
  * device copy of the symbols comes from the allocator in opt (or the
- * stream-ordered pool), taken and returned on the library's copy stream after
- * the build; h_symbols must stay valid until the call returns (it
+ * stream-ordered pool) and is returned after the build; h_symbols must stay valid until the call returns (it
  * synchronises once, as wt_build does).  Arguments and results as wt_build;
  * a device pointer as h_symbols returns WT_EINVAL.
  */
@@ -215,8 +214,7 @@ wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_
  * the answers after `stream` has been synchronised, and the host buffers must
  * stay valid until then.  Data errors are reported as for the device calls.
  * Device memory: two chunks of arguments and answers, from the tree's allocator
- * (or the stream-ordered pool), taken and returned on the library's copy
- * stream, after the last copy-out.
+ * (or the stream-ordered pool), returned after the last copy-out.
  */
 wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, const uint32_t* h_c,
                         const uint64_t* h_arg, void* h_out, uint64_t q, uint64_t chunk, wt_stream stream);
@@ -269,27 +267,40 @@ enum {
     WT_EXPORT_CODES = 6,
     WT_EXPORT_LENS = 7,
     WT_EXPORT_NODES = 8,
-    WT_EXPORT_EPS0 = 9,  /* learned select: per-segment bound for zeros, floor(zeros/K)+1 uint32 */
-    WT_EXPORT_EPS1 = 10, /* learned select: per-segment bound for ones, floor(ones/K)+1 uint32 */
-    WT_EXPORT_MLP = 11   /* learned select: 2 x 97 float MLP parameters of the level (b = 0, then b = 1) */
+    WT_EXPORT_EPS0 = 9,   /* learned select: bound of every anchor segment of the zeros, in bits,
+                             floor(zeros / (4 K)) + 1 uint32 */
+    WT_EXPORT_EPS1 = 10,  /* the same for the ones */
+    WT_EXPORT_MLP = 11,   /* learned select: 2 x 97 float MLP parameters of the level (b = 0, then b = 1) */
+    WT_EXPORT_RESID0 = 12, /* learned select (PLA): three knot residuals R_1..3 per anchor segment of the
+                             zeros, in bits, 3 (floor(zeros / (4 K)) + 1) int32 */
+    WT_EXPORT_RESID1 = 13  /* the same for the ones */
 };
 wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, uint64_t* count);
 
 /*
  * Learned select (not in the paper; the workload's "learned select").  For
- * every level and bit value b a model predicts the position of the k-th b-bit
- * from the select samples around k, which serve as knots: the sample positions
- * S_b[m] of the (m K)-th b-bits (Section 4.2), with the virtual (count_b + 1)-th
- * b-bit at the end of the level.
- *   mode 1 (PLA): linear interpolation between the knots.
- *   mode 2 (MLP): the fraction u = (k - mK) / (segment length) is mapped to
+ * every level and bit value b a model predicts the position of the k-th b-bit.
+ * The ranks are cut into anchor segments of 4 K ranks: segment m runs from the
+ * (4 m K)-th b-bit to the (4 (m+1) K)-th, whose positions are select samples
+ * the build already stores (Section 4.2), or to the virtual (count_b + 1)-th
+ * b-bit at the end of the level.  Each segment keeps one 8-byte record: three
+ * knot residuals and its error bound (about half the bytes of the select
+ * samples).
+ *   mode 1 (PLA): piecewise-linear with fitted knots: knot t = 1, 2, 3 sits at
+ *          rank k0 + floor(t (k1 - k0) / 4) and position x0 + floor(t (x1 -
+ *          x0) / 4) + R_t, the residuals R_t (WT_EXPORT_RESID0/1) fitted on
+ *          the GPU by least squares to the positions of the segment's b-bits;
+ *          a rank is predicted from its two knots (ka, xa), (kb, xb) as xa +
+ *          min(trunc(f(k - ka) * (f(xb - xa) / f(kb - ka))), xb - xa), each
+ *          step a correctly rounded FP32 operation.
+ *   mode 2 (MLP): the fraction u = (k - 4 m K) / (segment length) is mapped to
  *          u + g(u), g a 1 -> 32 -> 1 ReLU network in FP32 per (level, b), trained
  *          on the GPU with Adam on (u, position fraction) pairs drawn from the
  *          built levels (opt->pairs per model, opt->steps steps, learning rate
- *          opt->lr); g starts at 0, i.e. at mode 1.
+ *          opt->lr); g starts at 0, the line through the anchors.
  * wt_train_select then evaluates the model at the rank of every b-bit of every
  * level and stores per segment the largest distance between prediction and
- * position (WT_EXPORT_EPS0/1).  wt_select_learned answers the same queries as
+ * position, rounded up (WT_EXPORT_EPS0/1).  wt_select_learned answers the same queries as
  * wt_select: per level it searches only the window prediction +- bound; if the
  * counters show the bit is outside the window the level falls back to the
  * sampled select and a counter records it (wt_learned_info).  Results are
@@ -312,9 +323,11 @@ typedef struct {
     uint32_t mode;
     uint32_t pad;
     uint64_t fallbacks;                     /* level searches that left their window, since training */
-    uint64_t model_bytes;                   /* device bytes of bounds + parameters */
+    uint64_t model_bytes;                   /* device bytes of the records (residuals, bounds) + parameters */
     double eps_mean[WT_MAX_LEVELS][2];      /* mean per-segment bound, per level and b */
     uint32_t eps_max[WT_MAX_LEVELS][2];
+    uint64_t anchor_bytes;                  /* bytes of the select samples that serve as anchors (8 per
+                                               segment; stored once, with the tree) */
 } wt_learned_info_t;
 
 /* Synchronises the tree's stream; copies bound statistics to the host. */

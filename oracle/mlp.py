@@ -160,3 +160,121 @@ def predict_mlp_f32_all(k, k0, k1, x0, x1, P):
     span = x1 - x0
     off = (span.astype(np.float32) * hh).astype(np.float32).astype(np.int64)
     return x0 + np.minimum(off, span)
+
+
+# --------------------------------------------------------------------------
+# piecewise-linear model with fitted knots (the learned select's first model)
+#
+# Anchor segment m of a level and bit value b covers the ranks k with
+# floor(k / (A K)) = m (A = ANCHOR consecutive select samples per segment);
+# its ends are the anchors (k0, x0) = (m A K, S_b[A m]) and (k1, x1) =
+# ((m+1) A K, S_b[A (m+1)]), or (count_b + 1, size) for the last segment.
+# Knot t (t = 0..4) sits at rank kappa_t = k0 + floor(t (k1 - k0) / 4)
+# (kappa_4 = k1) and position x0 + floor(t (x1 - x0) / 4) + R_t, with the
+# fitted residuals R_1..3 (bits, signed) and R_0 = R_4 = 0.  A rank is
+# predicted from the two knots around it, (ka, xa) and (kb, xb), as xa +
+# min(trunc(f(k - ka) * (f(xb - xa) / f(kb - ka))), xb - xa) with f the
+# rounding to float32 and each product and quotient rounded to float32.
+# Segments shorter than four ranks interpolate between the anchors alone.
+# --------------------------------------------------------------------------
+
+ANCHOR = 4
+NKNOT = 3
+
+
+def anchor_knots(samples, total, size, m, K, A=ANCHOR):
+    """(k0, k1, x0, x1) of anchor segment m from the level's select samples."""
+    KA = A * K
+    k0, x0 = m * KA, int(samples[A * m])
+    if (m + 1) * KA <= total:
+        return k0, (m + 1) * KA, x0, int(samples[A * (m + 1)])
+    return k0, total + 1, x0, int(size)
+
+
+def spline_knots(kn, R):
+    """Knot ranks kappa_0..4 and positions xi_0..4 of a segment with residuals R[0..2]."""
+    k0, k1, x0, x1 = kn
+    kap = [k0 + ((t * (k1 - k0)) >> 2) for t in range(4)] + [k1]
+    xi = [x0] + [x0 + ((t * (x1 - x0)) >> 2) + int(R[t - 1]) for t in (1, 2, 3)] + [x1]
+    return kap, xi
+
+
+def interp_f32(ka, kb, xa, xb, k):
+    """xa + min(trunc(f(k - ka) * (f(xb - xa) / f(kb - ka))), xb - xa), float32 steps."""
+    f = np.float32
+    slope = f(f(xb - xa) / f(kb - ka))
+    off = int(f(f(k - ka) * slope))
+    return xa + min(off, xb - xa)
+
+
+def predict_spline(kn, R, k):
+    """Prediction for rank k (knots must be non-decreasing)."""
+    k0, k1, x0, x1 = kn
+    if k1 - k0 < 4:
+        return interp_f32(k0, k1, x0, x1, k)
+    kap, xi = spline_knots(kn, R)
+    t = int(k >= kap[1]) + int(k >= kap[2]) + int(k >= kap[3])
+    return interp_f32(kap[t], kap[t + 1], xi[t], xi[t + 1], k)
+
+
+def predict_spline_all(k, k0, k1, x0, x1, R):
+    """predict_spline for arrays: k, k0, k1, x0, x1 int64 arrays, R (len, 3) int64."""
+    k, k0, k1, x0, x1 = (np.asarray(a, np.int64) for a in (k, k0, k1, x0, x1))
+    R = np.asarray(R, np.int64).reshape(-1, 3)
+    span = k1 - k0
+    kap = [k0 + ((t * span) >> 2) for t in range(4)] + [k1]
+    xi = [x0] + [x0 + ((t * (x1 - x0)) >> 2) + R[:, t - 1] for t in (1, 2, 3)] + [x1]
+    t = (k >= kap[1]).astype(np.int64) + (k >= kap[2]) + (k >= kap[3])
+    short = span < 4
+    t = np.where(short, 0, t)
+    kap_a, xi_a = np.stack(kap), np.stack(xi)
+    idx = np.arange(k.size)
+    ka = np.where(short, k0, kap_a[t, idx])
+    kb = np.where(short, k1, kap_a[t + 1, idx])
+    xa = np.where(short, x0, xi_a[t, idx])
+    xb = np.where(short, x1, xi_a[t + 1, idx])
+    f = np.float32
+    slope = ((xb - xa).astype(f) / np.maximum(kb - ka, 1).astype(f)).astype(f)
+    off = ((k - ka).astype(f) * slope).astype(f).astype(np.int64)
+    return xa + np.minimum(off, xb - xa)
+
+
+def segment_anchor_all(samples, total, size, K, A=ANCHOR):
+    """For every rank k = 1..total: k, its segment m and the segment's anchors."""
+    k = np.arange(1, total + 1, dtype=np.int64)
+    KA = A * K
+    m = k // KA
+    samples = np.asarray(samples, np.int64)
+    k0 = m * KA
+    x0 = samples[A * m]
+    has_next = (m + 1) * KA <= total
+    k1 = np.where(has_next, (m + 1) * KA, total + 1)
+    x1 = np.where(has_next, samples[np.minimum(A * (m + 1), samples.size - 1)], size)
+    return k, m, k0, k1, x0, x1
+
+
+def fit_spline_lsq(kn, ks, pos):
+    """Least-squares residuals R_1..3 (FP64) of one segment: minimise
+    sum_k (base(k) + sum_t R_t phi_t(k) - pos(k))^2 over its ranks ks with
+    positions pos, base the untrained model (the piecewise-linear curve through
+    the knots with R = 0) and phi_t the hat function that is 1 at kappa_t and
+    0 at the neighbouring knots (the normal equations, a 3x3 system)."""
+    k0, k1, x0, x1 = kn
+    ks = np.asarray(ks, np.float64)
+    pos = np.asarray(pos, np.float64)
+    if k1 - k0 < 4 or ks.size == 0:
+        return np.zeros(3)
+    kap, xi0 = spline_knots(kn, [0, 0, 0])
+    kap = np.array(kap, np.float64)
+    base = np.interp(ks, kap, np.array(xi0, np.float64))
+    Phi = np.zeros((ks.size, 3))
+    for t in (1, 2, 3):
+        up = (ks >= kap[t - 1]) & (ks <= kap[t])
+        dn = (ks > kap[t]) & (ks <= kap[t + 1])
+        Phi[up, t - 1] = (ks[up] - kap[t - 1]) / (kap[t] - kap[t - 1])
+        Phi[dn, t - 1] = (kap[t + 1] - ks[dn]) / (kap[t + 1] - kap[t])
+    A = Phi.T @ Phi
+    y = Phi.T @ (pos - base)
+    if abs(np.linalg.det(A)) < 1e-12:
+        return np.linalg.lstsq(A, y, rcond=None)[0]
+    return np.linalg.solve(A, y)

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libwt.so")
 
 WT_OK, WT_EINVAL, WT_ESYMBOL, WT_ENOMEM, WT_ECUDA, WT_EQUERY, WT_ETIMEOUT, WT_EUNSUPPORTED = range(8)
 EXPORT_BITS, EXPORT_L1, EXPORT_L2, EXPORT_S0, EXPORT_S1, EXPORT_C, EXPORT_CODES, EXPORT_LENS, EXPORT_NODES = range(9)
-EXPORT_EPS0, EXPORT_EPS1, EXPORT_MLP = 9, 10, 11
+EXPORT_EPS0, EXPORT_EPS1, EXPORT_MLP, EXPORT_RESID0, EXPORT_RESID1 = 9, 10, 11, 12, 13
+ANCHOR = 4  # select samples per anchor segment of the learned select
 LEARN_NONE, LEARN_PLA, LEARN_MLP = 0, 1, 2
 MLP_PARAMS = 97
 MAX_LEVELS = 26
@@ -124,6 +125,7 @@ class LearnedInfo(ctypes.Structure):
         ("model_bytes", ctypes.c_uint64),
         ("eps_mean", (ctypes.c_double * 2) * MAX_LEVELS),
         ("eps_max", (ctypes.c_uint32 * 2) * MAX_LEVELS),
+        ("anchor_bytes", ctypes.c_uint64),
     ]
 
 
@@ -427,7 +429,7 @@ class Tree:
         cnt = ctypes.c_uint64()
         _check(lib().wt_export(self._h, level, what, None, ctypes.byref(cnt)), "wt_export")
         dt = {EXPORT_L2: np.uint16, EXPORT_LENS: np.uint8, EXPORT_EPS0: np.uint32, EXPORT_EPS1: np.uint32,
-              EXPORT_MLP: np.float32}.get(what, np.uint64)
+              EXPORT_MLP: np.float32, EXPORT_RESID0: np.int32, EXPORT_RESID1: np.int32}.get(what, np.uint64)
         width = 4 if what == EXPORT_NODES else 1
         out = np.zeros(cnt.value * width, dt)
         if cnt.value:

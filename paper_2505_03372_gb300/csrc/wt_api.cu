@@ -157,11 +157,14 @@ static bool is_host_ptr(const void* p) {
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
-// The library's two copy streams of the current device (host-to-device and
+// The library's copy streams of the current device (host-to-device and
 // device-to-host staging of wt_build_host and wt_query_host), created on first
 // use and kept for the life of the process.  A device reset destroys them: the
 // next call on that device after a reset fails with WT_ECUDA.
-static bool copy_streams(cudaStream_t* h2d, cudaStream_t* d2h) {
+struct Staging {
+    cudaStream_t h2d, d2h;
+};
+static bool staging_streams(Staging* out) {
     static std::mutex mu;
     static cudaStream_t st[256][2];
     int dev = 0;
@@ -172,9 +175,22 @@ static bool copy_streams(cudaStream_t* h2d, cudaStream_t* d2h) {
             st[dev][k] = nullptr;
             return false;
         }
-    *h2d = st[dev][0];
-    *d2h = st[dev][1];
+    out->h2d = st[dev][0];
+    out->d2h = st[dev][1];
     return true;
+}
+
+// `waiter` waits for the work queued on `on` so far (an event; a host
+// synchronisation if no event can be made).
+static void order_after(cudaStream_t waiter, cudaStream_t on) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ev, on) == cudaSuccess &&
+        cudaStreamWaitEvent(waiter, ev, 0) == cudaSuccess) {
+        cudaEventDestroy(ev);
+        return;
+    }
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamSynchronize(on);
 }
 
 static wt_tree_s* new_tree(cudaStream_t stream, const wt_allocator* alloc) {
@@ -261,27 +277,21 @@ wt_status wt_build_host(const void* h_symbols, uint64_t n, uint32_t sigma, uint3
     if (layout != WT_LAYOUT_TREE && layout != WT_LAYOUT_MATRIX) return WT_EINVAL;
     const wt_allocator* alloc = opt ? opt->allocator : nullptr;
     if (alloc && (!alloc->alloc || !alloc->free)) return WT_EINVAL;
-    // The device copy lives on the library's copy stream: allocated there,
-    // filled there chunk by chunk (`stream` waits per chunk), and returned there
-    // once that stream has waited for its last use on `stream`.  The copies do
-    // not wait for the work already queued on `stream`, and a caller's
-    // allocator sees the block taken and returned on one stream.
-    cudaStream_t cs = nullptr, unused = nullptr;
-    if (!copy_streams(&cs, &unused)) return WT_ECUDA;
+    // The device copy is filled chunk by chunk on the library's copy stream
+    // (`stream` waits per chunk).  From the pool it is taken on that copy
+    // stream, so the copies need not wait for the work already queued on
+    // `stream`; a caller's allocator gets the request on `stream` (the stream
+    // it is released on), and the copies then wait for that point.
+    Staging sg;
+    if (!staging_streams(&sg)) return WT_ECUDA;
     void* d_buf = nullptr;
-    if (n && dev_alloc(&d_buf, n * symbol_bytes, cs, alloc) != cudaSuccess) return WT_ENOMEM;
+    if (n && dev_alloc(&d_buf, n * symbol_bytes, alloc ? stream : sg.h2d, alloc) != cudaSuccess) return WT_ENOMEM;
+    if (n && alloc) order_after(sg.h2d, stream);
     wt_tree_s* t = new_tree(stream, alloc);
-    wt_status st = build_tree(d_buf, n, sigma, symbol_bytes, K, stream, t, layout, h_symbols, cs);
+    wt_status st = build_tree(d_buf, n, sigma, symbol_bytes, K, stream, t, layout, h_symbols, sg.h2d);
     if (n) {
-        cudaEvent_t ev = nullptr;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ev, stream) ==
-                cudaSuccess && cudaStreamWaitEvent(cs, ev, 0) == cudaSuccess) {
-            cudaEventDestroy(ev);
-        } else {
-            if (ev) cudaEventDestroy(ev);
-            cudaStreamSynchronize(stream);
-        }
-        dev_free(d_buf, cs, alloc);  // stream-ordered on the copy stream: after the level passes that read it
+        order_after(stream, sg.h2d);     // every chunk copied (also when the build stopped early)
+        dev_free(d_buf, stream, alloc);  // after the histogram and the level passes that read it
     }
     if (st != WT_OK) {
         release_tree(t);
@@ -339,7 +349,10 @@ struct HostPipe {
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_walk[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     bool ok = true;
     HostPipe() {
-        ok = copy_streams(&h2d, &d2h);
+        Staging sg;
+        ok = staging_streams(&sg);
+        h2d = sg.h2d;
+        d2h = sg.d2h;
         for (int b = 0; b < 2 && ok; b++)
             ok = cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&ev_walk[b], cudaEventDisableTiming) == cudaSuccess &&
@@ -375,11 +388,13 @@ wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, cons
     const int nbuf = nch > 1 ? 2 : 1;
     HostPipe hp;
     if (!hp.ok) return WT_ECUDA;
-    // the buffers are taken on the copy-in stream (no wait for the work queued
-    // on `stream`) and returned on it after the last copy-out
+    // From the pool the buffers are taken on the copy-in stream (no wait for the
+    // work queued on `stream`); a caller's allocator gets the request on
+    // `stream`, where they are also released, and the copy-in stream waits.
     const wt_allocator* alloc = tree_alloc(tree);
     void* mem = nullptr;
-    if (dev_alloc(&mem, per * nbuf, hp.h2d, alloc) != cudaSuccess) return WT_ENOMEM;
+    if (dev_alloc(&mem, per * nbuf, alloc ? stream : hp.h2d, alloc) != cudaSuccess) return WT_ENOMEM;
+    if (alloc) order_after(hp.h2d, stream);
     uint8_t* M = static_cast<uint8_t*>(mem);
     cudaStream_t s = stream;
     wt_status st = WT_OK;
@@ -429,7 +444,7 @@ wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, cons
         cudaStreamSynchronize(s);  // no events: order by waiting on the host instead
         cudaStreamSynchronize(hp.d2h);
         cudaStreamSynchronize(hp.h2d);
-        dev_free(mem, hp.h2d, alloc);
+        dev_free(mem, alloc ? s : hp.d2h, alloc);
         if (walked) cudaEventDestroy(walked);
         return WT_ECUDA;
     }
@@ -437,8 +452,7 @@ wt_status wt_query_host(wt_tree tree, uint32_t kind, const uint8_t* h_kind, cons
     cudaStreamWaitEvent(hp.d2h, walked, 0);
     cudaEventRecord(done, hp.d2h);
     cudaStreamWaitEvent(s, done, 0);
-    cudaStreamWaitEvent(hp.h2d, done, 0);
-    dev_free(mem, hp.h2d, alloc);  // after the last copy-out
+    dev_free(mem, alloc ? s : hp.d2h, alloc);  // after the last copy-out
     cudaEventDestroy(walked);
     cudaEventDestroy(done);
     return st;
@@ -522,18 +536,16 @@ wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, ui
             }
         }
         return WT_OK;
-    } else if (what == WT_EXPORT_EPS0 || what == WT_EXPORT_EPS1 || what == WT_EXPORT_MLP) {
+    } else if (what == WT_EXPORT_EPS0 || what == WT_EXPORT_EPS1 || what == WT_EXPORT_MLP ||
+               what == WT_EXPORT_RESID0 || what == WT_EXPORT_RESID1) {
         if (level >= L || tree->learned.mode == kLearnNone) return WT_EUNSUPPORTED;
         if (what == WT_EXPORT_MLP) {
             cnt = 2 * kMlpParams;
             src = tree->learned.mlp + 2 * level * kMlpParams;
             esz = 4;
         } else {
-            const uint32_t b = what == WT_EXPORT_EPS1;
-            const uint64_t c = b ? tree->level_ones[level] : tree->level_size[level] - tree->level_ones[level];
-            cnt = (c >> d.k_log2) + 1;
-            src = tree->learned.eps[level][b];
-            esz = 4;
+            const uint32_t b = (what == WT_EXPORT_EPS1 || what == WT_EXPORT_RESID1) ? 1u : 0u;
+            return export_learned(tree, level, b, what == WT_EXPORT_RESID0 || what == WT_EXPORT_RESID1, h_dst, count);
         }
     } else {
         if (level >= L) return WT_EINVAL;

@@ -215,19 +215,28 @@ struct LevelPassArgs {
     CodeParams cp;       // used when re-encoding at level 0
 };
 
-// Learned select (wt_train_select): per level and bit value b, the position of
-// the k-th b-bit is predicted between the select samples around k (the knots)
-// and the true position lies within eps[b][k >> k_log2] of the prediction.
+// Learned select (wt_train_select).  Per level and bit value b the b-bits'
+// ranks are cut into anchor segments of kAnchor select samples (kAnchor K
+// ranks); segment m runs between the anchors S_b[kAnchor m] and
+// S_b[kAnchor (m+1)] (the build's samples, not stored again).  Each segment
+// has one 8-byte record: three knot residuals (int16, in units of 2^rsh bits)
+// of the fitted piecewise-linear model and the segment's error bound (uint16,
+// in units of 2^esh bits): the k-th b-bit lies within the bound of the
+// model's prediction for k.
 constexpr uint32_t kMlpHidden = 32;
 constexpr uint32_t kMlpParams = 3 * kMlpHidden + 1;  // w1[32], b1[32], w2[32], b2
 constexpr uint32_t kLearnNone = 0, kLearnPla = 1, kLearnMlp = 2;
+constexpr uint32_t kAnchorLog2 = 2;  // kAnchor = 4 samples per anchor segment
+constexpr uint32_t kKnots = 3;       // interior knots per anchor segment
 
 struct LearnedDesc {
-    uint32_t mode;                     // kLearnNone / kLearnPla / kLearnMlp
+    uint32_t mode;                       // kLearnNone / kLearnPla (fitted knots) / kLearnMlp
     uint32_t pad;
-    const uint32_t* eps[kMaxLevels][2];  // per-segment error bounds, (count_b >> k_log2) + 1 entries
-    const float* mlp;                  // [level][b][kMlpParams], mode kLearnMlp only
-    unsigned long long* fallbacks;     // queries whose window check failed (answered by sampled select)
+    const ushort4* rec[kMaxLevels][2];   // (count_b >> (k_log2 + kAnchorLog2)) + 1 records: r1, r2, r3, eps
+    uint8_t rsh[kMaxLevels][2];          // residual unit 2^rsh bits
+    uint8_t esh[kMaxLevels][2];          // bound unit 2^esh bits
+    const float* mlp;                    // [level][b][kMlpParams], mode kLearnMlp only
+    unsigned long long* fallbacks;       // queries whose window check failed (answered by sampled select)
 };
 
 // ---------------------------------------------------------------------------

@@ -75,6 +75,7 @@ wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, ui
 wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out,
                                 uint64_t q, cudaStream_t s);
 void free_learned(wt_tree_s* t, cudaStream_t s);
+wt_status export_learned(const wt_tree_s* t, uint32_t level, uint32_t b, bool resid, void* h_dst, uint64_t* count);
 
 // ---- batches of trees (wt_batch.cu, built by wt_build.cu) ----
 struct BatchTreeInfo {

@@ -1,24 +1,31 @@
 // Learned select: a model per (level, bit value b) predicts where the k-th
-// b-bit of a level lies, a stored per-segment bound eps makes the prediction
+// b-bit of a level lies, a stored per-segment bound makes the prediction
 // exact, and the sampled select of Algorithm 2 is the fallback.
 //
-// Knots.  The build already stores, per level and b, the position S_b[m] of
-// the (m*K)-th b-bit (Section 4.2).  Those (rank -> position) pairs are the
-// knots of every model: k in segment m = k >> log2(K) lies between
-// (k0 = m*K, x0 = S_b[m]) and (k1 = (m+1)*K, x1 = S_b[m+1]); the last segment
-// ends at the virtual (count_b + 1)-th b-bit at position size_l.
+// Anchor segments.  The build stores, per level and b, the position S_b[m] of
+// the (m K)-th b-bit (Section 4.2).  Every kAnchor-th of those pairs is an
+// anchor: anchor segment m holds the ranks k with floor(k / (kAnchor K)) = m
+// and runs from (k0, x0) = (m kAnchor K, S_b[kAnchor m]) to (k1, x1) =
+// ((m+1) kAnchor K, S_b[kAnchor (m+1)]), the last one to the virtual
+// (count_b + 1)-th b-bit at position size_l.  Nothing of the anchors is stored
+// again; each segment owns one 8-byte record.
 //
-// Models.  PLA: linear interpolation between the knots (the predictor with
-// nothing learned).  MLP: the within-segment fraction u = (k - k0) / (k1 - k0)
-// is mapped to h = u + g(u), g a 1 -> 32 -> 1 ReLU network in FP32 shared by all
-// segments of a (level, b); prediction x0 + floor((x1 - x0) * h).  g is trained
-// on the GPU (Adam, full-batch) on pairs (u, (pos - x0) / (x1 - x0)) that the
-// scan kernel enumerates from the built levels; it starts at g = 0, i.e. at PLA.
+// Models.  PLA (fitted knots): knot t = 0..4 sits at rank kappa_t = k0 +
+// floor(t (k1 - k0) / 4) and position x0 + floor(t (x1 - x0) / 4) + R_t, the
+// residuals R_1..3 fitted on the GPU by least squares to the positions of the
+// segment's b-bits (the hat-function basis gives a 3x3 system per segment; R_0
+// = R_4 = 0); a rank is predicted by interpolating between the two knots
+// around it with two correctly rounded FP32 operations.  Untrained (R = 0) it
+// is the line through the anchors.  Nothing in a prediction divides integers.  MLP: the fraction u = (k - k0) / (k1 - k0) is
+// mapped to u + g(u), g a 1 -> 32 -> 1 ReLU network in FP32 shared by all
+// segments of a (level, b), trained with Adam on the GPU (g starts at 0, the
+// line through the anchors).
 //
 // Bounds.  A scan over every bit of every level evaluates the model at every
-// b-bit's rank k and keeps eps_b[m] = max |prediction(k) - position(k)| per
-// segment.  The prediction is a fixed sequence of correctly rounded operations
-// (__fmaf_rn, __fmul_rn, __fdiv_rn), so the query reproduces it exactly.
+// b-bit's rank and keeps the segment's largest |prediction - position|, stored
+// rounded up to a unit of 2^esh bits.  The MLP's prediction is a fixed chain of
+// correctly rounded operations (__fmaf_rn, __fmul_rn, __fdiv_rn), so the query
+// recomputes exactly the value the bound was taken on.
 //
 // Query.  At each level the window [p - eps, p + eps] replaces the sample range
 // of the sampled select: L1 scan, L2 binary search and word scan run inside
@@ -35,28 +42,53 @@
 
 namespace wt {
 
-struct Knots {
+struct Seg {
     uint64_t k0, k1, x0, x1;
 };
 
-__device__ __forceinline__ Knots seg_knots(const LevelDesc& lv, uint32_t b, uint64_t m, uint32_t kl) {
+// anchor segment m of (level, b); kl = log2 K
+__device__ __forceinline__ Seg anchor_seg(const LevelDesc& lv, uint32_t b, uint64_t m, uint32_t kl) {
     const uint64_t* S = b ? lv.s1 : lv.s0;
     const uint64_t total = b ? lv.ones : lv.size - lv.ones;
-    Knots kn;
-    kn.k0 = m << kl;
-    kn.x0 = __ldg(S + m);
-    if (((m + 1) << kl) <= total) {
-        kn.k1 = (m + 1) << kl;
-        kn.x1 = __ldg(S + m + 1);
+    const uint32_t ka = kl + kAnchorLog2;
+    Seg g;
+    g.k0 = m << ka;
+    g.x0 = __ldg(S + (m << kAnchorLog2));
+    if (((m + 1) << ka) <= total) {
+        g.k1 = (m + 1) << ka;
+        g.x1 = __ldg(S + ((m + 1) << kAnchorLog2));
     } else {
-        kn.k1 = total + 1;
-        kn.x1 = lv.size;
+        g.k1 = total + 1;
+        g.x1 = lv.size;
     }
-    return kn;
+    return g;
 }
 
-__device__ __forceinline__ uint64_t predict_pla(const Knots& kn, uint64_t k) {
-    return kn.x0 + ((k - kn.k0) * (kn.x1 - kn.x0)) / (kn.k1 - kn.k0);
+__device__ __forceinline__ uint64_t knot_rank(const Seg& g, uint32_t t) { return g.k0 + ((t * (g.k1 - g.k0)) >> 2); }
+
+// untrained knot position t: t quarters of the way from x0 to x1
+__device__ __forceinline__ uint64_t knot_base(const Seg& g, uint32_t t) { return g.x0 + ((t * (g.x1 - g.x0)) >> 2); }
+
+// xa + trunc((k - ka) * ((xb - xa) / (kb - ka))) in correctly rounded FP32, at most xb - xa
+__device__ __forceinline__ uint64_t interp(uint64_t ka, uint64_t kb, uint64_t xa, uint64_t xb, uint64_t k) {
+    const float slope = __fdiv_rn((float)(xb - xa), (float)(kb - ka));
+    const uint64_t off = (uint64_t)__fmul_rn((float)(k - ka), slope);
+    return xa + (off < xb - xa ? off : xb - xa);
+}
+
+// Fitted-knot prediction for rank k of segment g; R[t - 1] (bits) for knots t = 1..3.
+// Knot positions are non-decreasing and inside [x0, x1] (the fit guarantees it).
+// No integer division: the knots are quarters of the segment, the
+// interpolation between two knots is two FP32 operations.
+__device__ __forceinline__ uint64_t predict_knots(const Seg& g, const int64_t R[kKnots], uint64_t k) {
+    if (g.k1 - g.k0 < 4) return interp(g.k0, g.k1, g.x0, g.x1, k);
+    const uint64_t k1r = knot_rank(g, 1), k2r = knot_rank(g, 2), k3r = knot_rank(g, 3);
+    const uint32_t t = (k >= k1r) + (k >= k2r) + (k >= k3r);
+    const uint64_t ka = t == 0 ? g.k0 : (t == 1 ? k1r : (t == 2 ? k2r : k3r));
+    const uint64_t kb = t == 0 ? k1r : (t == 1 ? k2r : (t == 2 ? k3r : g.k1));
+    const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)knot_base(g, t) + R[t - 1]);
+    const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)knot_base(g, t + 1) + R[t]);
+    return interp(ka, kb, xa, xb, k);
 }
 
 // g(u) = b2 + sum_j w2[j] * relu(w1[j] * u + b1[j]); P = {w1[32], b1[32], w2[32], b2}
@@ -70,17 +102,188 @@ __device__ __forceinline__ float mlp_g(const float* P, float u) {
     return y;
 }
 
-__device__ __forceinline__ uint64_t predict_mlp(const Knots& kn, uint64_t k, const float* P) {
-    const float u = __fdiv_rn((float)(k - kn.k0), (float)(kn.k1 - kn.k0));
+__device__ __forceinline__ uint64_t predict_mlp(const Seg& g, uint64_t k, const float* P) {
+    const float u = __fdiv_rn((float)(k - g.k0), (float)(g.k1 - g.k0));
     float h = __fadd_rn(u, mlp_g(P, u));
     h = fminf(fmaxf(h, 0.f), 1.f);
-    const uint64_t span = kn.x1 - kn.x0;
+    const uint64_t span = g.x1 - g.x0;
     uint64_t off = (uint64_t)__fmul_rn((float)span, h);
-    return kn.x0 + (off < span ? off : span);
+    return g.x0 + (off < span ? off : span);
 }
 
-__device__ __forceinline__ uint64_t predict(uint32_t mode, const Knots& kn, uint64_t k, const float* P) {
-    return mode == kLearnMlp ? predict_mlp(kn, k, P) : predict_pla(kn, k);
+__device__ __forceinline__ void unpack_resid(const ushort4 r, uint32_t rsh, int64_t R[kKnots]) {
+    R[0] = (int64_t)(int16_t)r.x * (int64_t(1) << rsh);
+    R[1] = (int64_t)(int16_t)r.y * (int64_t(1) << rsh);
+    R[2] = (int64_t)(int16_t)r.z * (int64_t(1) << rsh);
+}
+
+__device__ __forceinline__ uint64_t predict(uint32_t mode, const Seg& g, const int64_t R[kKnots], uint64_t k,
+                                            const float* P) {
+    return mode == kLearnMlp ? predict_mlp(g, k, P) : predict_knots(g, R, k);
+}
+
+// ---------------------------------------------------------------------------
+// fit: least-squares knot residuals, one warp per anchor segment
+// ---------------------------------------------------------------------------
+
+struct FitArgs {
+    LevelDesc lv;
+    uint32_t b, kl;
+    uint64_t nseg;
+    float* resid;             // [nseg][3], bits
+    unsigned int* maxabs;     // float bits of the largest |residual| of the (level, b)
+};
+
+// The warp walks the segment's words 32 at a time; each lane enumerates the
+// b-bits of its word with their ranks and accumulates the normal equations of
+// the hat-function basis: knot t's function is 1 at kappa_t and falls
+// linearly to 0 at the neighbouring knots, so a rank touches at most two.
+__global__ void __launch_bounds__(256) fit_knots_kernel(const __grid_constant__ FitArgs a) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t m = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (m >= a.nseg) return;
+    const LevelDesc& lv = a.lv;
+    const Seg g = anchor_seg(lv, a.b, m, a.kl);
+    const uint64_t span = g.k1 - g.k0;
+    float* out = a.resid + 3 * m;
+    if (span < 4 || g.x1 <= g.x0) {
+        if (lane < 3) out[lane] = 0.f;
+        return;
+    }
+    uint64_t kap[5];
+#pragma unroll
+    for (uint32_t t = 0; t < 5; t++) kap[t] = t == 4 ? g.k1 : knot_rank(g, t);
+    // rank of the first b-bit at or after x0: k0 for m >= 1 (the anchor itself), 1 for m = 0
+    uint64_t rank = m ? g.k0 : 1;
+    float s00 = 0, s11 = 0, s22 = 0, s01 = 0, s12 = 0, y0 = 0, y1 = 0, y2 = 0;
+    const uint64_t w0 = g.x0 >> 6, w1 = (g.x1 - 1) >> 6;
+    for (uint64_t wb = w0; wb <= w1; wb += 32) {
+        const uint64_t w = wb + lane;
+        uint64_t x = 0;
+        if (w <= w1) {
+            x = __ldg(lv.words + w);
+            if (!a.b) x = ~x;
+            if (w == w0) x &= ~0ull << (g.x0 & 63);
+            const uint64_t end = g.x1 < lv.size ? g.x1 : lv.size;  // positions in [x0, min(x1, size))
+            if ((w << 6) + 64 > end) {
+                const uint64_t keep = end > (w << 6) ? end - (w << 6) : 0;
+                x &= keep >= 64 ? ~0ull : ((1ull << keep) - 1ull);
+            }
+        }
+        const uint32_t c = __popcll(x);
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (uint32_t)o) inc += v;
+        }
+        uint64_t k = rank + (inc - c);
+        rank += __shfl_sync(0xffffffffu, inc, 31);
+        while (x) {
+            const uint32_t i = __ffsll((long long)x) - 1;
+            x &= x - 1;
+            if (k >= g.k1) break;
+            const uint64_t pos = (w << 6) + i;
+            const uint32_t t = (k >= kap[1]) + (k >= kap[2]) + (k >= kap[3]);
+            const float u = (float)(k - kap[t]) / (float)(kap[t + 1] - kap[t]);
+            // distance of the position from the untrained model (the knots at quarters of the segment)
+            const float xa = (float)(knot_base(g, t) - g.x0), xb = (float)(knot_base(g, t + 1) - g.x0);
+            const float d = (float)(pos - g.x0) - (xa + u * (xb - xa));
+            const float pa = 1.f - u, pb = u;  // weights of knots t and t + 1
+            // knot indices 1..3 map to unknowns 0..2; knots 0 and 4 are the fixed anchors
+            if (t == 0) {
+                s00 += pb * pb;
+                y0 += pb * d;
+            } else if (t == 1) {
+                s00 += pa * pa;
+                s11 += pb * pb;
+                s01 += pa * pb;
+                y0 += pa * d;
+                y1 += pb * d;
+            } else if (t == 2) {
+                s11 += pa * pa;
+                s22 += pb * pb;
+                s12 += pa * pb;
+                y1 += pa * d;
+                y2 += pb * d;
+            } else {
+                s22 += pa * pa;
+                y2 += pa * d;
+            }
+            k++;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s00 += __shfl_xor_sync(0xffffffffu, s00, o);
+        s11 += __shfl_xor_sync(0xffffffffu, s11, o);
+        s22 += __shfl_xor_sync(0xffffffffu, s22, o);
+        s01 += __shfl_xor_sync(0xffffffffu, s01, o);
+        s12 += __shfl_xor_sync(0xffffffffu, s12, o);
+        y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+        y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+    }
+    if (lane == 0) {
+        // tridiagonal 3x3 solve in FP64 (Thomas); an unknown without data stays 0
+        double r[3] = {0, 0, 0};
+        const double d0 = s00, d1 = s11, d2 = s22, e01 = s01, e12 = s12;
+        const double det = d0 * (d1 * d2 - e12 * e12) - e01 * (e01 * d2);
+        if (fabs(det) > 1e-9 * (fabs(d0 * d1 * d2) + 1e-30)) {  // Cramer's rule
+            const double c0 = y0, c1 = y1, c2 = y2;
+            r[0] = (c0 * (d1 * d2 - e12 * e12) - e01 * (c1 * d2 - e12 * c2)) / det;
+            r[1] = (d0 * (c1 * d2 - e12 * c2) - c0 * e01 * d2) / det;
+            r[2] = (d0 * (d1 * c2 - c1 * e12) - e01 * e01 * c2 + c0 * e01 * e12) / det;
+        }
+        float mx = 0.f;
+        for (int t = 0; t < 3; t++) {
+            const float v = isfinite(r[t]) ? (float)r[t] : 0.f;
+            out[t] = v;
+            mx = fmaxf(mx, fabsf(v));
+        }
+        atomicMax(a.maxabs, __float_as_uint(mx));
+    }
+}
+
+__device__ __forceinline__ uint32_t shift_for(float maxv, float lim) {
+    uint32_t sh = 0;
+    while (sh < 30 && maxv > lim * (float)(1u << sh)) sh++;
+    return sh;
+}
+
+// Residuals to int16 units of 2^rsh bits, with the knots kept non-decreasing
+// and inside [x0, x1]; a segment where that fails keeps the line (R = 0).
+__global__ void __launch_bounds__(256) quantize_knots_kernel(const __grid_constant__ FitArgs a, ushort4* rec,
+                                                             const unsigned int* maxabs) {
+    const uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.nseg) return;
+    const uint32_t rsh = shift_for(__uint_as_float(*maxabs), 32767.f);
+    const Seg g = anchor_seg(a.lv, a.b, m, a.kl);
+    int32_t q[3] = {0, 0, 0};
+    if (g.k1 - g.k0 >= 4) {
+        int64_t prev = (int64_t)g.x0;
+        bool ok = true;
+        for (uint32_t t = 1; t <= 3; t++) {
+            const int64_t base = (int64_t)knot_base(g, t);
+            const float r = a.resid[3 * m + t - 1];
+            int64_t v = (int64_t)llrintf(r / (float)(1u << rsh));
+            v = v > 32767 ? 32767 : (v < -32767 ? -32767 : v);
+            int64_t xi = base + v * (int64_t(1) << rsh);
+            if (xi < prev) {  // raise to the previous knot, in whole units
+                v = (prev - base + (int64_t(1) << rsh) - 1) >> rsh;
+                xi = base + v * (int64_t(1) << rsh);
+            }
+            if (xi > (int64_t)g.x1) {
+                v = ((int64_t)g.x1 - base) >> rsh;
+                xi = base + v * (int64_t(1) << rsh);
+            }
+            if (xi < prev || xi > (int64_t)g.x1 || v > 32767 || v < -32767) ok = false;
+            q[t - 1] = (int32_t)v;
+            prev = xi;
+        }
+        if (!ok) q[0] = q[1] = q[2] = 0;
+    }
+    rec[m] = make_ushort4((uint16_t)(int16_t)q[0], (uint16_t)(int16_t)q[1], (uint16_t)(int16_t)q[2], 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -92,7 +295,10 @@ struct ScanArgs {
     uint32_t kl;
     uint32_t mode;
     const float* P[2];        // model parameters per b (mode kLearnMlp)
-    uint32_t* eps[2];         // zeroed before the scan; null = do not record bounds
+    const ushort4* rec[2];    // knot residuals per b (mode kLearnPla)
+    uint32_t rsh[2];
+    uint32_t* eps[2];         // per segment, zeroed before the scan; null = do not record bounds
+    unsigned int* epsmax;     // [2] largest bound of the level per b
     float2* pairs[2];         // training pairs (u, t) per b; null = do not record pairs
     uint32_t* npairs;         // [2]
     uint64_t stride[2];       // record the pair of every stride-th b-bit
@@ -102,16 +308,19 @@ struct ScanArgs {
 __global__ void __launch_bounds__(256) learn_scan_kernel(const __grid_constant__ ScanArgs a) {
     const LevelDesc& lv = a.lv;
     const uint64_t nblk = (lv.size + 511) / 512;
+    const uint32_t ka = a.kl + kAnchorLog2;
     for (uint64_t blk = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; blk < nblk;
          blk += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t pos0 = blk << 9;
         const uint64_t ones_before = __ldg(lv.l1 + (pos0 >> 16)) + __ldg(lv.l2 + blk);
 #pragma unroll 1
         for (uint32_t b = 0; b < 2; b++) {
+            if (!a.eps[b] && !a.pairs[b]) continue;
             uint64_t r = b ? ones_before : pos0 - ones_before;  // b-bits before the block
             uint64_t cur_m = ~0ull;
             uint32_t cur_max = 0;
-            Knots kn = {0, 1, 0, 0};
+            Seg g = {0, 1, 0, 0};
+            int64_t R[kKnots] = {0, 0, 0};
             const float* P = a.P[b];
 #pragma unroll 1
             for (uint32_t w = 0; w < 8; w++) {
@@ -126,32 +335,52 @@ __global__ void __launch_bounds__(256) learn_scan_kernel(const __grid_constant__
                     x &= x - 1;
                     const uint64_t k = ++r;
                     const uint64_t pos = p + i;
-                    const uint64_t m = k >> a.kl;
+                    const uint64_t m = k >> ka;
                     if (m != cur_m) {
-                        if (a.eps[b] && cur_m != ~0ull && cur_max) atomicMax(a.eps[b] + cur_m, cur_max);
+                        if (a.eps[b] && cur_m != ~0ull && cur_max) {
+                            atomicMax(a.eps[b] + cur_m, cur_max);
+                            atomicMax(a.epsmax + b, cur_max);
+                        }
                         cur_m = m;
                         cur_max = 0;
-                        kn = seg_knots(lv, b, m, a.kl);
+                        g = anchor_seg(lv, b, m, a.kl);
+                        if (a.mode == kLearnPla && a.rec[b]) unpack_resid(a.rec[b][m], a.rsh[b], R);
                     }
                     if (a.eps[b]) {
-                        const uint64_t pr = predict(a.mode, kn, k, P);
+                        const uint64_t pr = predict(a.mode, g, R, k, P);
                         const uint64_t e = pr > pos ? pr - pos : pos - pr;
                         const uint32_t e32 = e > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)e;
                         cur_max = e32 > cur_max ? e32 : cur_max;
                     }
-                    if (a.pairs[b] && (k % a.stride[b]) == 0 && k != kn.k0) {
+                    if (a.pairs[b] && (k % a.stride[b]) == 0 && k != g.k0) {
                         const uint32_t idx = atomicAdd(a.npairs + b, 1u);
                         if (idx < a.cap) {
-                            const float u = (float)(k - kn.k0) / (float)(kn.k1 - kn.k0);
-                            const float t = (float)((double)(pos - kn.x0) / (double)(kn.x1 - kn.x0));
+                            const float u = (float)(k - g.k0) / (float)(g.k1 - g.k0);
+                            const float t = (float)((double)(pos - g.x0) / (double)(g.x1 - g.x0));
                             a.pairs[b][idx] = make_float2(u, t);
                         }
                     }
                 }
             }
-            if (a.eps[b] && cur_m != ~0ull && cur_max) atomicMax(a.eps[b] + cur_m, cur_max);
+            if (a.eps[b] && cur_m != ~0ull && cur_max) {
+                atomicMax(a.eps[b] + cur_m, cur_max);
+                atomicMax(a.epsmax + b, cur_max);
+            }
         }
     }
+}
+
+// Bounds into the records: uint16 units of 2^esh bits, rounded up.
+__global__ void __launch_bounds__(256) store_bounds_kernel(ushort4* rec, const uint32_t* eps, uint64_t nseg,
+                                                           const unsigned int* epsmax) {
+    const uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nseg) return;
+    uint32_t esh = 0;
+    while (esh < 31 && ((uint64_t)*epsmax + (1ull << esh) - 1) >> esh > 65535) esh++;
+    const uint64_t q = ((uint64_t)eps[m] + (1ull << esh) - 1) >> esh;
+    ushort4 r = rec[m];
+    r.w = (uint16_t)q;
+    rec[m] = r;
 }
 
 // ---------------------------------------------------------------------------
@@ -321,10 +550,13 @@ __device__ __forceinline__ uint64_t select_b_window(const LevelDesc& lv, uint32_
 __device__ __forceinline__ uint64_t select_b_learned(const TreeDesc& t, const LearnedDesc& ld, const float* mlp_s,
                                                      uint32_t l, uint32_t b, uint64_t k, uint32_t& fb) {
     const LevelDesc& lv = t.lv[l];
-    const uint64_t m = k >> t.k_log2;
-    const Knots kn = seg_knots(lv, b, m, t.k_log2);
-    const uint64_t p = predict(ld.mode, kn, k, mlp_s + (2 * l + b) * kMlpParams);
-    const uint64_t e = __ldg(ld.eps[l][b] + m);
+    const uint64_t m = k >> (t.k_log2 + kAnchorLog2);
+    const Seg g = anchor_seg(lv, b, m, t.k_log2);
+    const ushort4 r = ld.rec[l][b][m];
+    int64_t R[kKnots];
+    unpack_resid(r, ld.rsh[l][b], R);
+    const uint64_t p = predict(ld.mode, g, R, k, mlp_s + (2 * l + b) * kMlpParams);
+    const uint64_t e = (uint64_t)r.w << ld.esh[l][b];
     const uint64_t lo = p > e ? p - e : 0;
     const uint64_t hi = umin64(p + e, lv.size - 1);
     bool ok = true;
@@ -399,58 +631,106 @@ void free_learned(wt_tree_s* t, cudaStream_t s) {
     memset(&t->learned, 0, sizeof(t->learned));
 }
 
+static uint64_t anchor_segments(const wt_tree_s* t, uint32_t l, uint32_t b) {
+    const uint64_t cnt = b ? t->level_ones[l] : t->level_size[l] - t->level_ones[l];
+    return (cnt >> (t->desc.k_log2 + kAnchorLog2)) + 1;
+}
+
+// mode kLearnPla: fit the knots (fit_knots_kernel, quantize_knots_kernel);
+// mode kLearnMlp: training pairs from the levels, then Adam.  Both: the bound
+// scan over every bit and the bounds into the records.
 wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, uint32_t pairs_cap, cudaStream_t s) {
     const uint32_t L = t->desc.cp.L, kl = t->desc.k_log2;
     free_learned(t, s);
     if (mode == kLearnNone || L == 0) return WT_OK;
-    // layout: fallback counter | MLP params | eps arrays
-    std::vector<size_t> eoff(2 * L);
+    const wt_allocator* A = tree_alloc(t);
+    // model memory: fallback counter | MLP params | records per (level, b)
+    std::vector<size_t> roff(2 * L);
     size_t off = 256 + ((2 * L * kMlpParams * 4 + 255) / 256) * 256;
-    for (uint32_t l = 0; l < L; l++) {
+    uint64_t max_seg = 1;
+    for (uint32_t l = 0; l < L; l++)
         for (uint32_t b = 0; b < 2; b++) {
-            const uint64_t cnt = b ? t->level_ones[l] : t->level_size[l] - t->level_ones[l];
-            eoff[2 * l + b] = off;
-            off += (((cnt >> kl) + 1) * 4 + 255) / 256 * 256;
+            roff[2 * l + b] = off;
+            const uint64_t ns = anchor_segments(t, l, b);
+            off += (ns * sizeof(ushort4) + 255) / 256 * 256;
+            max_seg = ns > max_seg ? ns : max_seg;
         }
-    }
     void* mem = nullptr;
-    if (dev_alloc(&mem, off, s, tree_alloc(t)) != cudaSuccess) return WT_ENOMEM;
+    if (dev_alloc(&mem, off, s, A) != cudaSuccess) return WT_ENOMEM;
     t->learned_mem = mem;
     t->learned_bytes = off;
     uint8_t* M = static_cast<uint8_t*>(mem);
-    WT_CUDA_TRY(cudaMemsetAsync(mem, 0, off, s));
     LearnedDesc& ld = t->learned;
     ld.mode = mode;
     ld.fallbacks = reinterpret_cast<unsigned long long*>(M);
     float* mlp = reinterpret_cast<float*>(M + 256);
     ld.mlp = mlp;
     for (uint32_t l = 0; l < L; l++)
-        for (uint32_t b = 0; b < 2; b++) ld.eps[l][b] = reinterpret_cast<uint32_t*>(M + eoff[2 * l + b]);
-
-    const int grid = sm_count() * 8;
+        for (uint32_t b = 0; b < 2; b++) ld.rec[l][b] = reinterpret_cast<const ushort4*>(M + roff[2 * l + b]);
+    // scratch: per (level, b) maxima | residuals of the largest segment count | bounds | training pairs
+    const size_t sc_max = 256, sc_res = sc_max + ((size_t)4 * L * 4 + 255) / 256 * 256;
+    const size_t sc_eps = sc_res + (max_seg * 3 * 4 + 255) / 256 * 256;
+    const size_t sc_pairs = sc_eps + (2 * max_seg * 4 + 255) / 256 * 256;
+    const size_t sc_end = sc_pairs + (mode == kLearnMlp ? (size_t)2 * L * pairs_cap * sizeof(float2) + 2 * L * 4 : 0);
+    void* scratch = nullptr;
+    if (dev_alloc(&scratch, sc_end, s, A) != cudaSuccess) {
+        free_learned(t, s);  // no half-trained model stays behind
+        return WT_ENOMEM;
+    }
+    uint8_t* X = static_cast<uint8_t*>(scratch);
+    unsigned int* maxabs = reinterpret_cast<unsigned int*>(X + sc_max);      // [L][2]
+    unsigned int* epsmax = maxabs + 2 * L;                                    // [L][2]
+    float* resid = reinterpret_cast<float*>(X + sc_res);
+    uint32_t* eps = reinterpret_cast<uint32_t*>(X + sc_eps);
+    wt_status st = WT_OK;
+    auto fail = [&](wt_status e) {
+        dev_free(scratch, s, A);
+        free_learned(t, s);
+        return e;
+    };
+    if (cudaMemsetAsync(mem, 0, off, s) != cudaSuccess || cudaMemsetAsync(scratch, 0, sc_res, s) != cudaSuccess)
+        return fail(WT_ECUDA);
     std::vector<float> hp(2 * L * kMlpParams);
     for (uint32_t i = 0; i < 2 * L; i++) init_mlp(hp.data() + i * kMlpParams);
-    WT_CUDA_TRY(cudaMemcpyAsync(mlp, hp.data(), hp.size() * 4, cudaMemcpyHostToDevice, s));
-    WT_CUDA_TRY(cudaStreamSynchronize(s));  // hp is a host temporary
+    if (cudaMemcpyAsync(mlp, hp.data(), hp.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)  // hp is a host temporary
+        return fail(WT_ECUDA);
+    const int grid = sm_count() * 8;
 
-    if (mode == kLearnMlp) {
-        // training pairs from the built levels, then Adam on every model at once
-        void* scratch = nullptr;
-        const size_t pbytes = (size_t)2 * L * pairs_cap * sizeof(float2);
-        if (dev_alloc(&scratch, pbytes + 2 * L * 4 + 256, s, tree_alloc(t)) != cudaSuccess) {
-            free_learned(t, s);  // no half-trained model stays behind
-            return WT_ENOMEM;
+    if (mode == kLearnPla) {
+        for (uint32_t l = 0; l < L && st == WT_OK; l++) {
+            if (!t->level_size[l]) continue;
+            for (uint32_t b = 0; b < 2; b++) {
+                FitArgs fa;
+                fa.lv = t->desc.lv[l];
+                fa.b = b;
+                fa.kl = kl;
+                fa.nseg = anchor_segments(t, l, b);
+                fa.resid = resid;
+                fa.maxabs = maxabs + 2 * l + b;
+                {
+                    ProfScope ps("learn_fit", s);
+                    fit_knots_kernel<<<(unsigned)((fa.nseg * 32 + 255) / 256), 256, 0, s>>>(fa);
+                }
+                {
+                    ProfScope ps("learn_quantize", s);
+                    quantize_knots_kernel<<<(unsigned)((fa.nseg + 255) / 256), 256, 0, s>>>(
+                        fa, const_cast<ushort4*>(ld.rec[l][b]), fa.maxabs);
+                }
+            }
         }
-        float2* pairs = static_cast<float2*>(scratch);
-        uint32_t* npairs = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(scratch) + pbytes);
-        WT_CUDA_TRY(cudaMemsetAsync(npairs, 0, 2 * L * 4, s));
+    } else {
+        // training pairs from the built levels, then Adam on every model at once
+        float2* pairs = reinterpret_cast<float2*>(X + sc_pairs);
+        uint32_t* npairs = reinterpret_cast<uint32_t*>(X + sc_pairs + (size_t)2 * L * pairs_cap * sizeof(float2));
+        if (cudaMemsetAsync(npairs, 0, 2 * L * 4, s) != cudaSuccess) return fail(WT_ECUDA);
         for (uint32_t l = 0; l < L; l++) {
             if (!t->level_size[l]) continue;
             ScanArgs a;
             memset(&a, 0, sizeof(a));
             a.lv = t->desc.lv[l];
             a.kl = kl;
-            a.mode = kLearnPla;
+            a.mode = kLearnMlp;
             a.cap = pairs_cap;
             a.npairs = npairs + 2 * l;
             for (uint32_t b = 0; b < 2; b++) {
@@ -461,33 +741,66 @@ wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, ui
             ProfScope ps("learn_pairs", s);
             learn_scan_kernel<<<grid, 256, 0, s>>>(a);
         }
-        {
-            const size_t sm = (size_t)pairs_cap * sizeof(float2);
-            static bool cfg = false;
-            if (!cfg) {
-                cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-                cfg = true;
-            }
-            ProfScope ps("mlp_train", s);
-            mlp_train_kernel<<<2 * L, kTrainThreads, sm, s>>>(pairs, npairs, pairs_cap, mlp, steps, lr, nullptr);
+        const size_t sm = (size_t)pairs_cap * sizeof(float2);
+        static bool cfg = false;
+        if (!cfg) {
+            cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            cfg = true;
         }
-        dev_free(scratch, s, tree_alloc(t));
+        ProfScope ps("mlp_train", s);
+        mlp_train_kernel<<<2 * L, kTrainThreads, sm, s>>>(pairs, npairs, pairs_cap, mlp, steps, lr, nullptr);
     }
+    std::vector<unsigned int> hmax(4 * L, 0);
+    if (cudaMemcpyAsync(hmax.data(), maxabs, 2 * L * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(WT_ECUDA);
+    for (uint32_t l = 0; l < L; l++)
+        for (uint32_t b = 0; b < 2; b++) {
+            float mx;
+            memcpy(&mx, &hmax[2 * l + b], 4);
+            uint32_t sh = 0;
+            while (sh < 30 && mx > 32767.f * (float)(1u << sh)) sh++;
+            ld.rsh[l][b] = (uint8_t)(mode == kLearnPla ? sh : 0);
+        }
+    // bounds: one scan per level over both bit values, then into the records
     for (uint32_t l = 0; l < L; l++) {
         if (!t->level_size[l]) continue;
+        const uint64_t ns[2] = {anchor_segments(t, l, 0), anchor_segments(t, l, 1)};
+        if (cudaMemsetAsync(eps, 0, (ns[0] + ns[1]) * 4, s) != cudaSuccess) return fail(WT_ECUDA);
         ScanArgs a;
         memset(&a, 0, sizeof(a));
         a.lv = t->desc.lv[l];
         a.kl = kl;
         a.mode = mode;
+        a.epsmax = epsmax + 2 * l;
         for (uint32_t b = 0; b < 2; b++) {
             a.P[b] = mlp + (2 * l + b) * kMlpParams;
-            a.eps[b] = const_cast<uint32_t*>(ld.eps[l][b]);
+            a.rec[b] = ld.rec[l][b];
+            a.rsh[b] = ld.rsh[l][b];
+            a.eps[b] = eps + (b ? ns[0] : 0);
             a.stride[b] = 1;
         }
-        ProfScope ps("learn_bounds", s);
-        learn_scan_kernel<<<grid, 256, 0, s>>>(a);
+        {
+            ProfScope ps("learn_bounds", s);
+            learn_scan_kernel<<<grid, 256, 0, s>>>(a);
+        }
+        for (uint32_t b = 0; b < 2; b++) {
+            ProfScope ps("learn_store", s);
+            store_bounds_kernel<<<(unsigned)((ns[b] + 255) / 256), 256, 0, s>>>(const_cast<ushort4*>(ld.rec[l][b]),
+                                                                                a.eps[b], ns[b], epsmax + 2 * l + b);
+        }
     }
+    std::vector<unsigned int> hemax(2 * L, 0);
+    if (cudaMemcpyAsync(hemax.data(), epsmax, 2 * L * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(WT_ECUDA);
+    for (uint32_t l = 0; l < L; l++)
+        for (uint32_t b = 0; b < 2; b++) {
+            uint32_t esh = 0;
+            while (esh < 31 && (((uint64_t)hemax[2 * l + b] + (1ull << esh) - 1) >> esh) > 65535) esh++;
+            ld.esh[l][b] = (uint8_t)esh;
+        }
+    dev_free(scratch, s, A);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
@@ -528,6 +841,33 @@ static bool tree_valid(const wt_tree_s* t) { return t && t->magic == kTreeMagic;
 
 static bool dev_ptr(const void* p) { return device_ptr_ok(p); }
 
+namespace wt {
+// wt_export of the learned model: per anchor segment the bound (uint32 bits)
+// or the three knot residuals (int32 bits).  Synchronous.
+wt_status export_learned(const wt_tree_s* t, uint32_t level, uint32_t b, bool resid, void* h_dst, uint64_t* count) {
+    const uint64_t segs = anchor_segments(t, level, b);
+    *count = resid ? 3 * segs : segs;
+    if (!h_dst) return WT_OK;
+    std::vector<ushort4> r(segs);
+    if (cudaStreamSynchronize(t->stream) != cudaSuccess ||
+        cudaMemcpy(r.data(), t->learned.rec[level][b], segs * sizeof(ushort4), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return WT_ECUDA;
+    for (uint64_t m = 0; m < segs; m++) {
+        if (resid) {
+            int32_t* o = static_cast<int32_t*>(h_dst) + 3 * m;
+            const uint32_t sh = t->learned.rsh[level][b];
+            o[0] = (int32_t)((int64_t)(int16_t)r[m].x * (int64_t(1) << sh));
+            o[1] = (int32_t)((int64_t)(int16_t)r[m].y * (int64_t(1) << sh));
+            o[2] = (int32_t)((int64_t)(int16_t)r[m].z * (int64_t(1) << sh));
+        } else {
+            const uint64_t e = (uint64_t)r[m].w << t->learned.esh[level][b];
+            static_cast<uint32_t*>(h_dst)[m] = (uint32_t)(e > 0xFFFFFFFFull ? 0xFFFFFFFFull : e);
+        }
+    }
+    return WT_OK;
+}
+}  // namespace wt
+
 extern "C" {
 
 wt_status wt_train_select(wt_tree tree, uint32_t mode, const wt_train_options* opt, wt_stream stream) {
@@ -559,23 +899,27 @@ wt_status wt_learned_info(wt_tree tree, wt_learned_info_t* out) {
     unsigned long long fb = 0;
     if (cudaMemcpy(&fb, ld.fallbacks, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return WT_ECUDA;
     out->fallbacks = fb;
-    const uint32_t L = tree->desc.cp.L, kl = tree->desc.k_log2;
+    const uint32_t L = tree->desc.cp.L;
+    uint64_t anchors = 0;
     for (uint32_t l = 0; l < L; l++) {
         for (uint32_t b = 0; b < 2; b++) {
-            const uint64_t cnt = b ? tree->level_ones[l] : tree->level_size[l] - tree->level_ones[l];
-            const uint64_t segs = (cnt >> kl) + 1;
-            std::vector<uint32_t> e(segs);
-            if (cudaMemcpy(e.data(), ld.eps[l][b], segs * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return WT_ECUDA;
+            const uint64_t segs = anchor_segments(tree, l, b);
+            anchors += segs * 8;
+            std::vector<ushort4> r(segs);
+            if (cudaMemcpy(r.data(), ld.rec[l][b], segs * sizeof(ushort4), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return WT_ECUDA;
             double sum = 0;
-            uint32_t mx = 0;
-            for (uint32_t v : e) {
-                sum += v;
-                mx = v > mx ? v : mx;
+            uint64_t mx = 0;
+            for (const ushort4& v : r) {
+                const uint64_t e = (uint64_t)v.w << ld.esh[l][b];
+                sum += (double)e;
+                mx = e > mx ? e : mx;
             }
             out->eps_mean[l][b] = segs ? sum / segs : 0.0;
-            out->eps_max[l][b] = mx;
+            out->eps_max[l][b] = (uint32_t)(mx > 0xFFFFFFFFull ? 0xFFFFFFFFull : mx);
         }
     }
+    out->anchor_bytes = anchors;
     out->model_bytes = tree->learned_bytes;
     return WT_OK;
 }

@@ -528,6 +528,66 @@ def test_mlp_predictor_within_fp32_bound_of_fp64_forward():
     assert u_max > 0.9
 
 
+def test_spline_predictor_by_hand_and_brute_force():
+    """The fitted-knot model's prediction: by hand on one segment, and the
+    array form against the scalar form over every rank of a random level."""
+    from oracle import mlp
+
+    # segment (k0, k1, x0, x1) = (0, 16, 0, 160): untrained knots at (0, 0), (4, 40), ..., (16, 160)
+    kn = (0, 16, 0, 160)
+    R = [5, -10, 0]  # knots at positions 0, 45, 70, 120, 160
+    kap, xi = mlp.spline_knots(kn, R)
+    assert kap == [0, 4, 8, 12, 16] and xi == [0, 45, 70, 120, 160]
+    assert mlp.predict_spline(kn, R, 2) == 22    # slope 45 / 4 = 11.25, 2 * 11.25 = 22.5 -> 22
+    assert mlp.predict_spline(kn, R, 4) == 45
+    assert mlp.predict_spline(kn, R, 6) == 57    # 45 + trunc(2 * 6.25)
+    assert mlp.predict_spline(kn, R, 13) == 130
+    assert mlp.predict_spline((0, 3, 10, 16), [99, 99, 99], 2) == 14  # short segment: the anchors only
+    # float32 steps: slope 1 / 3 rounds to 0.3333333432674408, and 3 * that rounds to 1.0 exactly
+    assert mlp.interp_f32(0, 3, 0, 1, 3) == 1
+    assert mlp.interp_f32(0, 3, 100, 101, 2) == 100  # 2 / 3 -> 0
+    # the offset is capped at the knot distance even when float32 rounds up
+    assert mlp.interp_f32(0, 1, 0, (1 << 25) - 1, 1) == (1 << 25) - 1
+    rng = np.random.default_rng(3)
+    bits = (rng.random(20000) < 0.3).astype(np.uint8)
+    pos = np.flatnonzero(bits)
+    K = 64
+    total, size = pos.size, bits.size
+    samples = np.concatenate([[0], pos[np.arange(K, total + 1, K) - 1]])
+    k, m, k0, k1, x0, x1 = mlp.segment_anchor_all(samples, total, size, K)
+    nseg = total // (mlp.ANCHOR * K) + 1
+    Rs = rng.integers(-3, 4, (nseg, 3))
+    pred = mlp.predict_spline_all(k, k0, k1, x0, x1, Rs[m])
+    for idx in list(range(0, total, 97)) + [total - 1]:
+        kn = mlp.anchor_knots(samples, total, size, int(m[idx]), K)
+        assert (int(k0[idx]), int(k1[idx]), int(x0[idx]), int(x1[idx])) == kn
+        assert int(pred[idx]) == mlp.predict_spline(kn, Rs[m[idx]], int(k[idx]))
+
+
+def test_spline_fit_is_the_least_squares_solution():
+    """fit_spline_lsq (normal equations on hat functions) against
+    numpy.linalg.lstsq on the explicit design matrix, and a noiseless
+    piecewise-linear curve through the knots is recovered exactly."""
+    from oracle import mlp
+
+    rng = np.random.default_rng(8)
+    kn = (1000, 1400, 50000, 58000)
+    ks = np.arange(1001, 1400)
+    pos = 50000 + (ks - 1000) * 20 + rng.normal(0, 40, ks.size).cumsum() * 0.1
+    R = mlp.fit_spline_lsq(kn, ks, pos)
+    kap = [1000 + t * 100 for t in range(5)]
+    X = np.zeros((ks.size, 3))
+    for t in (1, 2, 3):
+        X[:, t - 1] = np.clip(np.minimum((ks - kap[t - 1]) / 100.0, (kap[t + 1] - ks) / 100.0), 0, None)
+    base = 50000 + (ks - 1000) * 20.0
+    ref = np.linalg.lstsq(X, pos - base, rcond=None)[0]
+    assert np.allclose(R, ref, rtol=1e-9, atol=1e-6)
+    true = np.array([30.0, -55.0, 12.0])
+    knots_y = np.concatenate([[0.0], true, [0.0]])
+    exact = base + np.interp(ks, kap, knots_y)
+    assert np.allclose(mlp.fit_spline_lsq(kn, ks, exact), true, atol=1e-6)
+
+
 def test_bitvector_rank_select_by_brute_force():
     """The oracle's binary rank/select against one-position-at-a-time loops, plus
     the invariants rank_1(select_1(j)) = j - 1, B[select_b(j)] = b and
