@@ -363,8 +363,8 @@ typedef struct {
     uint32_t query_threads;
     const wt_allocator* allocator; /* NULL: cudaMalloc; else the batch's one allocation comes from it
                                       (allocated and released on the legacy default stream) */
-    uint32_t lp_ctas_per_sm;       /* CTAs per SM of the persistent batched level pass: 1, 2 or 3
-                                      (0: 3, the most that fit) */
+    uint32_t lp_ctas_per_sm;       /* CTAs per SM of the persistent batched level pass: 1 to 6
+                                      (0: 6, the most that fit) */
     uint32_t reserved[3];
 } wt_batch_options;
 

@@ -23,7 +23,12 @@
  *     plain cumulative popcount per 64-bit word, not on the L1/L2 blocks.  The
  *     L1/L2 counters, the select samples and the node-start ranks are produced
  *     by direct counting, only to be compared with the GPU's.  Queries follow
- *     Algorithms 5, 6, 7 and 8 with the corrections listed in the design notes.
+ *     Algorithms 5, 6, 7 and 8 read this way: the access loop runs over
+ *     l in [0, L), its "index" update means i, and a node of two symbols is
+ *     decided by one bit (no bit is read at a node of one symbol); the rank
+ *     walk stops at a node of one symbol (width <= 1, not <= 0); getNodeStart
+ *     encodes the start symbol passed in and "rightmost" means the first l code
+ *     bits are all ones; a level's bit is bit L-1-l of the left-aligned code.
  *
  * Parity status: every function here is pinned by tests/test_oracle_pins.py
  * (brute force on tiny inputs, the worked example of Section 5, closed forms

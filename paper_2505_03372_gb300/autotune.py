@@ -23,7 +23,7 @@ DEFAULT_CACHE = os.environ.get("WT_TUNE_CACHE", os.path.join(os.path.dirname(os.
                                                              ".tune_cache.json"))
 SAMPLE_K = (2048, 4096, 8192)
 QUERY_THREADS = (128, 256, 512)
-LP_CTAS = (1, 2, 3)
+LP_CTAS = (2, 4, 6)
 
 
 def stage1_candidates():

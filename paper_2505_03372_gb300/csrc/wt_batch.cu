@@ -158,8 +158,8 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
     const uint32_t qthreads = (opt && opt->query_threads) ? opt->query_threads : 256u;
     const wt_allocator* alloc = opt ? opt->allocator : nullptr;
     if (alloc && (!alloc->alloc || !alloc->free)) return WT_EINVAL;
-    const uint32_t lp_ctas = (opt && opt->lp_ctas_per_sm) ? opt->lp_ctas_per_sm : 3u;
-    if (lp_ctas > 3) return WT_EINVAL;
+    const uint32_t lp_ctas = (opt && opt->lp_ctas_per_sm) ? opt->lp_ctas_per_sm : 6u;
+    if (lp_ctas > 6) return WT_EINVAL;
     if (qthreads != 128 && qthreads != 256 && qthreads != 512) return WT_EINVAL;
     for (uint32_t i = 0; i < ntrees; i++) {
         const uint32_t sg = h_sigma[i];

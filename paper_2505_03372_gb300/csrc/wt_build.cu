@@ -4,7 +4,7 @@
 // Pipeline (all on the device, one stream):
 //   1. histogram of S with symbol validation (Section 5.1.1: shared-memory
 //      sub-histograms, persistent grid), which also counts the level-0 ones of
-//      every 32 KiB tile;
+//      every 16 KiB tile;
 //   2. C = exclusive prefix sum of the histogram;
 //   3. node table: for every node (depth l, code prefix p) its start C[a],
 //      the precomputed rank_0 at the start (Section 5.2.1) and the two
@@ -103,11 +103,17 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
+// Tiles of the level passes: 16 KiB of T_l each (1024 16-byte vectors); the
+// histogram counts the level-0 ones of every such tile.
+constexpr int kTileBytesHist = 16384;
+constexpr uint32_t kTileVecLog2 = 10;
+static_assert((16u << kTileVecLog2) == (uint32_t)kTileBytesHist, "tile size");
+
 // ===========================================================================
 // 1. histogram + validation
 // ===========================================================================
 
-// Also counts, per tile of 32 KB of S, the symbols whose level-0 bit is 1 (the
+// Also counts, per 16 KiB tile of S, the symbols whose level-0 bit is 1 (the
 // symbols >= m0, as codes grow with the symbol), so that the level-0 pass knows
 // every tile's prefix of ones (tcnt zeroed; null: not counted).
 template <typename T>
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
                                                    uint32_t cstride, uint32_t copies,
                                                    unsigned long long* __restrict__ hist, uint32_t* __restrict__ status,
                                                    uint32_t m0, unsigned long long* __restrict__ tcnt) {
-    constexpr uint32_t TE = 32768 / sizeof(T);  // elements per tile; a tile is 2048 16-byte vectors
+    constexpr uint32_t TE = kTileBytesHist / sizeof(T);  // elements per tile; a tile is 1024 16-byte vectors
     extern __shared__ uint32_t sh[];
     if constexpr (sizeof(T) == 1) {
         // Bytes: all 256 bins, one copy per lane, bin-major (copy k of bin b at
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
                 }
                 const uint32_t am = __activemask();
                 c = __reduce_add_sync(am, c);
-                if ((threadIdx.x & 31) == (uint32_t)(__ffs(am) - 1) && c) atomicAdd(tcnt + (v >> 11), (unsigned long long)c);
+                if ((threadIdx.x & 31) == (uint32_t)(__ffs(am) - 1) && c) atomicAdd(tcnt + (v >> kTileVecLog2), (unsigned long long)c);
             }
         }
         for (uint64_t j = nvec * 16 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(512) hist_kernel(const T* __restrict__ S, uint
         if (tcnt != nullptr) {
             const uint32_t am = __activemask();
             c = __reduce_add_sync(am, c);
-            if ((threadIdx.x & 31) == (uint32_t)(__ffs(am) - 1) && c) atomicAdd(tcnt + (v >> 11), (unsigned long long)c);
+            if ((threadIdx.x & 31) == (uint32_t)(__ffs(am) - 1) && c) atomicAdd(tcnt + (v >> kTileVecLog2), (unsigned long long)c);
         }
     }
     for (uint64_t j = nvec * V + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
@@ -380,9 +386,9 @@ __global__ void meta_kernel(const MetaArgs ma, uint32_t L, const uint64_t* __res
 // 4. the fused level pass
 // ===========================================================================
 
-constexpr int kTileBytes = 32768;
-constexpr int kLpThreads = 512;
-constexpr int kLpBlocksPerSM = 3;
+constexpr int kTileBytes = kTileBytesHist;
+constexpr int kLpThreads = 256;
+constexpr int kLpBlocksPerSM = 6;
 constexpr uint64_t kFlagAgg = 1, kFlagIncl = 2;
 
 // look-back state word: flag (2 bits) | aggregate (19 bits) | inclusive prefix (43 bits)
@@ -1178,7 +1184,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
     size_t s_excl = align_up(s_left + std::max<uint64_t>(nslots, 1) * 8, 256);
     size_t s_tmp = align_up(s_excl + (nslots + 1) * 8, 256);
     size_t s_meta = align_up(s_tmp + scan_tmp * 8, 256);
-    // ones of level 0 per 32 KB tile of S, counted by the histogram
+    // ones of level 0 per 16 KiB tile of S, counted by the histogram
     const uint64_t tiles0 = (n * w + kTileBytes - 1) / kTileBytes;
     size_t s_tcnt = align_up(s_meta + 2 * kMaxLevels * 8, 256);
     size_t s_end = align_up(s_tcnt + std::max<uint64_t>(tiles0, 1) * 8, 256);
@@ -1222,7 +1228,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         };
         cudaError_t e = cudaSuccess;
         if (h_src) {
-            const uint64_t chunk = (64ull << 20) / w;  // 64 MiB: a whole number of 32 KiB tiles
+            const uint64_t chunk = (64ull << 20) / w;  // 64 MiB: a whole number of 16 KiB tiles
             for (uint64_t off = 0; off < n && e == cudaSuccess; off += chunk) {
                 const uint64_t len = std::min(chunk, n - off);
                 cudaEvent_t ev = nullptr;

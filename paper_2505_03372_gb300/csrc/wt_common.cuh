@@ -306,10 +306,16 @@ __device__ __forceinline__ uint32_t select_in_word(uint64_t x, uint32_t k) {
     return pos;
 }
 
-// Binary select (Algorithm 2, with the readings of the design notes): the
-// position of the k-th (1-based) bit equal to b in level lv, 1 <= k <= count_b.
-// The samples around k bound the L1 blocks (linear scan, usually one or two)
-// and the L2 blocks (binary search); the word scan ends with select_in_word.
+// Binary select (Algorithm 2): the position of the k-th (1-based) bit equal to
+// b in level lv, 1 <= k <= count_b.  The listing is read this way: the sample
+// index is floor(k / K), samples[0] = 0 and samples[m] is the position of the
+// (m K)-th b-bit; the first L1 block is the floor (not the ceiling) of the
+// sample position over 65536; the L2 search stays inside the enclosing L1
+// block and below the next sample; the predicate of both searches is "fewer
+// than k b-bits before the block"; the word loop starts at the chosen L2
+// block's absolute position.  The samples around k bound the L1 blocks
+// (linear scan, usually one or two) and the L2 blocks (binary search); the
+// word scan ends with select_in_word.
 __device__ __forceinline__ uint64_t select_b(const LevelDesc& lv, uint32_t b, uint64_t k, uint32_t k_log2) {
     const uint64_t* S = b ? lv.s1 : lv.s0;
     const uint64_t total = b ? lv.ones : lv.size - lv.ones;

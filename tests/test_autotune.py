@@ -36,7 +36,7 @@ def test_staged_search_finds_the_fastest_and_caches_it(tmp_path):
     views, sg, q = _batch()
     t = FakeTimer()
     best = autotune.tune_batch(views, sg, q, cache_path=path, timer=t, device_name="GPU-A")
-    assert best == {"sample_k": 8192, "query_threads": 256, "lp_ctas_per_sm": 3}
+    assert best == {"sample_k": 8192, "query_threads": 256, "lp_ctas_per_sm": 6}
     assert len(t.calls) == 11
     assert all(c["sample_k"] == 4096 for c in t.calls[:9])
     assert {c["sample_k"] for c in t.calls[9:]} == {2048, 8192}
@@ -59,7 +59,7 @@ def test_unreadable_cache_is_ignored(tmp_path):
     views, sg, q = _batch()
     t = FakeTimer()
     best = autotune.tune_batch(views, sg, q, cache_path=str(path), timer=t, device_name="GPU-A")
-    assert len(t.calls) == 11 and best["lp_ctas_per_sm"] == 3
+    assert len(t.calls) == 11 and best["lp_ctas_per_sm"] == 6
     assert autotune.shape_key(views, sg, q, "GPU-A") in json.load(open(path))
 
 

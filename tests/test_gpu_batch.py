@@ -7,6 +7,7 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from paper_2505_03372_gb300 import binding as wt  # noqa: E402
 from paper_2505_03372_gb300 import workloads  # noqa: E402
+from guard import guarded, intact  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 U64MAX = np.iinfo(np.uint64).max
@@ -47,13 +48,16 @@ def test_batch_matches_oracle(K, qthreads):
     views = list(views) + [buf[:0]]
     sigmas = list(sigmas) + [7]
     with wt.Batch(views, sigmas, sample_k=K, query_threads=qthreads) as b:
-        out = b.set_queries(q["tree"], q["kind"], q["c"], q["arg"])
+        nq = q["arg"].numel()
+        out, full = guarded(nq, torch.int64)
+        b.set_queries(q["tree"], q["kind"], q["c"], q["arg"], out=out)
         want = _expected(views, sigmas, q)
         for _ in range(2):  # the graph can be launched again
             out.fill_(0)
             b.run()
             assert b.status_sync() == wt.WT_OK
             assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
+            assert intact(full, nq), "the batch wrote outside its output"
         # every tree's structure equals the naive oracle tree
         for i, (v, s) in enumerate(zip(views, sigmas)):
             S = v.cpu().numpy().view(np.uint16)
@@ -133,7 +137,7 @@ def test_autotuned_options_are_exact(tmp_path):
         assert b.status_sync() == wt.WT_OK
         assert np.array_equal(out.cpu().numpy().view(np.uint64), _expected(views, sigmas, q))
     # every level-pass grid gives the same answers
-    for lp in (1, 2):
+    for lp in (1, 3):
         with wt.Batch(views, sigmas, lp_ctas_per_sm=lp) as b:
             out = b.set_queries(q["tree"], q["kind"], q["c"], q["arg"])
             b.run()

@@ -11,6 +11,7 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from paper_2505_03372_gb300 import binding as wt  # noqa: E402
 from paper_2505_03372_gb300 import workloads  # noqa: E402
+from guard import guarded, intact  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +48,9 @@ def test_rank_select_match_oracle(nbits, fill, layout, K):
     q = 20000
     i = rng.integers(0, nbits + 1, q).astype(np.int64)
     i[:4] = [0, nbits, nbits + 1, nbits + 100]
-    got = bv.rank(torch.from_numpy(i).cuda()).cpu().numpy().view(np.uint64)
+    out, full = guarded(q, torch.int64)
+    got = bv.rank(torch.from_numpy(i).cuda(), out=out).cpu().numpy().view(np.uint64)
+    assert intact(full, q), "rank wrote outside its output"
     want = np.full(q, U64MAX, np.uint64)
     ok = i <= nbits
     want[ok] = oracle.bv_rank(bits, i[ok])
@@ -59,7 +62,9 @@ def test_rank_select_match_oracle(nbits, fill, layout, K):
         j[:3] = [0, cnt + 1, max(cnt, 1)]
         if cnt:
             j[3:3 + min(cnt, 50)] = np.arange(1, min(cnt, 50) + 1)  # the first b-bits
-        got = bv.select(b, torch.from_numpy(j).cuda()).cpu().numpy().view(np.uint64)
+        out, full = guarded(q, torch.int64)
+        got = bv.select(b, torch.from_numpy(j).cuda(), out=out).cpu().numpy().view(np.uint64)
+        assert intact(full, q), "select wrote outside its output"
         want = np.full(q, U64MAX, np.uint64)
         ok = (j >= 1) & (j <= cnt)
         want[ok] = oracle.bv_select(bits, b, j[ok])

@@ -16,6 +16,7 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from paper_2505_03372_gb300 import binding as wt  # noqa: E402
 from paper_2505_03372_gb300 import workloads  # noqa: E402
+from guard import guarded, intact  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -96,17 +97,23 @@ def _run_queries(t, S, sigma, n, rng, o2=None):
     counts = np.diff(o1.C).astype(np.int64)
     i_acc, c_rank, i_rank, c_sel, j_sel = _edge_queries(n, counts, rng)
     if n:
-        got = _u32(t.access(_dev(i_acc, np.int64)))
+        out, full = guarded(i_acc.size, torch.int32)
+        got = _u32(t.access(_dev(i_acc, np.int64), out=out))
+        assert intact(full, i_acc.size), "access wrote outside its output"
         assert np.array_equal(got, o1.access(i_acc)), "access"
         if o2 is not None:
             assert np.array_equal(got, o2.access(i_acc))
-    got = _u64(t.rank(_dev(c_rank, np.int32), _dev(i_rank, np.int64)))
+    out, full = guarded(i_rank.size, torch.int64)
+    got = _u64(t.rank(_dev(c_rank, np.int32), _dev(i_rank, np.int64), out=out))
+    assert intact(full, i_rank.size), "rank wrote outside its output"
     want = o1.rank(c_rank, i_rank)
     if not np.array_equal(got, want):
         bad = np.nonzero(got != want)[0][:5]
         raise AssertionError(f"rank mismatch at {bad}: c={c_rank[bad]} i={i_rank[bad]} gpu={got[bad]} want={want[bad]}")
     if c_sel.size:
-        got = _u64(t.select(_dev(c_sel, np.int32), _dev(j_sel, np.int64)))
+        out, full = guarded(c_sel.size, torch.int64)
+        got = _u64(t.select(_dev(c_sel, np.int32), _dev(j_sel, np.int64), out=out))
+        assert intact(full, c_sel.size), "select wrote outside its output"
         want = o1.select(c_sel, j_sel)
         if not np.array_equal(got, want):
             bad = np.nonzero(got != want)[0][:5]

@@ -22,6 +22,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
+from guard import guarded, intact  # noqa: E402
 from paper_2505_03372_gb300 import binding as wt  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -46,10 +47,11 @@ def _reference(bits01, K):
 
 def _call(words_dev, nbits, K, cap):
     """One call of the entry point through the C ABI; all buffers are allocated here, by the caller."""
-    l1 = torch.full((nbits // 65536 + 1,), 7, dtype=torch.int64, device="cuda")
-    l2 = torch.full((nbits // 512 + 1,), 7, dtype=torch.int16, device="cuda")
-    s0 = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
-    s1 = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    n1, n2 = nbits // 65536 + 1, nbits // 512 + 1
+    l1, g1 = guarded(n1, torch.int64)
+    l2, g2 = guarded(n2, torch.int16)
+    s0, g3 = guarded(cap, torch.int64)
+    s1, g4 = guarded(cap, torch.int64)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     ones = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     st = wt.lib().wt_bitvector_support_static(words_dev.data_ptr(), nbits, K, l1.data_ptr(), l2.data_ptr(),
@@ -58,6 +60,7 @@ def _call(words_dev, nbits, K, cap):
     assert st == wt.WT_OK, wt.status_str(st)
     torch.cuda.synchronize()
     assert status.item() == 0
+    assert intact(g1, n1) and intact(g2, n2) and intact(g3, cap) and intact(g4, cap), "wrote outside an output"
     return (l1.cpu().numpy().view(np.uint64), l2.cpu().numpy().view(np.uint16), s0.cpu().numpy().view(np.uint64),
             s1.cpu().numpy().view(np.uint64), int(ones.item()))
 
