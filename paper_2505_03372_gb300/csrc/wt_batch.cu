@@ -335,7 +335,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
             a.ctab_n = 0;
             a.cp = cps[i];
         }
-        cpre[i + 1] = cpre[i] + (n + kBatchChunk - 1) / kBatchChunk;
+        cpre[i + 1] = cpre[i] + (n + batch_chunk(h_sigma[i]) - 1) / batch_chunk(h_sigma[i]);
         spre[i + 1] = spre[i] + nslots;
     }
     BatchDev& bd = b->dev;

@@ -616,7 +616,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
                         ((uint32_t)ctab[(x >> 16) & 0xffu] << 16) | ((uint32_t)ctab[x >> 24] << 24);
             }
             in4[g * 32 + lane] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-        } else if (ENCODE) {
+        } else if (ENCODE && !a.cp.pow2) {  // a power-of-two alphabet has identity codes
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 uint32_t nv = 0;
@@ -1437,38 +1437,56 @@ __device__ __forceinline__ uint32_t find_tree(const uint64_t* prefix, uint32_t n
     return lo;
 }
 
-constexpr uint32_t kBatchSmemBins = 4096;
-
-// one CTA per chunk of kBatchChunk symbols of one tree
+// One CTA per chunk of one tree's symbols (batch_chunk(sigma) of them).  The
+// counts go to 32-bit bins in shared memory, kBatchSmemBins at a time: an
+// alphabet of up to that many bins takes one pass over the chunk, a larger
+// one takes one pass per window of bins (the chunk is re-read from L2), and
+// every nonzero bin is added once per window to the tree's histogram.
 template <typename T>
 __global__ void __launch_bounds__(512) batch_hist_kernel(const BatchTreeInfo* __restrict__ info,
                                                          const uint64_t* __restrict__ chunk_prefix, uint32_t ntrees) {
-    __shared__ uint32_t sh[kBatchSmemBins];
+    extern __shared__ uint32_t sh[];  // kBatchSmemBins
     __shared__ uint32_t s_tree;
     const uint64_t g = blockIdx.x;
     if (threadIdx.x == 0) s_tree = find_tree(chunk_prefix, ntrees, g);
     __syncthreads();
     const BatchTreeInfo& ti = info[s_tree];
-    const uint64_t c0 = (g - chunk_prefix[s_tree]) * kBatchChunk;
-    const uint64_t c1 = umin64(ti.n, c0 + kBatchChunk);
     const uint32_t sigma = ti.sigma;
-    const bool small = sigma <= kBatchSmemBins;
-    if (small)
-        for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
+    const uint64_t chunk = batch_chunk(sigma);
+    const uint64_t c0 = (g - chunk_prefix[s_tree]) * chunk;
+    const uint64_t c1 = umin64(ti.n, c0 + chunk);
     const T* S = reinterpret_cast<const T*>(ti.sym);
     unsigned long long* hist = reinterpret_cast<unsigned long long*>(ti.hist);
+    constexpr uint32_t V = 16 / sizeof(T);
+    // c0 is a multiple of the chunk, so S + c0 is 16-byte aligned like S
+    const uint64_t nvec = (c1 - c0) / V;
+    const uint4* S4 = reinterpret_cast<const uint4*>(S + c0);
     bool bad = false;
-    for (uint64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
-        const uint32_t v = (uint32_t)S[j];
-        if (v >= sigma) bad = true;
-        else if (small) atomicAdd(sh + v, 1u);
-        else atomicAdd(hist + v, 1ull);
+    for (uint32_t base = 0; base < sigma; base += kBatchSmemBins) {
+        const uint32_t nb = sigma - base < kBatchSmemBins ? sigma - base : kBatchSmemBins;
+        for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+        for (uint64_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+            const uint4 x = __ldg(S4 + v);
+            const T* e = reinterpret_cast<const T*>(&x);
+#pragma unroll
+            for (uint32_t k = 0; k < V; k++) {
+                const uint32_t s = (uint32_t)e[k];
+                if (s >= sigma) bad = true;
+                else if (s - base < nb) atomicAdd(sh + (s - base), 1u);
+            }
+        }
+        for (uint64_t j = c0 + nvec * V + threadIdx.x; j < c1; j += blockDim.x) {
+            const uint32_t s = (uint32_t)S[j];
+            if (s >= sigma) bad = true;
+            else if (s - base < nb) atomicAdd(sh + (s - base), 1u);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x)
+            if (sh[i]) atomicAdd(hist + base + i, (unsigned long long)sh[i]);
+        __syncthreads();
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(ti.status, kStSymbol);
-    if (small)
-        for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x)
-            if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
 }
 
 // one CTA per tree: C = exclusive scan of the histogram
@@ -1602,9 +1620,17 @@ wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kerne
     WT_CUDA_TRY(cudaMemsetAsync(b.counters, 0, (size_t)b.maxL * 8, s));
     if (b.total_chunks) {
         nk++;
-        if (b.w == 1) batch_hist_kernel<uint8_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
-        else if (b.w == 2) batch_hist_kernel<uint16_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
-        else batch_hist_kernel<uint32_t><<<(unsigned)b.total_chunks, 512, 0, s>>>(b.info, b.chunk_prefix, b.ntrees);
+        const size_t hsm = (size_t)kBatchSmemBins * 4;
+        static bool hcfg = false;
+        if (!hcfg) {
+            cudaFuncSetAttribute(batch_hist_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+            cudaFuncSetAttribute(batch_hist_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+            cudaFuncSetAttribute(batch_hist_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+            hcfg = true;
+        }
+        if (b.w == 1) batch_hist_kernel<uint8_t><<<(unsigned)b.total_chunks, 512, hsm, s>>>(b.info, b.chunk_prefix, b.ntrees);
+        else if (b.w == 2) batch_hist_kernel<uint16_t><<<(unsigned)b.total_chunks, 512, hsm, s>>>(b.info, b.chunk_prefix, b.ntrees);
+        else batch_hist_kernel<uint32_t><<<(unsigned)b.total_chunks, 512, hsm, s>>>(b.info, b.chunk_prefix, b.ntrees);
     }
     batch_C_kernel<<<b.ntrees, kScanThreads, 0, s>>>(b.info);
     nk++;

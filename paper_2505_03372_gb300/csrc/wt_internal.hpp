@@ -112,7 +112,14 @@ struct BatchDev {
     uint32_t* status_pool;           // [ntrees]
 };
 
-constexpr uint64_t kBatchChunk = 65536;  // symbols per histogram work item
+constexpr uint64_t kBatchChunk = 65536;  // symbols per histogram work item (small alphabets)
+constexpr uint32_t kBatchSmemBins = 16384;  // histogram bins counted in shared memory at once
+// Symbols per histogram work item of a tree: alphabets above kBatchSmemBins
+// are counted in shared memory one window of bins at a time, over larger
+// chunks, so that each bin is flushed to the tree's histogram once per window.
+inline __host__ __device__ uint64_t batch_chunk(uint32_t sigma) {
+    return sigma > kBatchSmemBins ? (1ull << 20) : kBatchChunk;
+}
 
 wt_status enqueue_batch_build(const BatchDev& b, cudaStream_t s, uint32_t* kernels);
 uint64_t batch_tile_elems(uint32_t w);
