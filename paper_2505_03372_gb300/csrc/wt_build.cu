@@ -1028,19 +1028,28 @@ __global__ void __launch_bounds__(kLpThreads, kLpBlocksPerSM)
     }
     __syncthreads();
     const uint64_t total = tile_prefix[ntrees];
+    const uint32_t lane = tid & 31;
     uint32_t phase = 0;
     for (;;) {
-        if (tid == 0) {
-            const uint64_t g = atomicAdd(counter, 1ull);
-            s_g = g;
+        if (tid < 32) {
+            // warp 0 takes the next tile and finds its tree: the last tree whose
+            // first tile is <= g, by a 32-ary search (one ballot per round).
+            // Invariant: tile_prefix[lo] <= g < tile_prefix[hi].
+            uint64_t g = 0;
+            if (lane == 0) g = atomicAdd(counter, 1ull);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (lane == 0) s_g = g;
             if (g < total) {
-                uint32_t lo = 0, hi = ntrees - 1;  // last tree whose first tile is <= g
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (tile_prefix[mid] <= g) lo = mid;
-                    else hi = mid - 1;
+                uint32_t lo = 0, hi = ntrees;
+                while (hi - lo > 1) {
+                    const uint32_t step = (hi - lo + 31) / 32;
+                    const uint32_t idx = lo + lane * step;
+                    const bool le = idx < hi && tile_prefix[idx] <= g;
+                    const uint32_t m = __ballot_sync(0xffffffffu, le);  // lane 0 (idx = lo) is always set
+                    lo += (31u - __clz(m)) * step;
+                    hi = hi < lo + step ? hi : lo + step;
                 }
-                s_tree = lo;
+                if (lane == 0) s_tree = lo;
             }
         }
         __syncthreads();

@@ -385,3 +385,44 @@ def test_large_batches_in_walk_order(name, n, nq):
         if "mixed_kind" in q:
             _check_mixed(t, q["mixed_kind"], q["mixed_c"], q["mixed_arg"], o1)
         assert t.status_sync() == wt.WT_OK
+
+
+@pytest.mark.slow
+def test_more_than_2_to_the_32_symbols():
+    """A text longer than 2^32 symbols (u8 over sigma = 5, 3 levels): positions,
+    L1 counters and samples pass 2^32, so every 64-bit path of the build and
+    the walks is taken.  Every level against the naive oracle tree, queries
+    (including positions and ranks near the end) against the definitions."""
+    n = (1 << 32) + 12345
+    sigma = 5
+    sym = workloads.make_symbols(n, sigma, 1, "uniform", seed=2024, device="cuda")
+    with wt.build(sym, sigma) as t:
+        S = _host(sym, 1)
+        del sym
+        o2 = oracle.O2Tree(S, sigma, K=4096)
+        inf = t.info()
+        assert inf.levels == o2.L == 3
+        for l in range(o2.L):
+            assert inf.level_size[l] == o2.level_size(l) and inf.level_ones[l] == o2.level_ones(l), l
+            for what in (wt.EXPORT_BITS, wt.EXPORT_L1, wt.EXPORT_L2, wt.EXPORT_S0, wt.EXPORT_S1):
+                assert np.array_equal(t.export(what, l), o2.export(what, l)), (l, what)
+        assert int(t.export(wt.EXPORT_S0, 0)[-1]) > (1 << 32)  # sample positions past 2^32
+        assert np.array_equal(t.export(wt.EXPORT_NODES), o2.export(oracle.EXPORT_NODES))
+        del o2
+        o1 = oracle.O1(S, sigma)
+        counts = np.diff(o1.C).astype(np.int64)
+        rng = np.random.default_rng(7)
+        q = 20000
+        i = np.concatenate([rng.integers(0, n, q), [0, n - 1, (1 << 32) - 1, 1 << 32, (1 << 32) + 1]]).astype(np.uint64)
+        c = rng.integers(0, sigma, i.size).astype(np.uint32)
+        assert np.array_equal(_u32(t.access(_dev(i, np.int64))), o1.access(i))
+        ir = i.copy()
+        ir[-1] = n  # rank at the very end
+        assert np.array_equal(_u64(t.rank(_dev(c, np.int32), _dev(ir, np.int64))), o1.rank(c, ir))
+        j = (rng.random(i.size) * counts[c]).astype(np.uint64) + 1
+        j[-5:] = counts[c[-5:]]  # last occurrences, far past 2^32
+        got = _u64(t.select(_dev(c, np.int32), _dev(j, np.int64)))
+        want = o1.select(c, j)
+        assert np.array_equal(got, want)
+        assert int(want.max()) > (1 << 32)
+        assert t.status_sync() == wt.WT_OK
