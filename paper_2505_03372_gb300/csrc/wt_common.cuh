@@ -306,6 +306,29 @@ __device__ __forceinline__ uint32_t select_in_word(uint64_t x, uint32_t k) {
     return pos;
 }
 
+// Position (0..63) of the k-th (1-based) set bit of x, popc(x) >= k: one split
+// of the word into 32-bit halves, then binary halving with 32-bit popcounts.
+__device__ __forceinline__ uint32_t select_in_word32(uint64_t x, uint32_t k) {
+    uint32_t w = (uint32_t)x;
+    const uint32_t pl = __popc(w);
+    uint32_t pos = 0;
+    if (k > pl) {
+        k -= pl;
+        w = (uint32_t)(x >> 32);
+        pos = 32;
+    }
+#pragma unroll
+    for (uint32_t wdt = 16; wdt >= 1; wdt >>= 1) {
+        const uint32_t c = __popc(w & ((1u << wdt) - 1u));
+        if (k > c) {
+            k -= c;
+            w >>= wdt;
+            pos += wdt;
+        }
+    }
+    return pos;
+}
+
 // Binary select (Algorithm 2): the position of the k-th (1-based) bit equal to
 // b in level lv, 1 <= k <= count_b.  The listing is read this way: the sample
 // index is floor(k / K), samples[0] = 0 and samples[m] is the position of the
@@ -313,78 +336,169 @@ __device__ __forceinline__ uint32_t select_in_word(uint64_t x, uint32_t k) {
 // sample position over 65536; the L2 search stays inside the enclosing L1
 // block and below the next sample; the predicate of both searches is "fewer
 // than k b-bits before the block"; the word loop starts at the chosen L2
-// block's absolute position.  The samples around k bound the L1 blocks
-// (linear scan, usually one or two) and the L2 blocks (binary search); the
-// word scan ends with select_in_word.
-__device__ __forceinline__ uint64_t select_b(const LevelDesc& lv, uint32_t b, uint64_t k, uint32_t k_log2) {
+// block's absolute position.
+//
+// The search runs in stages over a SelB state so that a thread can walk
+// several queries in lockstep (their loads of one stage in flight together):
+//   selb_range    the two samples around k (or a caller's window) -> position range
+//   selb_l1       the L1 block: one load, a scan only if the range crosses an
+//                 L1 boundary; the L2 entry at the range start is loaded with it
+//   selb_step     one step of the binary search over the L2 entries of the
+//                 range, relative to the L1 block (while lo < hi)
+//   selb_words    the first 32-byte half of the chosen 512-bit block
+//   selb_half     the second half instead, if the bit lies beyond the first
+//   selb_finish   word and bit inside the half (select_in_word32)
+// Inside an L1 block every quantity fits 32 bits.  The first L2 probe does not
+// wait for the L1 counter: the predicate compares with kk = k - (b-bits before
+// the L1 block) only after the probe is issued.
+// Level-wise trees of at least this many levels walk their selects two
+// queries per thread (do_select_n<2>), shallower ones one per thread.
+constexpr uint32_t kPairLevels = 8;
+
+struct SelB {
+    uint64_t k;               // rank sought (1-based) among the b-bits
+    uint64_t lo_pos, hi_pos;  // position range that holds the k-th b-bit
+    uint64_t i1, c1;          // L1 block and its counter
+    const uint16_t* L2;       // L2 counters of block i1
+    uint64_t w0, w1, w2, w3;  // one 32-byte half of the chosen 512-bit block
+    uint32_t b, lo, hi;       // bit value; L2 range [lo, hi] inside block i1
+    uint32_t kk, c2lo, kw;    // rank inside block i1; L2 counter at lo; rank inside the half
+    uint32_t half;            // 0 or 4: which half
+    bool ok;                  // the counters agree that the bit is in the range
+};
+
+
+// samples S_b[m], S_b[m + 1] around k (m = floor(k / K)); past the last sample
+// the range ends at the level's last bit.  on = false leaves a state that the
+// later stages walk on position 0 without effect.
+__device__ __forceinline__ void selb_range(SelB& s, const LevelDesc& lv, uint32_t b, uint64_t k, uint32_t k_log2,
+                                           bool on) {
     const uint64_t* S = b ? lv.s1 : lv.s0;
     const uint64_t total = b ? lv.ones : lv.size - lv.ones;
     const uint64_t m = k >> k_log2;
-    const uint64_t lo_pos = __ldg(S + m);
-    const uint64_t hi_pos = (((m + 1) << k_log2) <= total) ? __ldg(S + m + 1) : lv.size - 1;
-    // L1: last block i1 in [lo_pos>>16, hi_pos>>16] whose start has fewer than k b-bits before it
-    uint64_t i1 = lo_pos >> 16;
-    const uint64_t hi1 = hi_pos >> 16;
-    while (i1 < hi1) {
-        uint64_t nx = i1 + 1;
-        uint64_t c1 = __ldg(lv.l1 + nx);
-        uint64_t cb = b ? c1 : (nx << 16) - c1;
-        if (cb < k) i1 = nx;
-        else break;
+    s.b = b;
+    s.k = k;
+    s.ok = true;
+    s.lo_pos = on ? __ldg(S + m) : 0ull;
+    s.hi_pos = on ? ((((m + 1) << k_log2) <= total) ? __ldg(S + m + 1) : lv.size - 1) : 0ull;
+}
+
+// a caller's window [lo, hi] instead of the samples (lo <= hi <= size - 1);
+// the stages then also check that the k-th b-bit lies inside it (s.ok)
+__device__ __forceinline__ void selb_window(SelB& s, uint32_t b, uint64_t k, uint64_t lo, uint64_t hi) {
+    s.b = b;
+    s.k = k;
+    s.ok = true;
+    s.lo_pos = lo;
+    s.hi_pos = hi;
+}
+
+// Precondition: lo_pos <= hi_pos <= size - 1.
+__device__ __forceinline__ void selb_l1(SelB& s, const LevelDesc& lv) {
+    const uint64_t hi1 = s.hi_pos >> 16;
+    s.i1 = s.lo_pos >> 16;
+    s.c1 = __ldg(lv.l1 + s.i1);
+    s.lo = (uint32_t)(s.lo_pos >> 9) & 127u;
+    s.hi = (s.i1 == hi1) ? ((uint32_t)(s.hi_pos >> 9) & 127u) : 127u;
+    while (s.i1 < hi1) {  // last L1 block of the range with fewer than k b-bits before it
+        const uint64_t c1n = __ldg(lv.l1 + s.i1 + 1);
+        if ((s.b ? c1n : ((s.i1 + 1) << 16) - c1n) >= s.k) break;
+        s.i1++;
+        s.c1 = c1n;
+        s.lo = 0;
+        s.hi = (s.i1 == hi1) ? ((uint32_t)(s.hi_pos >> 9) & 127u) : 127u;
     }
-    const uint64_t c1 = __ldg(lv.l1 + i1);
-    const uint64_t base1 = b ? c1 : (i1 << 16) - c1;
-    uint64_t kk = k - base1;
-    // L2: last block in the range with fewer than kk b-bits (relative to the L1 block)
-    uint64_t lo2 = umax64(i1 << 7, lo_pos >> 9);
-    uint64_t hi2 = umin64((i1 << 7) + 127, hi_pos >> 9);
-    while (lo2 < hi2) {
-        uint64_t mid = (lo2 + hi2 + 1) >> 1;
-        uint64_t c2 = __ldg(lv.l2 + mid);
-        uint64_t cb = b ? c2 : ((mid << 9) - (i1 << 16)) - c2;
-        if (cb < kk) lo2 = mid;
-        else hi2 = mid - 1;
+    s.L2 = lv.l2 + (s.i1 << 7);
+    s.c2lo = __ldg(s.L2 + s.lo);
+}
+
+// b-bits of L1 block i1 before its L2 entry e (e relative to the block)
+__device__ __forceinline__ uint32_t selb_l2count(const SelB& s, uint32_t e, uint32_t v) {
+    return s.b ? v : (e << 9) - v;
+}
+
+// CHECK: a caller's window may miss the bit, so the stages keep s.ok; between
+// the samples the bit is always there and the checks are left out.
+template <bool CHECK>
+__device__ __forceinline__ void selb_rank(SelB& s) {
+    const uint64_t before = s.b ? s.c1 : (s.i1 << 16) - s.c1;
+    if (CHECK) s.ok = before < s.k;
+    s.kk = (uint32_t)(s.k - before);  // 1..65536 when the bit is in block i1
+}
+
+__device__ __forceinline__ void selb_step(SelB& s) {
+    const uint32_t mid = (s.lo + s.hi + 1) >> 1;
+    const uint32_t v = __ldg(s.L2 + mid);
+    if (selb_l2count(s, mid, v) < s.kk) {
+        s.lo = mid;
+        s.c2lo = v;
+    } else {
+        s.hi = mid - 1;
     }
-    {
-        uint64_t c2 = __ldg(lv.l2 + lo2);
-        kk -= b ? c2 : ((lo2 << 9) - (i1 << 16)) - c2;
+}
+
+__device__ __forceinline__ const uint64_t* selb_block(const SelB& s, const LevelDesc& lv) {
+    return lv.words + (((s.i1 << 7) + s.lo) << 3);
+}
+
+// rank inside the chosen 512-bit block; its first 32-byte half
+template <bool CHECK>
+__device__ __forceinline__ void selb_words(SelB& s, const LevelDesc& lv) {
+    const uint32_t before = selb_l2count(s, s.lo, s.c2lo);
+    if (CHECK) s.ok = s.ok && before < s.kk;
+    s.kw = s.kk - before;
+    s.half = 0;
+    ldg_nc_v4(selb_block(s, lv), s.w0, s.w1, s.w2, s.w3);
+}
+
+// the second half instead, if the bit lies beyond the first
+__device__ __forceinline__ void selb_half(SelB& s, const LevelDesc& lv, bool on) {
+    const uint64_t fl = s.b ? 0ull : ~0ull;
+    const uint32_t h = __popcll(s.w0 ^ fl) + __popcll(s.w1 ^ fl) + __popcll(s.w2 ^ fl) + __popcll(s.w3 ^ fl);
+    if (on && h < s.kw) {
+        s.kw -= h;
+        s.half = 4;
+        ldg_nc_v4(selb_block(s, lv) + 4, s.w0, s.w1, s.w2, s.w3);
     }
-    // words of the 512-bit block, one 32-byte half at a time
-    const uint64_t* wp = lv.words + (lo2 << 3);
-    uint32_t kw = (uint32_t)kk;
-    uint64_t w0, w1, w2, w3;
-    ldg_nc_v4(wp, w0, w1, w2, w3);
-    uint32_t wi = 0;
-    {
-        const uint32_t h = __popcll(b ? w0 : ~w0) + __popcll(b ? w1 : ~w1) + __popcll(b ? w2 : ~w2) +
-                           __popcll(b ? w3 : ~w3);
-        if (h < kw) {
-            kw -= h;
-            wi = 4;
-            ldg_nc_v4(wp + 4, w0, w1, w2, w3);
-        }
+}
+
+template <bool CHECK>
+__device__ __forceinline__ uint64_t selb_finish(SelB& s) {
+    const uint64_t fl = s.b ? 0ull : ~0ull;
+    const uint64_t a0 = s.w0 ^ fl, a1 = s.w1 ^ fl, a2 = s.w2 ^ fl, a3 = s.w3 ^ fl;
+    const uint32_t p0 = __popcll(a0), p1 = __popcll(a1), p2 = __popcll(a2);
+    uint64_t wv = a3;
+    uint32_t wj = 3, kw = s.kw;
+    if (p0 >= kw) {
+        wv = a0;
+        wj = 0;
+    } else if (p0 + p1 >= kw) {
+        wv = a1;
+        wj = 1;
+        kw -= p0;
+    } else if (p0 + p1 + p2 >= kw) {
+        wv = a2;
+        wj = 2;
+        kw -= p0 + p1;
+    } else {
+        kw -= p0 + p1 + p2;
+        if (CHECK) s.ok = s.ok && kw <= (uint32_t)__popcll(a3);
     }
-    uint64_t wv = b ? w3 : ~w3;
-    uint32_t wj = 3;
-    {
-        const uint64_t a0 = b ? w0 : ~w0, a1 = b ? w1 : ~w1, a2 = b ? w2 : ~w2;
-        const uint32_t p0 = __popcll(a0), p1 = __popcll(a1), p2 = __popcll(a2);
-        if (p0 >= kw) {
-            wv = a0;
-            wj = 0;
-        } else if (p0 + p1 >= kw) {
-            wv = a1;
-            wj = 1;
-            kw -= p0;
-        } else if (p0 + p1 + p2 >= kw) {
-            wv = a2;
-            wj = 2;
-            kw -= p0 + p1;
-        } else {
-            kw -= p0 + p1 + p2;
-        }
-    }
-    return ((lo2 << 9) + ((uint64_t)(wi + wj) << 6)) + select_in_word(wv, kw);
+    return ((((s.i1 << 7) + s.lo) << 9) + ((uint64_t)(s.half + wj) << 6)) + select_in_word32(wv, kw);
+}
+
+// Searches stay inside the level's arrays: lo <= hi always, hi is at most the
+// L2 entry of the range's last position, and a range that crosses an L1
+// boundary makes block i1 a full one.
+__device__ __forceinline__ uint64_t select_b(const LevelDesc& lv, uint32_t b, uint64_t k, uint32_t k_log2) {
+    SelB s;
+    selb_range(s, lv, b, k, k_log2, true);
+    selb_l1(s, lv);
+    selb_rank<false>(s);
+    while (s.lo < s.hi) selb_step(s);
+    selb_words<false>(s, lv);
+    selb_half(s, lv, true);
+    return selb_finish<false>(s);
 }
 
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t bits) { atomicOr(st, bits); }

@@ -491,91 +491,106 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __
 // query
 // ---------------------------------------------------------------------------
 
-// Sampled-select search restricted to the window [lo, hi]; ok = false if the
-// counters show the k-th b-bit is not inside it.
-__device__ __forceinline__ uint64_t select_b_window(const LevelDesc& lv, uint32_t b, uint64_t k, uint64_t lo,
-                                                    uint64_t hi, bool& ok) {
-    uint64_t i1 = lo >> 16;
-    const uint64_t hi1 = hi >> 16;
-    while (i1 < hi1) {
-        const uint64_t nx = i1 + 1;
-        const uint64_t c1 = __ldg(lv.l1 + nx);
-        if ((b ? c1 : (nx << 16) - c1) < k) i1 = nx;
-        else break;
-    }
-    const uint64_t c1 = __ldg(lv.l1 + i1);
-    const uint64_t base1 = b ? c1 : (i1 << 16) - c1;
-    if (base1 >= k) {
-        ok = false;
-        return 0;
-    }
-    uint64_t kk = k - base1;
-    uint64_t lo2 = umax64(i1 << 7, lo >> 9);
-    uint64_t hi2 = umin64((i1 << 7) + 127, hi >> 9);
-    if (lo2 > hi2) lo2 = hi2;
-    while (lo2 < hi2) {
-        const uint64_t mid = (lo2 + hi2 + 1) >> 1;
-        const uint64_t c2 = __ldg(lv.l2 + mid);
-        if ((b ? c2 : ((mid << 9) - (i1 << 16)) - c2) < kk) lo2 = mid;
-        else hi2 = mid - 1;
-    }
-    {
-        const uint64_t c2 = __ldg(lv.l2 + lo2);
-        const uint64_t cb = b ? c2 : ((lo2 << 9) - (i1 << 16)) - c2;
-        if (cb >= kk) {
-            ok = false;
-            return 0;
-        }
-        kk -= cb;
-    }
-    // words of the 512-bit block, one 32-byte half at a time
-    const uint64_t* wp = lv.words + (lo2 << 3);
-    uint32_t kw = (uint32_t)kk;
-#pragma unroll 1
-    for (uint32_t h = 0; h < 8; h += 4) {
-        uint64_t w[4];
-        ldg_nc_v4(wp + h, w[0], w[1], w[2], w[3]);
-#pragma unroll
-        for (uint32_t e = 0; e < 4; e++) {
-            const uint64_t a = b ? w[e] : ~w[e];
-            const uint32_t p = __popcll(a);
-            if (p >= kw) return (lo2 << 9) + ((uint64_t)(h + e) << 6) + select_in_word(a, kw);
-            kw -= p;
-        }
-    }
-    ok = false;  // not in this 512-bit block: the window did not hold the bit
-    return 0;
+// {start, r0} of node (l, p) from the node table (slots are 32-byte aligned)
+__device__ __forceinline__ ulonglong2 node_entry_sr(const TreeDesc& t, uint32_t l, uint64_t p) {
+    return ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + ((1ull << l) - 1 + p)));
 }
 
-__device__ __forceinline__ uint64_t select_b_learned(const TreeDesc& t, const LearnedDesc& ld, const float* mlp_s,
-                                                     uint32_t l, uint32_t b, uint64_t k, uint32_t& fb) {
-    const LevelDesc& lv = t.lv[l];
-    const uint64_t m = k >> (t.k_log2 + kAnchorLog2);
-    const Seg g = anchor_seg(lv, b, m, t.k_log2);
-    const ushort4 r = ld.rec[l][b][m];
-    int64_t R[kKnots];
-    unpack_resid(r, ld.rsh[l][b], R);
-    const uint64_t p = predict(ld.mode, g, R, k, mlp_s + (2 * l + b) * kMlpParams);
-    const uint64_t e = (uint64_t)r.w << ld.esh[l][b];
-    const uint64_t lo = p > e ? p - e : 0;
-    const uint64_t hi = umin64(p + e, lv.size - 1);
-    bool ok = true;
-    const uint64_t pos = select_b_window(lv, b, k, lo, hi, ok);
-    if (ok) return pos;
-    fb++;
-    return select_b(lv, b, k, t.k_log2);
+// Learned select of NQ queries in lockstep (see do_select_n): per level the
+// node entry (issued a level early), the anchor samples and the segment's
+// record, the model's prediction p, then the staged search of the binary
+// select (SelB) inside [p - eps, p + eps].  A query whose counters show the
+// bit outside its window falls back to the sampled select and is counted.
+template <int NQ>
+__device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const LearnedDesc& ld, const float* mlp_s,
+                                                    const uint32_t (&c)[NQ], const uint64_t (&jin)[NQ],
+                                                    const bool (&act)[NQ], uint64_t (&res)[NQ], uint32_t& fb) {
+    const CodeParams& cp = t.cp;
+    const uint32_t kl = t.k_log2;
+    uint32_t code[NQ], len[NQ];
+    uint64_t j[NQ];
+    ulonglong2 ne[NQ];
+    int lmax = -1;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        code[q] = 0;
+        len[q] = 0;
+        if (act[q]) encode(cp, c[q], code[q], len[q]);
+        j[q] = jin[q];
+        lmax = max(lmax, (int)len[q] - 1);
+        ne[q] = make_ulonglong2(0, 0);
+        if (len[q]) ne[q] = node_entry_sr(t, len[q] - 1, (uint64_t)code[q] >> (cp.L - (len[q] - 1)));
+    }
+    for (int l = lmax; l >= 0; l--) {
+        const LevelDesc& lv = t.lv[l];
+        bool on[NQ];
+        uint32_t b[NQ];
+        uint64_t start[NQ], k[NQ];
+        Seg g[NQ];
+        ushort4 r[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            on[q] = l < (int)len[q];
+            b[q] = (code[q] >> (cp.L - 1 - (uint32_t)l)) & 1u;
+            start[q] = ne[q].x;
+            // rank 1 of level l stands in for a query that is not on this level
+            k[q] = on[q] ? (b[q] ? (start[q] - ne[q].y) : ne[q].y) + j[q] : 1ull;
+            if (on[q] && l > 0) ne[q] = node_entry_sr(t, (uint32_t)l - 1, (uint64_t)code[q] >> (cp.L - (uint32_t)l + 1));
+            const uint64_t m = k[q] >> (kl + kAnchorLog2);
+            g[q] = anchor_seg(lv, b[q], m, kl);
+            r[q] = ld.rec[l][b[q]][m];
+        }
+        SelB s[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            int64_t R[kKnots];
+            unpack_resid(r[q], ld.rsh[l][b[q]], R);
+            const uint64_t p = predict(ld.mode, g[q], R, k[q], mlp_s + (2 * l + b[q]) * kMlpParams);
+            const uint64_t e = (uint64_t)r[q].w << ld.esh[l][b[q]];
+            const uint64_t hi = umin64(p + e, lv.size - 1);
+            const uint64_t lo = umin64(p > e ? p - e : 0ull, hi);  // lo <= hi <= size - 1
+            selb_window(s[q], b[q], k[q], lo, hi);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_l1(s[q], lv);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_rank<true>(s[q]);
+        bool more = true;
+        while (more) {
+            more = false;
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                if (s[q].lo < s[q].hi) selb_step(s[q]);
+                more = more || s[q].lo < s[q].hi;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_words<true>(s[q], lv);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_half(s[q], lv, on[q]);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            uint64_t pos = selb_finish<true>(s[q]);
+            if (on[q] && !s[q].ok) {
+                fb++;
+                pos = select_b(lv, b[q], k[q], kl);
+            }
+            if (on[q]) j[q] = pos + 1 - start[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; q++) res[q] = j[q] - 1;
 }
 
 constexpr int kLqThreads = 256;
 
 // ORD: the queries were sorted by walk key; idx[k] is query k's original slot.
-template <bool ORD>
-__global__ void __launch_bounds__(kLqThreads) select_learned_kernel(const __grid_constant__ TreeDesc t,
-                                                                    const __grid_constant__ LearnedDesc ld,
-                                                                    const uint32_t* __restrict__ qc,
-                                                                    const uint64_t* __restrict__ qj,
-                                                                    const uint32_t* __restrict__ idx,
-                                                                    uint64_t* __restrict__ out, uint64_t q) {
+// NQ = 2 for deep trees, as for the sampled select; the register bounds (40
+// and 77 per thread) are the largest occupancies without spills.
+template <bool ORD, int NQ>
+__global__ void __launch_bounds__(kLqThreads, NQ == 1 ? 6 : 3) select_learned_kernel(
+    const __grid_constant__ TreeDesc t, const __grid_constant__ LearnedDesc ld, const uint32_t* __restrict__ qc,
+    const uint64_t* __restrict__ qj, const uint32_t* __restrict__ idx, uint64_t* __restrict__ out, uint64_t q) {
     extern __shared__ float mlp_s[];
     if (ld.mode == kLearnMlp) {
         const uint32_t np = 2 * t.cp.L * kMlpParams;
@@ -583,27 +598,26 @@ __global__ void __launch_bounds__(kLqThreads) select_learned_kernel(const __grid
         __syncthreads();
     }
     uint32_t fb = 0;
-    for (uint64_t kq = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; kq < q; kq += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = __ldg(qc + kq);
-        uint64_t j = __ldg(qj + kq);
-        bool bad = c >= t.cp.sigma || j == 0;
-        if (!bad) bad = j > __ldg(t.C + c + 1) - __ldg(t.C + c);
-        uint64_t res = UINT64_MAX;
-        if (!bad) {
-            uint32_t code, len;
-            encode(t.cp, c, code, len);
-            for (int l = (int)len - 1; l >= 0; l--) {
-                const uint32_t b = (code >> (t.cp.L - 1 - (uint32_t)l)) & 1u;
-                const ulonglong2 ne =
-                    ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + ((1ull << l) - 1 + ((uint64_t)code >> (t.cp.L - (uint32_t)l)))));
-                const uint64_t kb = b ? (ne.x - ne.y) : ne.y;
-                const uint64_t pos = select_b_learned(t, ld, mlp_s, (uint32_t)l, b, kb + j, fb);
-                j = pos + 1 - ne.x;
-            }
-            res = j - 1;
+    const uint64_t stride = (uint64_t)NQ * gridDim.x * blockDim.x;
+    for (uint64_t k0 = (uint64_t)NQ * ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x); k0 < q; k0 += stride) {
+        uint32_t c[NQ];
+        uint64_t j[NQ], r[NQ];
+        bool in[NQ], ok[NQ], bad[NQ];
+        bool any_bad = false;
+#pragma unroll
+        for (int x = 0; x < NQ; x++) {
+            in[x] = k0 + x < q;
+            c[x] = in[x] ? __ldg(qc + k0 + x) : 0u;
+            j[x] = in[x] ? __ldg(qj + k0 + x) : 1ull;
+            bad[x] = in[x] && (c[x] >= t.cp.sigma || j[x] == 0 || j[x] > __ldg(t.C + c[x] + 1) - __ldg(t.C + c[x]));
+            ok[x] = in[x] && !bad[x];
+            any_bad = any_bad || bad[x];
         }
-        out[ORD ? __ldg(idx + kq) : kq] = res;
-        if (__any_sync(__activemask(), bad) && bad) atomicOr(t.status, kStQuery);
+        do_select_learned_n<NQ>(t, ld, mlp_s, c, j, ok, r, fb);
+#pragma unroll
+        for (int x = 0; x < NQ; x++)
+            if (in[x]) out[ORD ? __ldg(idx + k0 + x) : k0 + x] = bad[x] ? UINT64_MAX : r[x];
+        if (__any_sync(__activemask(), any_bad) && any_bad) atomicOr(t.status, kStQuery);
     }
     if (fb) atomicAdd(ld.fallbacks, (unsigned long long)fb);
 }
@@ -808,12 +822,15 @@ wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const u
                                 uint64_t q, cudaStream_t s) {
     if (!q) return WT_OK;
     const size_t sm = t->learned.mode == kLearnMlp ? (size_t)2 * t->desc.cp.L * kMlpParams * 4 : 0;
-    static int per_sm = 0;
-    if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_learned_kernel<false>, kLqThreads, 20 * 1024);
-        if (per_sm <= 0) per_sm = 1;
+    const bool pair = t->desc.cp.L >= kPairLevels;
+    static int per_sm[2] = {0, 0};
+    if (!per_sm[pair]) {
+        int v = 0;
+        if (pair) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, select_learned_kernel<false, 2>, kLqThreads, 20 * 1024);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, select_learned_kernel<false, 1>, kLqThreads, 20 * 1024);
+        per_sm[pair] = v > 0 ? v : 1;
     }
-    uint64_t need = (q + kLqThreads - 1) / kLqThreads, full = (uint64_t)per_sm * sm_count();
+    uint64_t need = (q + kLqThreads - 1) / kLqThreads, full = (uint64_t)per_sm[pair] * sm_count();
     const unsigned grid = (unsigned)(need < full ? need : full);
     const char* name = t->learned.mode == kLearnMlp ? "select_learned_mlp" : "select_learned_pla";
     // large batches walk in the same order as the sampled select's
@@ -822,14 +839,16 @@ wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const u
         wt_status st = order_queries(t, 2, nullptr, d_c, d_j, q, s, o);
         if (st == WT_OK) {
             ProfScope ps(name, s);
-            select_learned_kernel<true><<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, o.c, o.a, o.idx, d_out, q);
+            auto kfn = pair ? select_learned_kernel<true, 2> : select_learned_kernel<true, 1>;
+            kfn<<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, o.c, o.a, o.idx, d_out, q);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
         if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps(name, s);
-    select_learned_kernel<false><<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, d_c, d_j, nullptr, d_out, q);
+    auto kfn = pair ? select_learned_kernel<false, 2> : select_learned_kernel<false, 1>;
+    kfn<<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, d_c, d_j, nullptr, d_out, q);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 

@@ -63,24 +63,53 @@ __global__ void __launch_bounds__(kQThreads) rank_kernel(const __grid_constant__
     }
 }
 
-// The select walk is latency-bound on L1/L2 hits; compiled for seven resident
-// CTAs per SM (at most 36 registers) it keeps more walks in flight (measured:
-// 1.43 -> 1.37 ms per 10^7 sorted selects on the text workload).  Access and
-// rank keep their registers (forcing them spills and is slower).
-template <bool ORD>
-__global__ void __launch_bounds__(kQThreads, 7) select_kernel(const __grid_constant__ TreeDesc t,
-                                                           const uint32_t* __restrict__ qc,
-                                                           const uint64_t* __restrict__ qj,
-                                                           const uint32_t* __restrict__ idx,
-                                                           uint64_t* __restrict__ out, uint64_t q, uint32_t slots) {
+// Select walks.  The walk is latency-bound on L1/L2 hits: every level is a
+// chain of dependent loads (samples, L1 counter, about seven L2 probes, the
+// words).  Shallow trees run one query per thread, compiled for eight CTAs per
+// SM (32 registers); deep trees (kPairLevels levels or more) run two queries
+// per thread in lockstep (do_select_n<2>, four CTAs per SM, 64 registers),
+// which keeps twice the chains in flight per warp and lets the second query of
+// a pair (its sorted neighbour) hit the lines the first brought into L1.
+// Measured, 10^7 sorted selects: 7 levels 1.09 ms single / 1.20 ms paired;
+// 8 levels 1.88 / 1.45; 12 levels 3.84 / 2.47; 16 levels 4.40 / 2.97; 20
+// levels 7.08 / 5.14.  The threshold is kPairLevels.  Loading the first L2
+// probes together with the L1 counter (one probe, or three for a four-way
+// first step) was slower at every depth: the extra registers spill.
+
+template <bool ORD, int NQ>
+__global__ void __launch_bounds__(kQThreads, NQ == 1 ? 8 : 4) select_kernel(const __grid_constant__ TreeDesc t,
+                                                                          const uint32_t* __restrict__ qc,
+                                                                          const uint64_t* __restrict__ qj,
+                                                                          const uint32_t* __restrict__ idx,
+                                                                          uint64_t* __restrict__ out, uint64_t q,
+                                                                          uint32_t slots) {
     extern __shared__ ulonglong2 s_nodes[];
     const NodeCache nc = load_node_cache(t, s_nodes, slots);
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < q; k += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = __ldg(qc + k);
-        const uint64_t j = __ldg(qj + k);
-        const bool bad = !select_valid(t, c, j);
-        out[ORD ? __ldg(idx + k) : k] = bad ? UINT64_MAX : (t.layout ? do_select_m(t, c, j) : do_select(t, nc, c, j));
-        flag_query_error(t, bad);
+    const uint64_t stride = (uint64_t)NQ * gridDim.x * blockDim.x;
+    for (uint64_t k0 = (uint64_t)NQ * ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x); k0 < q; k0 += stride) {
+        uint32_t c[NQ];
+        uint64_t j[NQ], r[NQ];
+        bool in[NQ], ok[NQ], bad[NQ];
+        bool any_bad = false;
+#pragma unroll
+        for (int x = 0; x < NQ; x++) {
+            in[x] = k0 + x < q;
+            c[x] = in[x] ? __ldg(qc + k0 + x) : 0u;
+            j[x] = in[x] ? __ldg(qj + k0 + x) : 1ull;
+            bad[x] = in[x] && !select_valid(t, c[x], j[x]);
+            ok[x] = in[x] && !bad[x];
+            any_bad = any_bad || bad[x];
+        }
+        if (t.layout) {
+#pragma unroll
+            for (int x = 0; x < NQ; x++) r[x] = ok[x] ? do_select_m(t, c[x], j[x]) : 0ull;
+        } else {
+            do_select_n<NQ>(t, nc, c, j, ok, r);
+        }
+#pragma unroll
+        for (int x = 0; x < NQ; x++)
+            if (in[x]) out[ORD ? __ldg(idx + k0 + x) : k0 + x] = bad[x] ? UINT64_MAX : r[x];
+        flag_query_error(t, any_bad);
     }
 }
 
@@ -338,7 +367,10 @@ wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_k
 // launches
 // ---------------------------------------------------------------------------
 
-constexpr uint32_t kNodeCacheSlots = 2048;  // levels 0..10: 32 KB of {start, r0}
+// levels 0..7: 4 KB of {start, r0}.  A larger cache takes shared memory from
+// L1, where the walks' counters and words hit: 2048 slots (32 KB per CTA) made
+// the deep-tree walks up to 2.6x slower.
+constexpr uint32_t kNodeCacheSlots = 256;
 
 static uint32_t cache_slots(const wt_tree_s* t) {
     if (t->desc.layout != 0) return 0;  // a wavelet matrix has no node table to cache
@@ -346,6 +378,9 @@ static uint32_t cache_slots(const wt_tree_s* t) {
     const uint64_t nslots = L ? (1ull << L) - 1 : 0;
     return (uint32_t)(nslots < kNodeCacheSlots ? nslots : kNodeCacheSlots);
 }
+
+// deep level-wise trees walk their selects two per thread (see select_kernel)
+static bool pair_walks(const wt_tree_s* t) { return t->desc.layout == 0 && t->desc.cp.L >= kPairLevels; }
 
 template <typename K>
 static int grid_for(K kernel, uint64_t q, size_t smem) {
@@ -410,14 +445,16 @@ wt_status launch_select(const wt_tree_s* t, const uint32_t* d_c, const uint64_t*
         wt_status st = order_queries(t, 2, nullptr, d_c, d_j, q, s, o);
         if (st == WT_OK) {
             ProfScope ps("select", s);
-            WALK_LAUNCH(select_kernel<true>, t, q, s, o.c, o.a, o.idx, d_out);
+            auto kfn = pair_walks(t) ? select_kernel<true, 2> : select_kernel<true, 1>;
+            WALK_LAUNCH(kfn, t, q, s, o.c, o.a, o.idx, d_out);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
         if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps("select", s);
-    WALK_LAUNCH(select_kernel<false>, t, q, s, d_c, d_j, nullptr, d_out);
+    auto kfn = pair_walks(t) ? select_kernel<false, 2> : select_kernel<false, 1>;
+    WALK_LAUNCH(kfn, t, q, s, d_c, d_j, nullptr, d_out);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 

@@ -66,23 +66,78 @@ __device__ __forceinline__ uint64_t do_rank(const TreeDesc& t, const NodeCache& 
 }
 
 // Algorithms 7 and 8: leaf to root; the node of c at level l is the prefix of
-// its code, so getNodeStart becomes a table index.
-__device__ __forceinline__ uint64_t do_select(const TreeDesc& t, const NodeCache& nc, uint32_t c, uint64_t j) {
+// its code, so getNodeStart becomes a table index.  NQ queries walk in
+// lockstep, one level at a time from the longest code down: at every stage of
+// the binary select (wt_common.cuh, SelB) the loads of all NQ queries are
+// issued before any is used, so one thread keeps NQ dependent chains in
+// flight.  A query joins at its own leaf level (levels above its code length
+// are skipped); act[q] = false walks nothing.
+template <int NQ>
+__device__ __forceinline__ void do_select_n(const TreeDesc& t, const NodeCache& nc, const uint32_t (&c)[NQ],
+                                            const uint64_t (&jin)[NQ], const bool (&act)[NQ], uint64_t (&res)[NQ]) {
     const CodeParams& cp = t.cp;
-    uint32_t code, len;
-    encode(cp, c, code, len);
-    if (len == 0) return j - 1;
-    int l = (int)len - 1;
-    ulonglong2 ne = node_sr(t, nc, (uint32_t)l, (uint64_t)code >> (cp.L - (uint32_t)l));
-    for (; l >= 0; l--) {
-        const uint32_t b = (code >> (cp.L - 1 - (uint32_t)l)) & 1u;
-        const uint64_t start = ne.x;
-        const uint64_t kb = b ? (start - ne.y) : ne.y;  // b-bits before the node
-        if (l > 0) ne = node_sr(t, nc, (uint32_t)l - 1, (uint64_t)code >> (cp.L - (uint32_t)l + 1));
-        const uint64_t pos = select_b(t.lv[l], b, kb + j, t.k_log2);
-        j = pos + 1 - start;
+    uint32_t code[NQ], len[NQ];
+    uint64_t j[NQ];
+    ulonglong2 ne[NQ];
+    int lmax = -1;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        code[q] = 0;
+        len[q] = 0;
+        if (act[q]) encode(cp, c[q], code[q], len[q]);
+        j[q] = jin[q];
+        lmax = max(lmax, (int)len[q] - 1);
+        ne[q] = make_ulonglong2(0, 0);
+        if (len[q]) ne[q] = node_sr(t, nc, len[q] - 1, (uint64_t)code[q] >> (cp.L - (len[q] - 1)));
     }
-    return j - 1;
+    for (int l = lmax; l >= 0; l--) {
+        const LevelDesc& lv = t.lv[l];
+        bool on[NQ];
+        uint64_t start[NQ];
+        SelB s[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            on[q] = l < (int)len[q];
+            const uint32_t b = (code[q] >> (cp.L - 1 - (uint32_t)l)) & 1u;
+            start[q] = ne[q].x;
+            const uint64_t kb = b ? (start[q] - ne[q].y) : ne[q].y;  // b-bits before the node
+            if (on[q] && l > 0) ne[q] = node_sr(t, nc, (uint32_t)l - 1, (uint64_t)code[q] >> (cp.L - (uint32_t)l + 1));
+            selb_range(s[q], lv, b, kb + j[q], t.k_log2, on[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_l1(s[q], lv);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_rank<false>(s[q]);
+        bool more = true;
+        while (more) {
+            more = false;
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                if (s[q].lo < s[q].hi) selb_step(s[q]);
+                more = more || s[q].lo < s[q].hi;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_words<false>(s[q], lv);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) selb_half(s[q], lv, on[q]);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const uint64_t pos = selb_finish<false>(s[q]);
+            if (on[q]) j[q] = pos + 1 - start[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; q++) res[q] = j[q] - 1;
+}
+
+__device__ __forceinline__ uint64_t do_select(const TreeDesc& t, const NodeCache& nc, uint32_t c, uint64_t j) {
+    const uint32_t cc[1] = {c};
+    const uint64_t jj[1] = {j};
+    const bool act[1] = {true};
+    uint64_t r[1];
+    do_select_n<1>(t, nc, cc, jj, act, r);
+    return r[0];
 }
 
 // ---------------------------------------------------------------------------

@@ -426,3 +426,39 @@ def test_more_than_2_to_the_32_symbols():
         assert np.array_equal(got, want)
         assert int(want.max()) > (1 << 32)
         assert t.status_sync() == wt.WT_OK
+
+
+@pytest.mark.parametrize("n,sigma,w,nq", [
+    (200003, 96, 1, 4001),         # 7 levels: one select per thread
+    (200003, 1000, 2, 4001),       # 10 levels: two per thread, unsorted
+    (1 << 27, 1000, 2, (1 << 17) + 1),  # two per thread, in walk order
+])
+def test_select_walk_pairs_with_odd_counts_and_invalid_queries(n, sigma, w, nq):
+    """Deep trees walk their selects two per thread in lockstep.  An odd batch
+    leaves the last thread one query; invalid queries (symbol out of range,
+    j = 0, j past the count) sit next to valid ones in the same pairs.  Every
+    valid answer equals the definition, every invalid one is the sentinel."""
+    sym = workloads.make_symbols(n, sigma, w, "zipf", 1.0, seed=n + sigma, device="cuda")
+    S = _host(sym, w)
+    o1 = oracle.O1(S, sigma)
+    counts = np.diff(o1.C).astype(np.int64)
+    present = np.nonzero(counts)[0]
+    rng = np.random.default_rng(nq)
+    c = present[rng.integers(0, present.size, nq)].astype(np.uint32)
+    j = (rng.random(nq) * counts[c]).astype(np.uint64) + 1
+    bad = rng.random(nq) < 0.01
+    kinds = rng.integers(0, 3, nq)
+    c[bad & (kinds == 0)] = sigma + 5
+    j[bad & (kinds == 1)] = 0
+    jb = bad & (kinds == 2)
+    j[jb] = counts[c[jb]].astype(np.uint64) + 1
+    with wt.build(sym, sigma) as t:
+        assert (t.info().levels >= 8) == (sigma >= 256)
+        out, full = guarded(nq, torch.int64)
+        got = _u64(t.select(_dev(c, np.int32), _dev(j, np.int64), out=out))
+        assert intact(full, nq), "select wrote outside its output"
+        want = np.full(nq, np.uint64(0xFFFFFFFFFFFFFFFF), np.uint64)
+        ok = ~bad
+        want[ok] = o1.select(c[ok], j[ok])
+        assert np.array_equal(got, want)
+        assert t.status_sync() == wt.WT_EQUERY
