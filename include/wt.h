@@ -291,8 +291,7 @@ wt_status wt_export(wt_tree tree, uint32_t level, uint32_t what, void* h_dst, ui
  *          x0) / 4) + R_t, the residuals R_t (WT_EXPORT_RESID0/1) fitted on
  *          the GPU by least squares to the positions of the segment's b-bits;
  *          a rank is predicted from its two knots (ka, xa), (kb, xb) as xa +
- *          min(trunc(f(k - ka) * (f(xb - xa) / f(kb - ka))), xb - xa), each
- *          step a correctly rounded FP32 operation.
+ *          floor((k - ka) (xb - xa) / (kb - ka)), exact integer arithmetic.
  *   mode 2 (MLP): the fraction u = (k - 4 m K) / (segment length) is mapped to
  *          u + g(u), g a 1 -> 32 -> 1 ReLU network in FP32 per (level, b), trained
  *          on the GPU with Adam on (u, position fraction) pairs drawn from the

@@ -171,10 +171,9 @@ def predict_mlp_f32_all(k, k0, k1, x0, x1, P):
 # ((m+1) A K, S_b[A (m+1)]), or (count_b + 1, size) for the last segment.
 # Knot t (t = 0..4) sits at rank kappa_t = k0 + floor(t (k1 - k0) / 4)
 # (kappa_4 = k1) and position x0 + floor(t (x1 - x0) / 4) + R_t, with the
-# fitted residuals R_1..3 (bits, signed) and R_0 = R_4 = 0.  A rank is
-# predicted from the two knots around it, (ka, xa) and (kb, xb), as xa +
-# min(trunc(f(k - ka) * (f(xb - xa) / f(kb - ka))), xb - xa) with f the
-# rounding to float32 and each product and quotient rounded to float32.
+# fitted residuals R_1..3 (bits, signed) and R_0 = R_4 = 0.  A rank k is
+# predicted from the two knots around it, (ka, xa) and (kb, xb) with ka <= k
+# < kb, as xa + floor((k - ka) (xb - xa) / (kb - ka)) in exact integers.
 # Segments shorter than four ranks interpolate between the anchors alone.
 # --------------------------------------------------------------------------
 
@@ -199,22 +198,19 @@ def spline_knots(kn, R):
     return kap, xi
 
 
-def interp_f32(ka, kb, xa, xb, k):
-    """xa + min(trunc(f(k - ka) * (f(xb - xa) / f(kb - ka))), xb - xa), float32 steps."""
-    f = np.float32
-    slope = f(f(xb - xa) / f(kb - ka))
-    off = int(f(f(k - ka) * slope))
-    return xa + min(off, xb - xa)
+def interp(ka, kb, xa, xb, k):
+    """xa + floor((k - ka) (xb - xa) / (kb - ka)), Python integers."""
+    return xa + ((k - ka) * (xb - xa)) // (kb - ka)
 
 
 def predict_spline(kn, R, k):
     """Prediction for rank k (knots must be non-decreasing)."""
     k0, k1, x0, x1 = kn
     if k1 - k0 < 4:
-        return interp_f32(k0, k1, x0, x1, k)
+        return interp(k0, k1, x0, x1, k)
     kap, xi = spline_knots(kn, R)
     t = int(k >= kap[1]) + int(k >= kap[2]) + int(k >= kap[3])
-    return interp_f32(kap[t], kap[t + 1], xi[t], xi[t + 1], k)
+    return interp(kap[t], kap[t + 1], xi[t], xi[t + 1], k)
 
 
 def predict_spline_all(k, k0, k1, x0, x1, R):
@@ -233,10 +229,7 @@ def predict_spline_all(k, k0, k1, x0, x1, R):
     kb = np.where(short, k1, kap_a[t + 1, idx])
     xa = np.where(short, x0, xi_a[t, idx])
     xb = np.where(short, x1, xi_a[t + 1, idx])
-    f = np.float32
-    slope = ((xb - xa).astype(f) / np.maximum(kb - ka, 1).astype(f)).astype(f)
-    off = ((k - ka).astype(f) * slope).astype(f).astype(np.int64)
-    return xa + np.minimum(off, xb - xa)
+    return xa + ((k - ka) * (xb - xa)) // np.maximum(kb - ka, 1)
 
 
 def segment_anchor_all(samples, total, size, K, A=ANCHOR):

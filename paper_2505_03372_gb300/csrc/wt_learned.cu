@@ -14,9 +14,10 @@
 // floor(t (k1 - k0) / 4) and position x0 + floor(t (x1 - x0) / 4) + R_t, the
 // residuals R_1..3 fitted on the GPU by least squares to the positions of the
 // segment's b-bits (the hat-function basis gives a 3x3 system per segment; R_0
-// = R_4 = 0); a rank is predicted by interpolating between the two knots
-// around it with two correctly rounded FP32 operations.  Untrained (R = 0) it
-// is the line through the anchors.  Nothing in a prediction divides integers.  MLP: the fraction u = (k - k0) / (k1 - k0) is
+// = R_4 = 0); a rank k is predicted by interpolating between the two knots
+// (ka, xa), (kb, xb) around it, xa + floor((k - ka) (xb - xa) / (kb - ka)),
+// exact in integers (a shift in every full segment).  Untrained (R = 0) it is
+// the line through the anchors.  MLP: the fraction u = (k - k0) / (k1 - k0) is
 // mapped to u + g(u), g a 1 -> 32 -> 1 ReLU network in FP32 shared by all
 // segments of a (level, b), trained with Adam on the GPU (g starts at 0, the
 // line through the anchors).
@@ -69,26 +70,32 @@ __device__ __forceinline__ uint64_t knot_rank(const Seg& g, uint32_t t) { return
 // untrained knot position t: t quarters of the way from x0 to x1
 __device__ __forceinline__ uint64_t knot_base(const Seg& g, uint32_t t) { return g.x0 + ((t * (g.x1 - g.x0)) >> 2); }
 
-// xa + trunc((k - ka) * ((xb - xa) / (kb - ka))) in correctly rounded FP32, at most xb - xa
-__device__ __forceinline__ uint64_t interp(uint64_t ka, uint64_t kb, uint64_t xa, uint64_t xb, uint64_t k) {
-    const float slope = __fdiv_rn((float)(xb - xa), (float)(kb - ka));
-    const uint64_t off = (uint64_t)__fmul_rn((float)(k - ka), slope);
-    return xa + (off < xb - xa ? off : xb - xa);
+// xa + floor((k - ka) (xb - xa) / (kb - ka)) for ka <= k < kb, exact in 64-bit
+// integers ((k - ka) < 2^14 and xb - xa < 2^48).  Knots of a full segment are
+// K = 2^kl ranks apart, so the division is a shift there; only the last
+// segment of a (level, b) divides.
+__device__ __forceinline__ uint64_t interp(uint64_t ka, uint64_t kb, uint64_t xa, uint64_t xb, uint64_t k,
+                                           uint32_t kl) {
+    const uint64_t d = kb - ka, prod = (k - ka) * (xb - xa);
+    return xa + (d == (1ull << kl) ? (prod >> kl) : prod / d);
 }
 
 // Fitted-knot prediction for rank k of segment g; R[t - 1] (bits) for knots t = 1..3.
 // Knot positions are non-decreasing and inside [x0, x1] (the fit guarantees it).
-// No integer division: the knots are quarters of the segment, the
-// interpolation between two knots is two FP32 operations.
-__device__ __forceinline__ uint64_t predict_knots(const Seg& g, const int64_t R[kKnots], uint64_t k) {
-    if (g.k1 - g.k0 < 4) return interp(g.k0, g.k1, g.x0, g.x1, k);
+// The knots are quarters of the segment; the interpolation between the two
+// knots around k is exact integer arithmetic.
+__device__ __forceinline__ uint64_t predict_knots(const Seg& g, const int64_t R[kKnots], uint64_t k, uint32_t kl) {
+    if (g.k1 - g.k0 < 4) return interp(g.k0, g.k1, g.x0, g.x1, k, kl);
     const uint64_t k1r = knot_rank(g, 1), k2r = knot_rank(g, 2), k3r = knot_rank(g, 3);
     const uint32_t t = (k >= k1r) + (k >= k2r) + (k >= k3r);
     const uint64_t ka = t == 0 ? g.k0 : (t == 1 ? k1r : (t == 2 ? k2r : k3r));
     const uint64_t kb = t == 0 ? k1r : (t == 1 ? k2r : (t == 2 ? k3r : g.k1));
-    const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)knot_base(g, t) + R[t - 1]);
-    const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)knot_base(g, t + 1) + R[t]);
-    return interp(ka, kb, xa, xb, k);
+    // R indexed by selects (a computed index would put R in local memory)
+    const int64_t ra = t == 1 ? R[0] : (t == 2 ? R[1] : R[2]);
+    const int64_t rb = t == 0 ? R[0] : (t == 1 ? R[1] : R[2]);
+    const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)knot_base(g, t) + ra);
+    const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)knot_base(g, t + 1) + rb);
+    return interp(ka, kb, xa, xb, k, kl);
 }
 
 // g(u) = b2 + sum_j w2[j] * relu(w1[j] * u + b1[j]); P = {w1[32], b1[32], w2[32], b2}
@@ -118,8 +125,8 @@ __device__ __forceinline__ void unpack_resid(const ushort4 r, uint32_t rsh, int6
 }
 
 __device__ __forceinline__ uint64_t predict(uint32_t mode, const Seg& g, const int64_t R[kKnots], uint64_t k,
-                                            const float* P) {
-    return mode == kLearnMlp ? predict_mlp(g, k, P) : predict_knots(g, R, k);
+                                            const float* P, uint32_t kl) {
+    return mode == kLearnMlp ? predict_mlp(g, k, P) : predict_knots(g, R, k, kl);
 }
 
 // ---------------------------------------------------------------------------
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(256) learn_scan_kernel(const __grid_constant__
                         if (a.mode == kLearnPla && a.rec[b]) unpack_resid(a.rec[b][m], a.rsh[b], R);
                     }
                     if (a.eps[b]) {
-                        const uint64_t pr = predict(a.mode, g, R, k, P);
+                        const uint64_t pr = predict(a.mode, g, R, k, P, a.kl);
                         const uint64_t e = pr > pos ? pr - pos : pos - pr;
                         const uint32_t e32 = e > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)e;
                         cur_max = e32 > cur_max ? e32 : cur_max;
@@ -545,7 +552,7 @@ __device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const Lea
         for (int q = 0; q < NQ; q++) {
             int64_t R[kKnots];
             unpack_resid(r[q], ld.rsh[l][b[q]], R);
-            const uint64_t p = predict(ld.mode, g[q], R, k[q], mlp_s + (2 * l + b[q]) * kMlpParams);
+            const uint64_t p = predict(ld.mode, g[q], R, k[q], mlp_s + (2 * l + b[q]) * kMlpParams, kl);
             const uint64_t e = (uint64_t)r[q].w << ld.esh[l][b[q]];
             const uint64_t hi = umin64(p + e, lv.size - 1);
             const uint64_t lo = umin64(p > e ? p - e : 0ull, hi);  // lo <= hi <= size - 1
@@ -585,10 +592,12 @@ __device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const Lea
 constexpr int kLqThreads = 256;
 
 // ORD: the queries were sorted by walk key; idx[k] is query k's original slot.
-// NQ = 2 for deep trees, as for the sampled select; the register bounds (40
-// and 77 per thread) are the largest occupancies without spills.
+// NQ = 2 for deep trees, as for the sampled select.  Bounds: 48 registers for
+// one query per thread, 64 for two (a few spilled words cost less than the
+// fourth CTA per SM gains: 36.9 -> 35.4 ms for 10^8 PLA selects on a 16-level
+// tree).
 template <bool ORD, int NQ>
-__global__ void __launch_bounds__(kLqThreads, NQ == 1 ? 6 : 3) select_learned_kernel(
+__global__ void __launch_bounds__(kLqThreads, NQ == 1 ? 5 : 4) select_learned_kernel(
     const __grid_constant__ TreeDesc t, const __grid_constant__ LearnedDesc ld, const uint32_t* __restrict__ qc,
     const uint64_t* __restrict__ qj, const uint32_t* __restrict__ idx, uint64_t* __restrict__ out, uint64_t q) {
     extern __shared__ float mlp_s[];

@@ -543,11 +543,11 @@ def test_spline_predictor_by_hand_and_brute_force():
     assert mlp.predict_spline(kn, R, 6) == 57    # 45 + trunc(2 * 6.25)
     assert mlp.predict_spline(kn, R, 13) == 130
     assert mlp.predict_spline((0, 3, 10, 16), [99, 99, 99], 2) == 14  # short segment: the anchors only
-    # float32 steps: slope 1 / 3 rounds to 0.3333333432674408, and 3 * that rounds to 1.0 exactly
-    assert mlp.interp_f32(0, 3, 0, 1, 3) == 1
-    assert mlp.interp_f32(0, 3, 100, 101, 2) == 100  # 2 / 3 -> 0
-    # the offset is capped at the knot distance even when float32 rounds up
-    assert mlp.interp_f32(0, 1, 0, (1 << 25) - 1, 1) == (1 << 25) - 1
+    # exact integer interpolation: floor of the rational, no float rounding
+    assert mlp.interp(0, 3, 0, 1, 2) == 0            # 2 / 3 -> 0
+    assert mlp.interp(0, 3, 100, 103, 2) == 102
+    assert mlp.interp(0, 4096, 0, 1 << 40, 4095) == (1 << 40) - (1 << 28)  # float32 would round this
+    assert mlp.interp(7, 10, 50, 50, 9) == 50        # flat knots
     rng = np.random.default_rng(3)
     bits = (rng.random(20000) < 0.3).astype(np.uint8)
     pos = np.flatnonzero(bits)
