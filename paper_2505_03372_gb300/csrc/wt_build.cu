@@ -400,15 +400,18 @@ __device__ __forceinline__ uint64_t lb_agg(uint64_t s) { return (s >> 2) & ((1u 
 __device__ __forceinline__ uint64_t lb_incl(uint64_t s) { return s >> 21; }
 
 
-// 32-bit shared-memory addressing for the byte / half / word scatter stores
-__device__ __forceinline__ void sts_elem(uint32_t addr, uint8_t v) {
-    asm volatile("st.shared.u8 [%0], %1;" ::"r"(addr), "h"((unsigned short)v) : "memory");
+// 32-bit shared-memory addressing for the byte / half / word scatter stores.
+// The value is a 32-bit register whose low 8 / 16 bits are stored: no
+// truncation instruction per element (the byte stores of one word pass w,
+// w >> 8, w >> 16, w >> 24; measured 0.734 -> 0.716 ms per u8 level pass).
+__device__ __forceinline__ void sts_b8(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.b8 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
-__device__ __forceinline__ void sts_elem(uint32_t addr, uint16_t v) {
-    asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+__device__ __forceinline__ void sts_b16(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
-__device__ __forceinline__ void sts_elem(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+__device__ __forceinline__ void sts_b32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 __device__ __forceinline__ uint4 lds_u128(uint32_t addr) {
     uint4 v;
@@ -467,21 +470,21 @@ __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V,
             const uint32_t I01 = ((b1 & s01) | (b0 & ~s01)) + __byte_perm(off, 0, 0x4140);
             const uint32_t I23 = ((b1 & s23) | (b0 & ~s23)) + __byte_perm(off, 0, 0x4342);
             const uint32_t ob = ABS ? 0u : out;
-            if (FULL || jw + 0 < count) sts_elem(ob + (I01 & 0xFFFFu), (T)w);
-            if (FULL || jw + 1 < count) sts_elem(ob + (I01 >> 16), (T)(w >> 8));
-            if (FULL || jw + 2 < count) sts_elem(ob + (I23 & 0xFFFFu), (T)(w >> 16));
-            if (FULL || jw + 3 < count) sts_elem(ob + (I23 >> 16), (T)(w >> 24));
+            if (FULL || jw + 0 < count) sts_b8(ob + (I01 & 0xFFFFu), w);
+            if (FULL || jw + 1 < count) sts_b8(ob + (I01 >> 16), w >> 8);
+            if (FULL || jw + 2 < count) sts_b8(ob + (I23 & 0xFFFFu), w >> 16);
+            if (FULL || jw + 3 < count) sts_b8(ob + (I23 >> 16), w >> 24);
         } else if (W == 2) {
             const uint32_t bb = (m >> (2 * i)) & 3u;
             const uint32_t sel = (bb & 1u ? 0x0000FFFFu : 0u) | (bb & 2u ? 0xFFFF0000u : 0u);
             // second element: ones before it if it is a one, zeros before it otherwise
             const uint32_t off = ((bb ^ (bb >> 1)) & 1u) ? 0u : 0x00010000u;
             const uint32_t I = ((b1 & sel) | (b0 & ~sel)) + off;
-            if (FULL || jw + 0 < count) sts_elem(out + 2 * (I & 0xFFFFu), (T)w);
-            if (FULL || jw + 1 < count) sts_elem(out + 2 * (I >> 16), (T)(w >> 16));
+            if (FULL || jw + 0 < count) sts_b16(out + 2 * (I & 0xFFFFu), w);
+            if (FULL || jw + 1 < count) sts_b16(out + 2 * (I >> 16), w >> 16);
         } else {
             const uint32_t bit = (m >> i) & 1u;
-            if (FULL || jw < count) sts_elem(out + 4 * ((bit ? b1 : b0) & 0xFFFFu), (T)w);
+            if (FULL || jw < count) sts_b32(out + 4 * ((bit ? b1 : b0) & 0xFFFFu), w);
         }
     }
 }
@@ -862,14 +865,19 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             const uint32_t nv = count - t * 64;
             const uint64_t valid = nv >= 64 ? ~0ull : ((1ull << nv) - 1ull);
             const uint64_t z = ~x & valid;
-            const uint64_t g1 = E + pre, g0 = R0 + (uint64_t)t * 64 - pre;  // ones / zeros before the word
             const uint32_t c1 = __popcll(x), c0 = __popcll(z);
+            // a multiple of K falls in the word iff the count before it, mod K,
+            // overflows there (32-bit test; measured 0.716 -> 0.707 ms per u8 pass)
+            const uint32_t km = (1u << kl) - 1u;
+            const bool x1 = (((uint32_t)E + pre) & km) + c1 > km;
+            const bool x0 = (((uint32_t)R0 + t * 64u - pre) & km) + c0 > km;
+            const uint64_t g1 = E + pre, g0 = R0 + (uint64_t)t * 64 - pre;  // ones / zeros before the word
             const uint64_t base = t0 + (uint64_t)t * 64;
-            if (((g1 + c1) >> kl) != (g1 >> kl)) {
+            if (x1) {
                 const uint64_t m = (g1 + c1) >> kl;
                 if (m < a.n_s1) a.s1[m] = base + select_in_word(x, (uint32_t)((m << kl) - g1));
             }
-            if (((g0 + c0) >> kl) != (g0 >> kl)) {
+            if (x0) {
                 const uint64_t m = (g0 + c0) >> kl;
                 if (m < a.n_s0) a.s0[m] = base + select_in_word(z, (uint32_t)((m << kl) - g0));
             }
