@@ -85,6 +85,22 @@ __device__ __forceinline__ uint64_t interp(uint64_t ka, uint64_t kb, uint64_t xa
 // The knots are quarters of the segment; the interpolation between the two
 // knots around k is exact integer arithmetic.
 __device__ __forceinline__ uint64_t predict_knots(const Seg& g, const int64_t R[kKnots], uint64_t k, uint32_t kl) {
+    if (g.k1 - g.k0 == (4ull << kl)) {
+        // a full segment (all but the last of a level and b): knots K ranks
+        // apart, so t = (k - k0) / K and the interpolation divides by K; the
+        // same integers as the general form below, with shifts for divisions
+        const uint32_t off = (uint32_t)(k - g.k0);
+        const uint32_t t = off >> kl;
+        const uint64_t span = g.x1 - g.x0;
+        const int64_t ra = t == 1 ? R[0] : (t == 2 ? R[1] : R[2]);
+        const int64_t rb = t == 0 ? R[0] : (t == 1 ? R[1] : R[2]);
+        const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)(g.x0 + ((t * span) >> 2)) + ra);
+        const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)(g.x0 + (((t + 1) * span) >> 2)) + rb);
+        const uint64_t dx = xb - xa;
+        const uint32_t dk = off & ((1u << kl) - 1u);  // k - ka < K
+        const uint64_t prod = dx < (1ull << 32) ? (uint64_t)dk * (uint32_t)dx : (uint64_t)dk * dx;
+        return xa + (prod >> kl);
+    }
     if (g.k1 - g.k0 < 4) return interp(g.k0, g.k1, g.x0, g.x1, k, kl);
     const uint64_t k1r = knot_rank(g, 1), k2r = knot_rank(g, 2), k3r = knot_rank(g, 3);
     const uint32_t t = (k >= k1r) + (k >= k2r) + (k >= k3r);
