@@ -609,7 +609,37 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
         uint4 V = in4[g * 32 + lane];
         const uint32_t j0 = g * GE + lane * VEPL;
         uint32_t wv[4] = {V.x, V.y, V.z, V.w};
-        if (ENCODE && W == 1 && a.ctab_n == 256) {
+        if (ENCODE && W == 1 && a.swar_codes) {
+            // byte symbols, sigma <= 128 with at most three segments: the code
+            // of a symbol in segment i is A_i + ((s & (2^e_i - 1)) << sh_i)
+            // (closed form of `encode`), four bytes at a time.  Segment i
+            // starts at P_i; a byte is in segment i or later iff s + (128 -
+            // P_i) sets its bit 7 (s < 128, so no carry leaves a byte; the
+            // bytes past a ragged tile's end carry only into higher bytes,
+            // which are past the end too).
+            const uint32_t L = a.cp.L, r = a.cp.r;
+            auto seg = [&](uint32_t x, uint32_t i) {
+                const uint32_t e = a.cp.e[i];
+                const uint32_t len = (i + 1 == r) ? i + e : i + 1 + e;
+                const uint32_t add = ((1u << i) - 1u) << (L - i);
+                return ((x & (((1u << e) - 1u) * 0x01010101u)) << (L - len)) + add * 0x01010101u;
+            };
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const uint32_t x = wv[i];
+                uint32_t code = seg(x, 0);
+#pragma unroll
+                for (uint32_t k = 1; k < 3; k++) {
+                    if (k < r) {
+                        const uint32_t g = (x + (128u - (uint32_t)a.cp.P[k]) * 0x01010101u) & 0x80808080u;
+                        const uint32_t m = (g >> 7) * 0xFFu;
+                        code = (code & ~m) | (seg(x, k) & m);
+                    }
+                }
+                wv[i] = code;
+            }
+            in4[g * 32 + lane] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        } else if (ENCODE && W == 1 && a.ctab_n == 256) {
             // byte symbols: a 256-entry table, no bounds tests (entries past
             // sigma and past the tile's end are never used)
 #pragma unroll
@@ -1397,7 +1427,11 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.pshift = matrix ? 32 : L - l;  // the matrix: every tile lies in the level's one node
             a.k_log2 = k_log2;
             a.cp = cp;
-            a.ctab_n = w == 1 ? 256u : ((uint64_t)sigma * w <= kCodeTableBytes) ? sigma : 0;
+            // level 0 re-encodes bytes of a small alphabet with few segments
+            // arithmetically (measured faster than the code table), others
+            // through a code table in shared memory when it fits
+            a.swar_codes = (w == 1 && !cp.pow2 && sigma <= 128 && cp.r <= 3) ? 1u : 0u;
+            a.ctab_n = a.swar_codes ? 0u : w == 1 ? 256u : ((uint64_t)sigma * w <= kCodeTableBytes) ? sigma : 0;
             // Tile prefixes: from the counts the previous pass gathered, else by look-back.
             if (have_excl) a.tile_excl = texcl;
             else WT_CUDA_TRY(cudaMemsetAsync(state, 0, a.ntiles * 8, s));
