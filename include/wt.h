@@ -52,7 +52,9 @@ typedef enum {
     WT_ECUDA = 4,       /* a CUDA runtime call failed (launch error, ...) */
     WT_EQUERY = 5,      /* some query argument was out of range; that output holds a sentinel */
     WT_ETIMEOUT = 6,    /* a bounded device-side wait gave up; results of that call are not valid */
-    WT_EUNSUPPORTED = 7 /* operation not available for this tree (e.g. no trained select model) */
+    WT_EUNSUPPORTED = 7, /* operation not available for this tree (e.g. no trained select model) */
+    WT_EBOUNDS = 8      /* debug library only (libwt_debug.so): a query walk's load failed its
+                           bounds check and was skipped; results of that call are not valid */
 } wt_status;
 
 /*
@@ -448,7 +450,10 @@ wt_status wt_bitvector_support_static(const uint64_t* d_words, uint64_t nbits, u
  *  select:  d_out[k] = position of the d_j[k]-th (1-based) bit equal to b
  *           (b = 0 or 1) for 1 <= d_j[k] <= count_b.
  * Out-of-range queries yield UINT64_MAX and OR 1 << WT_EQUERY into *d_status
- * (optional device word).  Asynchronous on `stream`.  Host-detectable errors
+ * (optional device word).  In the debug library a load outside the arrays'
+ * documented lengths is skipped and ORs 1 << WT_EBOUNDS into *d_status (for
+ * example, select with samples that point past nbits).  Asynchronous on
+ * `stream`.  Host-detectable errors
  * (null or non-device pointers, nbits == 0, b > 1, sample_k not a power of two
  * in [256, 2^20], ones > nbits) return WT_EINVAL before any work is queued.
  */

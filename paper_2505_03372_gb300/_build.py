@@ -1,7 +1,9 @@
-"""Compile libwt.so (sm_103a) in-tree with nvcc.
+"""Compile libwt.so (sm_103a) in-tree with nvcc, and its debug twin
+libwt_debug.so (the same sources with WT_DEBUG_BOUNDS=1: bounds-checked walk
+loads that report WT_EBOUNDS).
 
-Each translation unit under csrc/ is compiled in parallel into _build/, then
-linked into paper_2505_03372_gb300/libwt.so.  No CMake; one -gencode.
+Each translation unit under csrc/ is compiled in parallel into _build/ (and
+_build/debug/), then linked.  No CMake; one -gencode.
 """
 from __future__ import annotations
 
@@ -38,17 +40,31 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OBJDIR, exist_ok=True)
+VARIANTS = {
+    # name: (library, object directory, extra nvcc flags)
+    "release": (LIB, OBJDIR, []),
+    # every load of a query walk checked against its array's length (WT_EBOUNDS)
+    "debug": (os.path.join(HERE, "libwt_debug.so"), os.path.join(OBJDIR, "debug"), ["-DWT_DEBUG_BOUNDS=1"]),
+}
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), variants=("release", "debug")) -> str:
+    """Compile the requested variants (translation units of all of them in one
+    parallel pool) and link each library; returns the release library's path."""
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "wt.h")]
     jobs = []
-    objs = []
-    for src in SOURCES:
-        s = os.path.join(CSRC, src)
-        o = os.path.join(OBJDIR, src.replace(".cu", ".o"))
-        objs.append(o)
-        if force or _stale(o, [s] + hdrs):
-            jobs.append([nvcc(), *_flags(), *extra_flags, "-c", s, "-o", o])
+    links = []
+    for v in variants:
+        lib, objdir, vflags = VARIANTS[v]
+        os.makedirs(objdir, exist_ok=True)
+        objs = []
+        for src in SOURCES:
+            s = os.path.join(CSRC, src)
+            o = os.path.join(objdir, src.replace(".cu", ".o"))
+            objs.append(o)
+            if force or _stale(o, [s] + hdrs):
+                jobs.append([nvcc(), *_flags(), *vflags, *extra_flags, "-c", s, "-o", o])
+        links.append((lib, objs))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -58,12 +74,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stdout + r.stderr)
 
     if jobs:
-        with concurrent.futures.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(jobs), max(os.cpu_count() or 1, 1))) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
+    for lib, objs in links:
+        if force or jobs or _stale(lib, objs):
+            tmp = lib + ".tmp%d" % os.getpid()
+            run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+            os.replace(tmp, lib)
     return LIB
 
 

@@ -14,9 +14,11 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libwt.so")
+# WT_LIB_VARIANT=debug loads libwt_debug.so: the same library with every load of
+# a query walk bounds-checked (a failed check reports WT_EBOUNDS)
+LIB_PATH = os.path.join(_HERE, "libwt_debug.so" if os.environ.get("WT_LIB_VARIANT") == "debug" else "libwt.so")
 
-WT_OK, WT_EINVAL, WT_ESYMBOL, WT_ENOMEM, WT_ECUDA, WT_EQUERY, WT_ETIMEOUT, WT_EUNSUPPORTED = range(8)
+WT_OK, WT_EINVAL, WT_ESYMBOL, WT_ENOMEM, WT_ECUDA, WT_EQUERY, WT_ETIMEOUT, WT_EUNSUPPORTED, WT_EBOUNDS = range(9)
 EXPORT_BITS, EXPORT_L1, EXPORT_L2, EXPORT_S0, EXPORT_S1, EXPORT_C, EXPORT_CODES, EXPORT_LENS, EXPORT_NODES = range(9)
 EXPORT_EPS0, EXPORT_EPS1, EXPORT_MLP, EXPORT_RESID0, EXPORT_RESID1 = 9, 10, 11, 12, 13
 ANCHOR = 4  # select samples per anchor segment of the learned select
@@ -606,7 +608,7 @@ class Bitvector:
         torch.cuda.synchronize()
         v = int(self.status.item())
         self.status.zero_()
-        for code in (WT_ETIMEOUT, WT_EQUERY):
+        for code in (WT_EBOUNDS, WT_ETIMEOUT, WT_EQUERY):
             if v & (1 << code):
                 return code
         return WT_OK

@@ -83,6 +83,7 @@ wt_status run_alphabet(const void* d_symbols, uint64_t n, void* d_out, uint32_t*
     lv.s1 = reinterpret_cast<uint64_t*>(M + o_s1);
     lv.size = nbits;
     uint32_t* status = reinterpret_cast<uint32_t*>(M + o_st);
+    lv.status = status;
     wt_status st = WT_OK;
     uint64_t sigma = 0;
     if (cudaMemsetAsync(mem, 0, total, s) != cudaSuccess) st = WT_ECUDA;

@@ -228,6 +228,7 @@ const char* wt_status_str(wt_status s) {
         case WT_EQUERY: return "WT_EQUERY: query argument out of range";
         case WT_ETIMEOUT: return "WT_ETIMEOUT: bounded device wait gave up";
         case WT_EUNSUPPORTED: return "WT_EUNSUPPORTED: operation not available";
+        case WT_EBOUNDS: return "WT_EBOUNDS: a query walk's load failed its bounds check (debug library)";
     }
     return "unknown wt_status";
 }
@@ -466,6 +467,7 @@ wt_status wt_status_sync(wt_tree tree, wt_stream stream) {
     if (bits) {
         if (cudaMemset(tree->desc.status, 0, 4) != cudaSuccess) return WT_ECUDA;
     }
+    if (bits & kStBounds) return WT_EBOUNDS;
     if (bits & kStTimeout) return WT_ETIMEOUT;
     if (bits & kStSymbol) return WT_ESYMBOL;
     if (bits & kStQuery) return WT_EQUERY;

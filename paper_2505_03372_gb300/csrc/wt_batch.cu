@@ -316,6 +316,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
             v.l2 = reinterpret_cast<uint16_t*>(M + to[i].l2[l]);
             v.s0 = reinterpret_cast<uint64_t*>(M + to[i].s0[l]);
             v.s1 = reinterpret_cast<uint64_t*>(M + to[i].s1[l]);
+            v.status = ti.status;
             LevelPassArgs& a = lpa[(size_t)l * ntrees + i];
             a.src = l == 0 ? h_symbols[i] : static_cast<const void*>(M + to[i].tbuf[(l - 1) & 1]);
             a.dst = (l + 1 < L) ? static_cast<void*>(M + to[i].tbuf[l & 1]) : nullptr;
@@ -407,6 +408,7 @@ wt_status wt_batch_status_sync(wt_batch batch, wt_stream stream) {
     uint32_t bits = 0;
     for (uint32_t v : st) bits |= v;
     if (bits && cudaMemset(batch->dev.status_pool, 0, st.size() * 4) != cudaSuccess) return WT_ECUDA;
+    if (bits & kStBounds) return WT_EBOUNDS;
     if (bits & kStTimeout) return WT_ETIMEOUT;
     if (bits & kStSymbol) return WT_ESYMBOL;
     if (bits & kStQuery) return WT_EQUERY;

@@ -69,6 +69,7 @@ extern "C" wt_status wt_bitvector_rank(const uint64_t* d_words, uint64_t nbits, 
     lv.l1 = d_l1;
     lv.l2 = d_l2;
     lv.size = nbits;
+    lv.status = d_status;
     ProfScope ps("bv_rank", stream);
     bv_rank_kernel<<<bv_grid(bv_rank_kernel, q), kBvThreads, 0, stream>>>(lv, d_i, d_out, q, d_status);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
@@ -94,6 +95,7 @@ extern "C" wt_status wt_bitvector_select(const uint64_t* d_words, uint64_t nbits
     lv.s1 = d_s1;
     lv.size = nbits;
     lv.ones = ones;
+    lv.status = d_status;
     ProfScope ps(b ? "bv_select1" : "bv_select0", stream);
     bv_select_kernel<<<bv_grid(bv_select_kernel, q), kBvThreads, 0, stream>>>(lv, b, k_log2, d_j, d_out, q,
                                                                               d_status);

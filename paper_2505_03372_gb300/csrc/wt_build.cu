@@ -1370,6 +1370,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
         d.s1 = reinterpret_cast<uint64_t*>(M + lay[l].s1);
         d.size = t->level_size[l];
         d.ones = t->level_ones[l];
+        d.status = t->desc.status;
     }
 
     // ---- level passes ----

@@ -173,6 +173,7 @@ struct LevelDesc {
     const uint64_t* s1;     // floor(ones/K) + 1 entries, s1[0] = 0
     uint64_t size;
     uint64_t ones;
+    uint32_t* status;  // where a debug build reports a failed bounds check (may be null)
 };
 
 // Everything a query kernel needs, passed by value as a __grid_constant__.
@@ -256,6 +257,43 @@ __device__ __forceinline__ void ldg_nc_v4(const uint64_t* p, uint64_t& a, uint64
     asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
 }
 
+// Debug builds (compiled with WT_DEBUG_BOUNDS=1: libwt_debug.so) check the
+// index of every load a query walk makes against the array's length above
+// (words: the 512-bit blocks up to the one holding position size, plus the
+// node table's 2^L - 1 slots); a failed check sets WT_EBOUNDS in the status
+// word and the load is skipped (its value is taken as 0).  Release builds
+// compile the checks out.
+#ifndef WT_DEBUG_BOUNDS
+#define WT_DEBUG_BOUNDS 0
+#endif
+constexpr uint32_t kStBounds = 1u << WT_EBOUNDS;
+
+__device__ __forceinline__ bool dbg_in(bool in_range, uint32_t* status) {
+#if WT_DEBUG_BOUNDS
+    if (!in_range) {
+        if (status) atomicOr(status, kStBounds);
+        return false;
+    }
+#endif
+    return true;
+}
+__device__ __forceinline__ uint64_t lv_nl1(const LevelDesc& lv) { return (lv.size >> 16) + 1; }
+__device__ __forceinline__ uint64_t lv_nl2(const LevelDesc& lv) { return (lv.size >> 9) + 1; }
+__device__ __forceinline__ uint64_t lv_nwords(const LevelDesc& lv) { return ((lv.size >> 9) + 1) * 8; }
+__device__ __forceinline__ uint64_t lv_nsamples(const LevelDesc& lv, uint32_t b, uint32_t k_log2) {
+    return ((b ? lv.ones : lv.size - lv.ones) >> k_log2) + 1;
+}
+// checked loads: words[i .. i + 3] as one 32-byte load, and one element
+__device__ __forceinline__ void ld_words4(const LevelDesc& lv, uint64_t i, uint64_t& a, uint64_t& b, uint64_t& c,
+                                          uint64_t& d) {
+    if (dbg_in(i + 3 < lv_nwords(lv), lv.status)) ldg_nc_v4(lv.words + i, a, b, c, d);
+    else a = b = c = d = 0;
+}
+template <typename T>
+__device__ __forceinline__ T ld_chk(const T* p, uint64_t i, uint64_t n, uint32_t* status) {
+    return dbg_in(i < n, status) ? __ldg(p + i) : T(0);
+}
+
 // Binary rank_1 (Algorithm 1 with 64-bit words): ones in B_l[0, pos), and the
 // bit at pos (needed by access, returned with the rank as in Section 5.2.1).
 // Reads the L1 and L2 counters and the words of pos's 512-bit block up to pos.
@@ -263,12 +301,11 @@ __device__ __forceinline__ uint64_t rank1_bit(const LevelDesc& lv, uint64_t pos,
     const uint64_t blk = pos >> 9;
     const uint32_t wi = (uint32_t)(pos >> 6) & 7u;
     const uint32_t bi = (uint32_t)pos & 63u;
-    const uint64_t* base = lv.words + (blk << 3);  // 64-byte aligned
     uint64_t w[8];
-    ldg_nc_v4(base, w[0], w[1], w[2], w[3]);
+    ld_words4(lv, blk << 3, w[0], w[1], w[2], w[3]);  // 64-byte aligned block
     w[4] = w[5] = w[6] = w[7] = 0;
-    if (wi >= 4) ldg_nc_v4(base + 4, w[4], w[5], w[6], w[7]);
-    uint64_t r = __ldg(lv.l1 + (pos >> 16)) + (uint64_t)__ldg(lv.l2 + blk);
+    if (wi >= 4) ld_words4(lv, (blk << 3) + 4, w[4], w[5], w[6], w[7]);
+    uint64_t r = ld_chk(lv.l1, pos >> 16, lv_nl1(lv), lv.status) + (uint64_t)ld_chk(lv.l2, blk, lv_nl2(lv), lv.status);
     uint32_t c = 0;
 #pragma unroll
     for (uint32_t k = 0; k < 8; k++) {
@@ -288,7 +325,7 @@ __device__ __forceinline__ uint64_t rank1(const LevelDesc& lv, uint64_t pos) {
 }
 
 __device__ __forceinline__ uint32_t bit_at(const LevelDesc& lv, uint64_t pos) {
-    return (uint32_t)(__ldg(lv.words + (pos >> 6)) >> (pos & 63)) & 1u;
+    return (uint32_t)(ld_chk(lv.words, pos >> 6, lv_nwords(lv), lv.status) >> (pos & 63)) & 1u;
 }
 
 // Position (0..63) of the k-th (1-based) set bit of x; popc(x) >= k.  Binary
@@ -366,6 +403,10 @@ struct SelB {
     uint32_t kk, c2lo, kw;    // rank inside block i1; L2 counter at lo; rank inside the half
     uint32_t half;            // 0 or 4: which half
     bool ok;                  // the counters agree that the bit is in the range
+#if WT_DEBUG_BOUNDS
+    uint64_t dbg_nl2;         // L2 entries from block i1's first one to the end
+    uint32_t* dbg_status;
+#endif
 };
 
 
@@ -380,8 +421,9 @@ __device__ __forceinline__ void selb_range(SelB& s, const LevelDesc& lv, uint32_
     s.b = b;
     s.k = k;
     s.ok = true;
-    s.lo_pos = on ? __ldg(S + m) : 0ull;
-    s.hi_pos = on ? ((((m + 1) << k_log2) <= total) ? __ldg(S + m + 1) : lv.size - 1) : 0ull;
+    const uint64_t ns = lv_nsamples(lv, b, k_log2);
+    s.lo_pos = on ? ld_chk(S, m, ns, lv.status) : 0ull;
+    s.hi_pos = on ? ((((m + 1) << k_log2) <= total) ? ld_chk(S, m + 1, ns, lv.status) : lv.size - 1) : 0ull;
 }
 
 // a caller's window [lo, hi] instead of the samples (lo <= hi <= size - 1);
@@ -398,11 +440,11 @@ __device__ __forceinline__ void selb_window(SelB& s, uint32_t b, uint64_t k, uin
 __device__ __forceinline__ void selb_l1(SelB& s, const LevelDesc& lv) {
     const uint64_t hi1 = s.hi_pos >> 16;
     s.i1 = s.lo_pos >> 16;
-    s.c1 = __ldg(lv.l1 + s.i1);
+    s.c1 = ld_chk(lv.l1, s.i1, lv_nl1(lv), lv.status);
     s.lo = (uint32_t)(s.lo_pos >> 9) & 127u;
     s.hi = (s.i1 == hi1) ? ((uint32_t)(s.hi_pos >> 9) & 127u) : 127u;
     while (s.i1 < hi1) {  // last L1 block of the range with fewer than k b-bits before it
-        const uint64_t c1n = __ldg(lv.l1 + s.i1 + 1);
+        const uint64_t c1n = ld_chk(lv.l1, s.i1 + 1, lv_nl1(lv), lv.status);
         if ((s.b ? c1n : ((s.i1 + 1) << 16) - c1n) >= s.k) break;
         s.i1++;
         s.c1 = c1n;
@@ -410,7 +452,11 @@ __device__ __forceinline__ void selb_l1(SelB& s, const LevelDesc& lv) {
         s.hi = (s.i1 == hi1) ? ((uint32_t)(s.hi_pos >> 9) & 127u) : 127u;
     }
     s.L2 = lv.l2 + (s.i1 << 7);
-    s.c2lo = __ldg(s.L2 + s.lo);
+    s.c2lo = ld_chk(lv.l2, (s.i1 << 7) + s.lo, lv_nl2(lv), lv.status);
+#if WT_DEBUG_BOUNDS
+    s.dbg_nl2 = lv_nl2(lv) > (s.i1 << 7) ? lv_nl2(lv) - (s.i1 << 7) : 0;
+    s.dbg_status = lv.status;
+#endif
 }
 
 // b-bits of L1 block i1 before its L2 entry e (e relative to the block)
@@ -429,17 +475,17 @@ __device__ __forceinline__ void selb_rank(SelB& s) {
 
 __device__ __forceinline__ void selb_step(SelB& s) {
     const uint32_t mid = (s.lo + s.hi + 1) >> 1;
+#if WT_DEBUG_BOUNDS
+    const uint32_t v = ld_chk(s.L2, mid, s.dbg_nl2, s.dbg_status);
+#else
     const uint32_t v = __ldg(s.L2 + mid);
+#endif
     if (selb_l2count(s, mid, v) < s.kk) {
         s.lo = mid;
         s.c2lo = v;
     } else {
         s.hi = mid - 1;
     }
-}
-
-__device__ __forceinline__ const uint64_t* selb_block(const SelB& s, const LevelDesc& lv) {
-    return lv.words + (((s.i1 << 7) + s.lo) << 3);
 }
 
 // rank inside the chosen 512-bit block; its first 32-byte half
@@ -449,7 +495,7 @@ __device__ __forceinline__ void selb_words(SelB& s, const LevelDesc& lv) {
     if (CHECK) s.ok = s.ok && before < s.kk;
     s.kw = s.kk - before;
     s.half = 0;
-    ldg_nc_v4(selb_block(s, lv), s.w0, s.w1, s.w2, s.w3);
+    ld_words4(lv, ((s.i1 << 7) + s.lo) << 3, s.w0, s.w1, s.w2, s.w3);
 }
 
 // the second half instead, if the bit lies beyond the first
@@ -459,7 +505,7 @@ __device__ __forceinline__ void selb_half(SelB& s, const LevelDesc& lv, bool on)
     if (on && h < s.kw) {
         s.kw -= h;
         s.half = 4;
-        ldg_nc_v4(selb_block(s, lv) + 4, s.w0, s.w1, s.w2, s.w3);
+        ld_words4(lv, (((s.i1 << 7) + s.lo) << 3) + 4, s.w0, s.w1, s.w2, s.w3);
     }
 }
 

@@ -54,10 +54,11 @@ __device__ __forceinline__ Seg anchor_seg(const LevelDesc& lv, uint32_t b, uint6
     const uint32_t ka = kl + kAnchorLog2;
     Seg g;
     g.k0 = m << ka;
-    g.x0 = __ldg(S + (m << kAnchorLog2));
+    const uint64_t ns = lv_nsamples(lv, b, kl);
+    g.x0 = ld_chk(S, m << kAnchorLog2, ns, lv.status);
     if (((m + 1) << ka) <= total) {
         g.k1 = (m + 1) << ka;
-        g.x1 = __ldg(S + ((m + 1) << kAnchorLog2));
+        g.x1 = ld_chk(S, (m + 1) << kAnchorLog2, ns, lv.status);
     } else {
         g.k1 = total + 1;
         g.x1 = lv.size;
@@ -516,7 +517,9 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __
 
 // {start, r0} of node (l, p) from the node table (slots are 32-byte aligned)
 __device__ __forceinline__ ulonglong2 node_entry_sr(const TreeDesc& t, uint32_t l, uint64_t p) {
-    return ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + ((1ull << l) - 1 + p)));
+    const uint64_t slot = (1ull << l) - 1 + p;
+    if (!dbg_in(slot < (1ull << t.cp.L) - 1, t.status)) return make_ulonglong2(0, 0);
+    return ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + slot));
 }
 
 // Learned select of NQ queries in lockstep (see do_select_n): per level the
@@ -561,7 +564,9 @@ __device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const Lea
             if (on[q] && l > 0) ne[q] = node_entry_sr(t, (uint32_t)l - 1, (uint64_t)code[q] >> (cp.L - (uint32_t)l + 1));
             const uint64_t m = k[q] >> (kl + kAnchorLog2);
             g[q] = anchor_seg(lv, b[q], m, kl);
-            r[q] = ld.rec[l][b[q]][m];
+            // records: (count_b >> (log2 K + kAnchorLog2)) + 1 per (level, b)
+            r[q] = dbg_in(m < (lv_nsamples(lv, b[q], kl + kAnchorLog2)), lv.status) ? ld.rec[l][b[q]][m]
+                                                                                   : make_ushort4(0, 0, 0, 0);
         }
         SelB s[NQ];
 #pragma unroll

@@ -17,6 +17,7 @@ __device__ __forceinline__ ulonglong2 node_sr(const TreeDesc& t, const NodeCache
     // {start, r0} of node (l, p); slots are 32-byte aligned
     const uint64_t slot = (1ull << l) - 1 + p;
     if (slot < nc.slots) return nc.s[slot];
+    if (!dbg_in(slot < (1ull << t.cp.L) - 1, t.status)) return make_ulonglong2(0, 0);
     return ldg_nc_v2(reinterpret_cast<const uint64_t*>(t.nodes + slot));
 }
 

@@ -37,6 +37,16 @@ def test_every_declared_symbol_is_exported(libwt):
         assert hasattr(libwt, name), f"{name} declared in include/wt.h but not exported by libwt.so"
 
 
+def test_debug_library_exports_the_same_symbols(libwt):
+    """libwt_debug.so (bounds-checked walk loads) is built beside libwt.so and
+    exports every declared entry point too."""
+    dbg = ctypes.CDLL(os.path.join(ROOT, "paper_2505_03372_gb300", "libwt_debug.so"))
+    for name in sorted(_declared()):
+        assert hasattr(dbg, name), f"{name} not exported by libwt_debug.so"
+    dbg.wt_status_str.restype = ctypes.c_char_p
+    assert dbg.wt_status_str(8).decode().startswith("WT_EBOUNDS")
+
+
 def test_binding_lists_match_header(libwt):
     from paper_2505_03372_gb300 import binding
 
@@ -46,7 +56,7 @@ def test_binding_lists_match_header(libwt):
 def test_status_strings(libwt):
     from paper_2505_03372_gb300 import binding
 
-    for s in range(8):
+    for s in range(9):
         assert binding.status_str(s).startswith("WT_")
 
 
