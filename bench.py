@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' records")
     ap.add_argument("--n", type=int, default=None, help="override the workload's n (small profiling cases)")
     ap.add_argument("--query-scale", type=float, default=1.0, help="scale the query counts (small profiling cases)")
+    ap.add_argument("--overlap", action="store_true",
+                    help="sort the query batches on a second stream while the level passes run (measured: no "
+                         "gain on one GB300, the level pass already fills the SMs)")
     ap.add_argument("--layout", default="tree", choices=["tree", "matrix"],
                     help="level-wise wavelet tree (the paper's) or the wavelet matrix variant")
     return ap.parse_args()
@@ -291,7 +294,41 @@ def prepare(wl, rank):
     return sym, counts, q, outs, Q
 
 
-def make_step(wt, wl, layout):
+def make_step(wt, wl, layout, overlap=False):
+    """One step: build, then every query batch.  With `overlap`, the batches are
+    sorted by walk key (wt_order_queries) on a second stream while the build's
+    level passes run, and walked (wt_walk_ordered) on the build's stream after
+    it.  wt_build returns only after the histogram and C are done (it reads
+    the level sizes back), so all of the previous step's work has finished by
+    then and the orders never overlap another step."""
+    side = None
+    if overlap:
+        import torch
+
+        side = torch.cuda.Stream(priority=-1)  # the orders' CTAs go ahead of waiting level-pass CTAs
+
+    def step_overlap(sym_dev, qd, od):
+        import torch
+
+        t = wt.build(sym_dev, wl.sigma, sample_k=wl.sample_k, layout=layout)
+        main = torch.cuda.current_stream()
+        jobs = []
+        with torch.cuda.stream(side):
+            if "access_i" in qd:
+                jobs.append((t.order(wt.ORDER_ACCESS, qd["access_i"], stream=side), od["access"]))
+            if "rank_i" in qd:
+                jobs.append((t.order(wt.ORDER_RANK, qd["rank_i"], c=qd["rank_c"], stream=side), od["rank"]))
+            if "select_j" in qd:
+                jobs.append((t.order(wt.ORDER_SELECT, qd["select_j"], c=qd["select_c"], stream=side), od["select"]))
+            if "mixed_arg" in qd:
+                jobs.append((t.order(wt.ORDER_MIXED, qd["mixed_arg"], c=qd["mixed_c"], kinds=qd["mixed_kind"],
+                                     stream=side), od["mixed"]))
+        for o, out in jobs:
+            t.walk(o, out=out, stream=main)
+        for o, _ in jobs:
+            o.close(stream=main)
+        return t
+
     def step(sym_dev, qd, od):
         t = wt.build(sym_dev, wl.sigma, sample_k=wl.sample_k, layout=layout)
         if "access_i" in qd:
@@ -303,17 +340,17 @@ def make_step(wt, wl, layout):
         if "mixed_arg" in qd:
             t.query_mixed(qd["mixed_kind"], qd["mixed_c"], qd["mixed_arg"], out=od["mixed"])
         return t
-    return step
+    return step_overlap if overlap else step
 
 
-def measure(wt, wl, sym, q, outs, steps, warmup, layout, barrier=lambda: None, clocks_gpu=None):
+def measure(wt, wl, sym, q, outs, steps, warmup, layout, barrier=lambda: None, clocks_gpu=None, overlap=False):
     """Warm-up steps, then `steps` timed steps (build + every query batch) with
     CUDA events on the launching stream; per-kernel times from libwt's
     launch events.  Returns the step time, launches, kernel report and the
     level sizes."""
     import torch
 
-    step = make_step(wt, wl, layout)
+    step = make_step(wt, wl, layout, overlap)
     inf = None
     for _ in range(max(warmup, 3)):
         t = step(sym, q, outs)
@@ -496,7 +533,8 @@ def run_ours(args):
             dist.barrier()
 
     sym, counts, q, outs, Q = prepare(wl, rank)
-    m = measure(wt, wl, sym, q, outs, args.steps, args.warmup, layout, barrier, local if rank == 0 else None)
+    m = measure(wt, wl, sym, q, outs, args.steps, args.warmup, layout, barrier, local if rank == 0 else None,
+                overlap=args.overlap)
     ms_step = job_ms(m["ms"], dist)
     value = job_value(world, Q, ms_step)
     phases, roof, kern = analyse(wl, q, m, args.steps)
@@ -508,7 +546,9 @@ def run_ours(args):
         "config": {"workload": wl.describe() + ("; wavelet matrix layout" if args.layout == "matrix" else ""),
                    "queries_per_step_per_gpu": Q, "sample_k": wl.sample_k,
                    "l2_flush": "inputs larger than L2 (1 GiB symbols, ~0.9 GiB tree, 0.5 GiB queries)",
-                   "parallelism": "replicated build, sharded queries" if world > 1 else "1 GPU"},
+                   "parallelism": "replicated build, sharded queries" if world > 1 else "1 GPU",
+                   "query_order": "second stream, overlapping the level passes (wt_order_queries)" if args.overlap
+                   else "build's stream, after the build"},
         "phases": phases, "roofline": roof, "kernels": kern, "gpu_launches": m["launches"], "clocks": m["clk"],
         "parity": definitional_check(wl, sym, q, outs),
     }
@@ -545,7 +585,7 @@ def config_records(args, wt, workloads):
     for name in ("plain", "large_alphabet", "learned"):
         wl = workloads.WORKLOADS[name]
         sym, counts, q, outs, Q = prepare(wl, 0)
-        m = measure(wt, wl, sym, q, outs, max(3, min(args.steps, 5)), 3, wt.LAYOUT_TREE)
+        m = measure(wt, wl, sym, q, outs, max(3, min(args.steps, 5)), 3, wt.LAYOUT_TREE, overlap=args.overlap)
         phases, roof, kern = analyse(wl, q, m, max(3, min(args.steps, 5)))
         rec = {"workload": wl.describe(), "ms_per_step": m["ms"], "Mqps": Q / (m["ms"] * 1e-3) / 1e6,
                "queries_per_step": Q, "build_ms": phases["build_ms"], "build_GBps": phases["build_GBps"],

@@ -43,6 +43,7 @@ extern "C" {
 typedef struct CUstream_st* wt_stream; /* identical to cudaStream_t */
 typedef struct wt_tree_s* wt_tree;     /* opaque, owned by libwt, immutable after build */
 typedef struct wt_batch_s* wt_batch;   /* opaque: many trees built and queried by one graph launch */
+typedef struct wt_order_s* wt_order;   /* opaque: a query batch sorted by walk key (wt_order_queries) */
 
 typedef enum {
     WT_OK = 0,
@@ -193,6 +194,35 @@ wt_status wt_select(wt_tree tree, const uint32_t* d_c, const uint64_t* d_j, uint
  */
 wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_c, const uint64_t* d_arg,
                          uint64_t* d_out, uint64_t q, wt_stream stream);
+
+/*
+ * wt_order_queries / wt_walk_ordered / wt_order_destroy — the query calls
+ * above in two steps, so that the first can run on another stream while the
+ * build's level passes run (Sections 5.2-5.4: the walks; the ordering is this
+ * library's, see wt_access).
+ *  wt_order_queries: copy the batch (kind 0 access: d_arg = i; 1 rank: d_c,
+ *     d_arg = i; 2 select: d_c, d_arg = j; 3 mixed: d_kind, d_c, d_arg as in
+ *     wt_query_mixed) into arrays the order owns, sorted by where each walk
+ *     goes when the batch and the tree are large enough (the same rule as
+ *     wt_access).  It needs only the tree's header (n, sigma, C), which is
+ *     final when wt_build / wt_build_host return, so `stream` may be any
+ *     stream of the tree's device.  The input arrays may be reused once
+ *     `stream` has passed this call.  *out is null on error.  Trees of a batch
+ *     (wt_batch_tree) return WT_EUNSUPPORTED.
+ *  wt_walk_ordered: walk an order on `stream` (waiting for the order's
+ *     stream), writing answer k of the original batch to d_out[k]: uint32_t
+ *     for access, uint64_t otherwise; same answers, sentinels and status as
+ *     the one-step calls.  The tree must be the one the order was made for.
+ *  wt_order_destroy: release the order after the work queued on `stream`
+ *     (the stream of its last walk); the memory returns on the order's own
+ *     stream, which must still exist, after it waits for `stream`.
+ * Pointers: device memory of the current device.  Errors: WT_EINVAL for a
+ * bad tree, order, kind or pointer, WT_ENOMEM, WT_ECUDA.
+ */
+wt_status wt_order_queries(wt_tree tree, uint32_t kind, const uint8_t* d_kind, const uint32_t* d_c,
+                           const uint64_t* d_arg, uint64_t q, wt_stream stream, wt_order* out);
+wt_status wt_walk_ordered(wt_tree tree, wt_order order, void* d_out, wt_stream stream);
+wt_status wt_order_destroy(wt_order order, wt_stream stream);
 
 /*
  * wt_query_host — the end-to-end query path of Section 6 (queries copied in

@@ -33,8 +33,52 @@ EXPORTED = (
     "wt_profile_report", "wt_bitvector_support_static", "wt_train_select", "wt_select_learned", "wt_learned_info",
     "wt_mlp_gradient", "wt_batch_create", "wt_batch_set_queries", "wt_batch_run", "wt_batch_status_sync",
     "wt_batch_tree", "wt_batch_bytes", "wt_batch_destroy", "wt_selftest_lookback_timeout", "wt_bitvector_rank",
-    "wt_bitvector_select", "wt_alphabet",
+    "wt_bitvector_select", "wt_alphabet", "wt_order_queries", "wt_walk_ordered", "wt_order_destroy",
 )
+
+# wt_order_queries kinds
+ORDER_ACCESS, ORDER_RANK, ORDER_SELECT, ORDER_MIXED = 0, 1, 2, 3
+
+
+class Order:
+    """A query batch sorted by walk key (wt_order_queries); see Tree.order,
+    Tree.walk.  close(stream) releases it after the work queued on `stream`."""
+
+    def __init__(self, tree, kind, arg, c=None, kinds=None, stream=None):
+        import torch
+
+        if kind not in (ORDER_ACCESS, ORDER_RANK, ORDER_SELECT, ORDER_MIXED):
+            raise ValueError("kind must be one of ORDER_ACCESS, ORDER_RANK, ORDER_SELECT, ORDER_MIXED")
+        self.kind, self.q, self.device = kind, arg.numel(), arg.device
+        if kind != ORDER_ACCESS and (c is None or c.numel() != self.q):
+            raise ValueError("c must have arg's length")
+        if kind == ORDER_MIXED and (kinds is None or kinds.numel() != self.q or kinds.dtype != torch.uint8):
+            raise ValueError("kinds must be uint8 with arg's length")
+        self._stream = stream
+        h = ctypes.c_void_p()
+        dk = _dptr(kinds, "kinds") if kind == ORDER_MIXED and self.q else None
+        dc = _as_u32(c, "c") if kind != ORDER_ACCESS and self.q else None
+        da = _as_u64(arg, "arg") if self.q else None
+        _check(lib().wt_order_queries(tree._h, kind, dk, dc, da, self.q, _stream(stream), ctypes.byref(h)),
+               "wt_order_queries")
+        self._h = h.value
+
+    def close(self, stream=None):
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().wt_order_destroy(h, _stream(stream)), "wt_order_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class WTError(RuntimeError):
@@ -156,6 +200,9 @@ def lib():
         L.wt_rank.argtypes = [vp, vp, vp, vp, u64, vp]
         L.wt_select.argtypes = [vp, vp, vp, vp, u64, vp]
         L.wt_query_mixed.argtypes = [vp, vp, vp, vp, vp, u64, vp]
+        L.wt_order_queries.argtypes = [vp, u32, vp, vp, vp, u64, vp, ctypes.POINTER(vp)]
+        L.wt_walk_ordered.argtypes = [vp, vp, vp, vp]
+        L.wt_order_destroy.argtypes = [vp, vp]
         L.wt_query_host.argtypes = [vp, u32, vp, vp, vp, vp, u64, u64, vp]
         L.wt_status_sync.argtypes = [vp, vp]
         L.wt_info.argtypes = [vp, ctypes.POINTER(Info)]
@@ -346,6 +393,24 @@ class Tree:
         if q:
             _check(lib().wt_select(self._h, _as_u32(c, "c"), _as_u64(j, "j"), _dptr(out, "out"), q,
                                    _stream(stream)), "wt_select")
+        return out
+
+    def order(self, kind: int, arg, c=None, kinds=None, stream=None) -> "Order":
+        """wt_order_queries: the batch (ORDER_ACCESS: arg = i; ORDER_RANK: c, i;
+        ORDER_SELECT: c, j; ORDER_MIXED: kinds, c, arg) sorted by walk key into
+        arrays the order owns, on `stream` (may differ from the build's, so the
+        sort overlaps the level passes)."""
+        return Order(self, kind, arg, c, kinds, stream)
+
+    def walk(self, order: "Order", out=None, stream=None):
+        """wt_walk_ordered: the order's answers, in the batch's original order."""
+        import torch
+
+        if out is None:
+            out = torch.empty(order.q, dtype=torch.int32 if order.kind == ORDER_ACCESS else torch.int64,
+                              device=order.device)
+        if order.q:
+            _check(lib().wt_walk_ordered(self._h, order._h, _dptr(out, "out"), _stream(stream)), "wt_walk_ordered")
         return out
 
     def query_mixed(self, kind, c, arg, out=None, stream=None):

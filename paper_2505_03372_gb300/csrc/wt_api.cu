@@ -340,6 +340,82 @@ wt_status wt_query_mixed(wt_tree tree, const uint8_t* d_kind, const uint32_t* d_
 }
 
 // ---------------------------------------------------------------------------
+// ordering as a step of its own
+// ---------------------------------------------------------------------------
+
+constexpr uint64_t kOrderMagic = 0x5754474f52444552ull;
+
+struct wt_order_s {
+    uint64_t magic;
+    const wt_tree_s* tree;
+    uint32_t kind;
+    uint64_t q;
+    bool ord;             // sorted by walk key (else the batch as it was given)
+    Ordered o;
+    cudaEvent_t ready;    // recorded on `stream` after the arrays are written
+    cudaStream_t stream;  // the order's stream: its memory is taken and returned there
+    uint32_t has_alloc;
+    wt_allocator alloc;
+};
+
+wt_status wt_order_queries(wt_tree tree, uint32_t kind, const uint8_t* d_kind, const uint32_t* d_c,
+                           const uint64_t* d_arg, uint64_t q, wt_stream stream, wt_order* out) {
+    if (!out) return WT_EINVAL;
+    *out = nullptr;
+    if (!tree_ok(tree) || kind > 3) return WT_EINVAL;
+    if (tree->is_view) return WT_EUNSUPPORTED;
+    if (q && (!is_device_ptr(d_arg) || (kind >= 1 && !is_device_ptr(d_c)) || (kind == 3 && !is_device_ptr(d_kind))))
+        return WT_EINVAL;
+    wt_order_s* od = new wt_order_s();
+    od->magic = kOrderMagic;
+    od->tree = tree;
+    od->kind = kind;
+    od->q = q;
+    od->stream = stream;
+    od->has_alloc = tree->has_alloc;
+    od->alloc = tree->alloc;
+    wt_status st = q ? prepare_order(tree, kind, d_kind, d_c, d_arg, q, stream, od->o, od->ord) : WT_OK;
+    if (st == WT_OK && cudaEventCreateWithFlags(&od->ready, cudaEventDisableTiming) != cudaSuccess) st = WT_ECUDA;
+    if (st == WT_OK && cudaEventRecord(od->ready, stream) != cudaSuccess) st = WT_ECUDA;
+    if (st != WT_OK) {
+        if (od->o.mem) dev_free(od->o.mem, stream, od->has_alloc ? &od->alloc : nullptr);
+        if (od->ready) cudaEventDestroy(od->ready);
+        delete od;
+        return st;
+    }
+    *out = od;
+    return WT_OK;
+}
+
+wt_status wt_walk_ordered(wt_tree tree, wt_order order, void* d_out, wt_stream stream) {
+    if (!tree_ok(tree) || !order || order->magic != kOrderMagic || order->tree != tree) return WT_EINVAL;
+    if (!order->q) return WT_OK;
+    if (!is_device_ptr(d_out)) return WT_EINVAL;
+    if (cudaStreamWaitEvent(stream, order->ready, 0) != cudaSuccess) return WT_ECUDA;
+    return walk_prepared(tree, order->kind, order->ord, order->o, d_out, order->q, stream);
+}
+
+wt_status wt_order_destroy(wt_order order, wt_stream stream) {
+    if (!order || order->magic != kOrderMagic) return WT_EINVAL;
+    wt_status st = WT_OK;
+    if (order->o.mem) {
+        // the last walk may still read the arrays on `stream`: the order's stream
+        // waits for it, then the memory goes back where it was taken
+        cudaEvent_t done = nullptr;
+        if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(done, stream) != cudaSuccess || cudaStreamWaitEvent(order->stream, done, 0) != cudaSuccess)
+            st = WT_ECUDA;
+        if (done) cudaEventDestroy(done);
+        if (st != WT_OK) cudaStreamSynchronize(stream);  // no event: wait for the walk on the host instead
+        dev_free(order->o.mem, order->stream, order->has_alloc ? &order->alloc : nullptr);
+    }
+    cudaEventDestroy(order->ready);
+    order->magic = 0;
+    delete order;
+    return st;
+}
+
+// ---------------------------------------------------------------------------
 // host-resident query pipeline
 // ---------------------------------------------------------------------------
 

@@ -136,6 +136,12 @@ struct Ordered {
     uint32_t* idx = nullptr;
 };
 bool use_order(const wt_tree_s* t, uint64_t q);
+// the batch sorted by walk key (ord = true), or copied as it is (small batches), into o
+wt_status prepare_order(const wt_tree_s* t, uint32_t kind, const uint8_t* d_kind, const uint32_t* d_c,
+                        const uint64_t* d_a, uint64_t q, cudaStream_t s, Ordered& o, bool& ord);
+// the walk of a prepared batch: answer k of the original order lands in d_out[k]
+wt_status walk_prepared(const wt_tree_s* t, uint32_t kind, bool ord, const Ordered& o, void* d_out, uint64_t q,
+                        cudaStream_t s);
 // kindsel: 0 access, 1 rank, 2 select, 3 mixed (d_kind per query)
 wt_status order_queries(const wt_tree_s* t, uint32_t kindsel, const uint8_t* d_kind, const uint32_t* d_c,
                         const uint64_t* d_a, uint64_t q, cudaStream_t s, Ordered& o);

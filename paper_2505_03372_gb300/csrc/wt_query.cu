@@ -477,4 +477,55 @@ wt_status launch_mixed(const wt_tree_s* t, const uint8_t* d_kind, const uint32_t
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
+// ---------------------------------------------------------------------------
+// ordering as a step of its own (wt_order_queries / wt_walk_ordered): the
+// batch is sorted (or, below the ordering thresholds, copied) into private
+// arrays, so it can run on another stream while the build's level passes run
+// ---------------------------------------------------------------------------
+
+wt_status prepare_order(const wt_tree_s* t, uint32_t kind, const uint8_t* d_kind, const uint32_t* d_c,
+                        const uint64_t* d_a, uint64_t q, cudaStream_t s, Ordered& o, bool& ord) {
+    ord = use_order(t, q);
+    const uint32_t* c = kind >= 1 ? d_c : nullptr;
+    const uint8_t* k = kind == 3 ? d_kind : nullptr;
+    if (ord) return order_queries(t, kind, k, c, d_a, q, s, o);
+    auto al = [](uint64_t x) { return (x + 255) & ~255ull; };
+    const uint64_t off_c = al(q * 8), off_k = off_c + (c ? al(q * 4) : 0), total = off_k + (k ? al(q) : 0);
+    if (dev_alloc(&o.mem, total ? total : 256, s, tree_alloc(t)) != cudaSuccess) return WT_ENOMEM;
+    uint8_t* M = static_cast<uint8_t*>(o.mem);
+    o.a = reinterpret_cast<uint64_t*>(M);
+    o.c = c ? reinterpret_cast<uint32_t*>(M + off_c) : nullptr;
+    o.kind = k ? M + off_k : nullptr;
+    o.idx = nullptr;
+    cudaError_t e = cudaMemcpyAsync(o.a, d_a, q * 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && c) e = cudaMemcpyAsync(o.c, c, q * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && k) e = cudaMemcpyAsync(o.kind, k, q, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? WT_OK : WT_ECUDA;
+}
+
+wt_status walk_prepared(const wt_tree_s* t, uint32_t kind, bool ord, const Ordered& o, void* d_out, uint64_t q,
+                        cudaStream_t s) {
+    if (!q) return WT_OK;
+    if (kind == 0) {
+        ProfScope ps("access", s);
+        auto kfn = ord ? access_kernel<true> : access_kernel<false>;
+        WALK_LAUNCH(kfn, t, q, s, o.a, o.idx, static_cast<uint32_t*>(d_out));
+    } else if (kind == 1) {
+        ProfScope ps("rank", s);
+        auto kfn = ord ? rank_kernel<true> : rank_kernel<false>;
+        WALK_LAUNCH(kfn, t, q, s, o.c, o.a, o.idx, static_cast<uint64_t*>(d_out));
+    } else if (kind == 2) {
+        ProfScope ps("select", s);
+        const bool pair = pair_walks(t);
+        auto kfn = ord ? (pair ? select_kernel<true, 2> : select_kernel<true, 1>)
+                       : (pair ? select_kernel<false, 2> : select_kernel<false, 1>);
+        WALK_LAUNCH(kfn, t, q, s, o.c, o.a, o.idx, static_cast<uint64_t*>(d_out));
+    } else {
+        ProfScope ps("mixed", s);
+        auto kfn = ord ? mixed_kernel<true> : mixed_kernel<false>;
+        WALK_LAUNCH(kfn, t, q, s, o.kind, o.c, o.a, o.idx, static_cast<uint64_t*>(d_out));
+    }
+    return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
+}
+
 }  // namespace wt
