@@ -98,7 +98,8 @@ __device__ __forceinline__ void do_select_n(const TreeDesc& t, const NodeCache& 
         SelB s[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            on[q] = l < (int)len[q];
+            // a lone query walks from its own leaf level, so it is on every level of the loop
+            on[q] = NQ == 1 || l < (int)len[q];
             const uint32_t b = (code[q] >> (cp.L - 1 - (uint32_t)l)) & 1u;
             start[q] = ne[q].x;
             const uint64_t kb = b ? (start[q] - ne[q].y) : ne[q].y;  // b-bits before the node
