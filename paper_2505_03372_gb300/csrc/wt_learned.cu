@@ -556,7 +556,7 @@ __device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const Lea
         ushort4 r[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            on[q] = l < (int)len[q];
+            on[q] = NQ == 1 || l < (int)len[q];  // a lone query is on every level of the loop
             b[q] = (code[q] >> (cp.L - 1 - (uint32_t)l)) & 1u;
             start[q] = ne[q].x;
             // rank 1 of level l stands in for a query that is not on this level
