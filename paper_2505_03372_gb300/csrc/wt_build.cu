@@ -603,7 +603,7 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
 
     // ---- phase 1: level bits of every lane's 16 bytes -> shared memory ----
     const uint32_t shift = a.shift_bit;
-#pragma unroll 1
+#pragma unroll 2  // two groups in flight: 0.707 -> 0.702 ms per u8 pass (no unrolling: 0.707, four: 0.713)
     for (int gg = 0; gg < GPW; gg++) {
         const int g = warp * GPW + gg;
         uint4 V = in4[g * 32 + lane];
