@@ -527,7 +527,7 @@ __device__ __forceinline__ ulonglong2 node_entry_sr(const TreeDesc& t, uint32_t 
 // record, the model's prediction p, then the staged search of the binary
 // select (SelB) inside [p - eps, p + eps].  A query whose counters show the
 // bit outside its window falls back to the sampled select and is counted.
-template <int NQ>
+template <int NQ, uint32_t MODE>
 __device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const LearnedDesc& ld, const float* mlp_s,
                                                     const uint32_t (&c)[NQ], const uint64_t (&jin)[NQ],
                                                     const bool (&act)[NQ], uint64_t (&res)[NQ], uint32_t& fb) {
@@ -573,7 +573,7 @@ __device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const Lea
         for (int q = 0; q < NQ; q++) {
             int64_t R[kKnots];
             unpack_resid(r[q], ld.rsh[l][b[q]], R);
-            const uint64_t p = predict(ld.mode, g[q], R, k[q], mlp_s + (2 * l + b[q]) * kMlpParams, kl);
+            const uint64_t p = predict(MODE, g[q], R, k[q], mlp_s + (2 * l + b[q]) * kMlpParams, kl);
             const uint64_t e = (uint64_t)r[q].w << ld.esh[l][b[q]];
             const uint64_t hi = umin64(p + e, lv.size - 1);
             const uint64_t lo = umin64(p > e ? p - e : 0ull, hi);  // lo <= hi <= size - 1
@@ -617,12 +617,15 @@ constexpr int kLqThreads = 256;
 // one query per thread, 64 for two (a few spilled words cost less than the
 // fourth CTA per SM gains: 36.9 -> 35.4 ms for 10^8 PLA selects on a 16-level
 // tree).
-template <bool ORD, int NQ>
+// MODE (kLearnPla or kLearnMlp) is a template parameter: each model's walk
+// carries only its own prediction code, and the fitted-knot walk needs fewer
+// registers without the network's.
+template <bool ORD, int NQ, uint32_t MODE>
 __global__ void __launch_bounds__(kLqThreads, NQ == 1 ? 5 : 4) select_learned_kernel(
     const __grid_constant__ TreeDesc t, const __grid_constant__ LearnedDesc ld, const uint32_t* __restrict__ qc,
     const uint64_t* __restrict__ qj, const uint32_t* __restrict__ idx, uint64_t* __restrict__ out, uint64_t q) {
     extern __shared__ float mlp_s[];
-    if (ld.mode == kLearnMlp) {
+    if (MODE == kLearnMlp) {
         const uint32_t np = 2 * t.cp.L * kMlpParams;
         for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) mlp_s[i] = ld.mlp[i];
         __syncthreads();
@@ -643,7 +646,7 @@ __global__ void __launch_bounds__(kLqThreads, NQ == 1 ? 5 : 4) select_learned_ke
             ok[x] = in[x] && !bad[x];
             any_bad = any_bad || bad[x];
         }
-        do_select_learned_n<NQ>(t, ld, mlp_s, c, j, ok, r, fb);
+        do_select_learned_n<NQ, MODE>(t, ld, mlp_s, c, j, ok, r, fb);
 #pragma unroll
         for (int x = 0; x < NQ; x++)
             if (in[x]) out[ORD ? __ldg(idx + k0 + x) : k0 + x] = bad[x] ? UINT64_MAX : r[x];
@@ -848,37 +851,47 @@ wt_status train_select(wt_tree_s* t, uint32_t mode, uint32_t steps, float lr, ui
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
+using LearnedKernel = void (*)(TreeDesc, LearnedDesc, const uint32_t*, const uint64_t*, const uint32_t*, uint64_t*,
+                               uint64_t);
+
+static LearnedKernel learned_kernel(bool ord, bool pair, bool mlp) {
+    if (ord) {
+        if (pair) return mlp ? select_learned_kernel<true, 2, kLearnMlp> : select_learned_kernel<true, 2, kLearnPla>;
+        return mlp ? select_learned_kernel<true, 1, kLearnMlp> : select_learned_kernel<true, 1, kLearnPla>;
+    }
+    if (pair) return mlp ? select_learned_kernel<false, 2, kLearnMlp> : select_learned_kernel<false, 2, kLearnPla>;
+    return mlp ? select_learned_kernel<false, 1, kLearnMlp> : select_learned_kernel<false, 1, kLearnPla>;
+}
+
 wt_status launch_select_learned(const wt_tree_s* t, const uint32_t* d_c, const uint64_t* d_j, uint64_t* d_out,
                                 uint64_t q, cudaStream_t s) {
     if (!q) return WT_OK;
-    const size_t sm = t->learned.mode == kLearnMlp ? (size_t)2 * t->desc.cp.L * kMlpParams * 4 : 0;
+    const bool mlp = t->learned.mode == kLearnMlp;
+    const size_t sm = mlp ? (size_t)2 * t->desc.cp.L * kMlpParams * 4 : 0;
     const bool pair = t->desc.cp.L >= kPairLevels;
-    static int per_sm[2] = {0, 0};
-    if (!per_sm[pair]) {
+    static int per_sm[2][2] = {{0, 0}, {0, 0}};
+    if (!per_sm[pair][mlp]) {
         int v = 0;
-        if (pair) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, select_learned_kernel<false, 2>, kLqThreads, 20 * 1024);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, select_learned_kernel<false, 1>, kLqThreads, 20 * 1024);
-        per_sm[pair] = v > 0 ? v : 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, learned_kernel(false, pair, mlp), kLqThreads, 20 * 1024);
+        per_sm[pair][mlp] = v > 0 ? v : 1;
     }
-    uint64_t need = (q + kLqThreads - 1) / kLqThreads, full = (uint64_t)per_sm[pair] * sm_count();
+    uint64_t need = (q + kLqThreads - 1) / kLqThreads, full = (uint64_t)per_sm[pair][mlp] * sm_count();
     const unsigned grid = (unsigned)(need < full ? need : full);
-    const char* name = t->learned.mode == kLearnMlp ? "select_learned_mlp" : "select_learned_pla";
+    const char* name = mlp ? "select_learned_mlp" : "select_learned_pla";
     // large batches walk in the same order as the sampled select's
     if (use_order(t, q)) {
         Ordered o;
         wt_status st = order_queries(t, 2, nullptr, d_c, d_j, q, s, o);
         if (st == WT_OK) {
             ProfScope ps(name, s);
-            auto kfn = pair ? select_learned_kernel<true, 2> : select_learned_kernel<true, 1>;
-            kfn<<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, o.c, o.a, o.idx, d_out, q);
+            learned_kernel(true, pair, mlp)<<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, o.c, o.a, o.idx, d_out, q);
             if (cudaGetLastError() != cudaSuccess) st = WT_ECUDA;
         }
         if (o.mem) dev_free(o.mem, s, tree_alloc(t));
         return st;
     }
     ProfScope ps(name, s);
-    auto kfn = pair ? select_learned_kernel<false, 2> : select_learned_kernel<false, 1>;
-    kfn<<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, d_c, d_j, nullptr, d_out, q);
+    learned_kernel(false, pair, mlp)<<<grid, kLqThreads, sm, s>>>(t->desc, t->learned, d_c, d_j, nullptr, d_out, q);
     return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ECUDA;
 }
 
