@@ -81,11 +81,20 @@ __device__ __forceinline__ uint64_t interp(uint64_t ka, uint64_t kb, uint64_t xa
     return xa + (d == (1ull << kl) ? (prod >> kl) : prod / d);
 }
 
-// Fitted-knot prediction for rank k of segment g; R[t - 1] (bits) for knots t = 1..3.
+// Residual of knot t = 1..3 of a record, in bits.
+__device__ __forceinline__ int64_t resid(const ushort4 r, uint32_t rsh, uint32_t t) {
+    const uint16_t v = t == 1 ? r.x : (t == 2 ? r.y : r.z);
+    return (int64_t)(int16_t)v * (int64_t(1) << rsh);
+}
+
+// Fitted-knot prediction for rank k of segment g, record rec (residuals in
+// units of 2^rsh bits for knots t = 1..3).  Only the residuals of the two
+// knots around k are unpacked.
 // Knot positions are non-decreasing and inside [x0, x1] (the fit guarantees it).
 // The knots are quarters of the segment; the interpolation between the two
 // knots around k is exact integer arithmetic.
-__device__ __forceinline__ uint64_t predict_knots(const Seg& g, const int64_t R[kKnots], uint64_t k, uint32_t kl) {
+__device__ __forceinline__ uint64_t predict_knots(const Seg& g, const ushort4 rec, uint32_t rsh, uint64_t k,
+                                                  uint32_t kl) {
     if (g.k1 - g.k0 == (4ull << kl)) {
         // a full segment (all but the last of a level and b): knots K ranks
         // apart, so t = (k - k0) / K and the interpolation divides by K; the
@@ -93,10 +102,8 @@ __device__ __forceinline__ uint64_t predict_knots(const Seg& g, const int64_t R[
         const uint32_t off = (uint32_t)(k - g.k0);
         const uint32_t t = off >> kl;
         const uint64_t span = g.x1 - g.x0;
-        const int64_t ra = t == 1 ? R[0] : (t == 2 ? R[1] : R[2]);
-        const int64_t rb = t == 0 ? R[0] : (t == 1 ? R[1] : R[2]);
-        const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)(g.x0 + ((t * span) >> 2)) + ra);
-        const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)(g.x0 + (((t + 1) * span) >> 2)) + rb);
+        const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)(g.x0 + ((t * span) >> 2)) + resid(rec, rsh, t));
+        const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)(g.x0 + (((t + 1) * span) >> 2)) + resid(rec, rsh, t + 1));
         const uint64_t dx = xb - xa;
         const uint32_t dk = off & ((1u << kl) - 1u);  // k - ka < K
         const uint64_t prod = dx < (1ull << 32) ? (uint64_t)dk * (uint32_t)dx : (uint64_t)dk * dx;
@@ -107,11 +114,8 @@ __device__ __forceinline__ uint64_t predict_knots(const Seg& g, const int64_t R[
     const uint32_t t = (k >= k1r) + (k >= k2r) + (k >= k3r);
     const uint64_t ka = t == 0 ? g.k0 : (t == 1 ? k1r : (t == 2 ? k2r : k3r));
     const uint64_t kb = t == 0 ? k1r : (t == 1 ? k2r : (t == 2 ? k3r : g.k1));
-    // R indexed by selects (a computed index would put R in local memory)
-    const int64_t ra = t == 1 ? R[0] : (t == 2 ? R[1] : R[2]);
-    const int64_t rb = t == 0 ? R[0] : (t == 1 ? R[1] : R[2]);
-    const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)knot_base(g, t) + ra);
-    const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)knot_base(g, t + 1) + rb);
+    const uint64_t xa = t == 0 ? g.x0 : (uint64_t)((int64_t)knot_base(g, t) + resid(rec, rsh, t));
+    const uint64_t xb = t == 3 ? g.x1 : (uint64_t)((int64_t)knot_base(g, t + 1) + resid(rec, rsh, t + 1));
     return interp(ka, kb, xa, xb, k, kl);
 }
 
@@ -135,15 +139,9 @@ __device__ __forceinline__ uint64_t predict_mlp(const Seg& g, uint64_t k, const 
     return g.x0 + (off < span ? off : span);
 }
 
-__device__ __forceinline__ void unpack_resid(const ushort4 r, uint32_t rsh, int64_t R[kKnots]) {
-    R[0] = (int64_t)(int16_t)r.x * (int64_t(1) << rsh);
-    R[1] = (int64_t)(int16_t)r.y * (int64_t(1) << rsh);
-    R[2] = (int64_t)(int16_t)r.z * (int64_t(1) << rsh);
-}
-
-__device__ __forceinline__ uint64_t predict(uint32_t mode, const Seg& g, const int64_t R[kKnots], uint64_t k,
+__device__ __forceinline__ uint64_t predict(uint32_t mode, const Seg& g, const ushort4 rec, uint32_t rsh, uint64_t k,
                                             const float* P, uint32_t kl) {
-    return mode == kLearnMlp ? predict_mlp(g, k, P) : predict_knots(g, R, k, kl);
+    return mode == kLearnMlp ? predict_mlp(g, k, P) : predict_knots(g, rec, rsh, k, kl);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,7 +342,7 @@ __global__ void __launch_bounds__(256) learn_scan_kernel(const __grid_constant__
             uint64_t cur_m = ~0ull;
             uint32_t cur_max = 0;
             Seg g = {0, 1, 0, 0};
-            int64_t R[kKnots] = {0, 0, 0};
+            ushort4 rec = make_ushort4(0, 0, 0, 0);  // R = 0: the line through the anchors
             const float* P = a.P[b];
 #pragma unroll 1
             for (uint32_t w = 0; w < 8; w++) {
@@ -368,10 +366,10 @@ __global__ void __launch_bounds__(256) learn_scan_kernel(const __grid_constant__
                         cur_m = m;
                         cur_max = 0;
                         g = anchor_seg(lv, b, m, a.kl);
-                        if (a.mode == kLearnPla && a.rec[b]) unpack_resid(a.rec[b][m], a.rsh[b], R);
+                        if (a.mode == kLearnPla && a.rec[b]) rec = a.rec[b][m];
                     }
                     if (a.eps[b]) {
-                        const uint64_t pr = predict(a.mode, g, R, k, P, a.kl);
+                        const uint64_t pr = predict(a.mode, g, rec, a.rsh[b], k, P, a.kl);
                         const uint64_t e = pr > pos ? pr - pos : pos - pr;
                         const uint32_t e32 = e > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)e;
                         cur_max = e32 > cur_max ? e32 : cur_max;
@@ -571,9 +569,7 @@ __device__ __forceinline__ void do_select_learned_n(const TreeDesc& t, const Lea
         SelB s[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            int64_t R[kKnots];
-            unpack_resid(r[q], ld.rsh[l][b[q]], R);
-            const uint64_t p = predict(MODE, g[q], R, k[q], mlp_s + (2 * l + b[q]) * kMlpParams, kl);
+            const uint64_t p = predict(MODE, g[q], r[q], ld.rsh[l][b[q]], k[q], mlp_s + (2 * l + b[q]) * kMlpParams, kl);
             const uint64_t e = (uint64_t)r[q].w << ld.esh[l][b[q]];
             const uint64_t hi = umin64(p + e, lv.size - 1);
             const uint64_t lo = umin64(p > e ? p - e : 0ull, hi);  // lo <= hi <= size - 1
