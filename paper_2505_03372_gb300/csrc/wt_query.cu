@@ -155,8 +155,11 @@ constexpr uint32_t kKeyBits = 16;
 constexpr uint32_t kOrdBuckets = 256;
 constexpr uint32_t kOrdThreads = 512;
 constexpr uint32_t kOrdWarps = kOrdThreads / 32;
-constexpr uint32_t kOrdPer = 8;
-constexpr uint32_t kChunk = kOrdThreads * kOrdPer;  // queries per CTA; warp w owns [256 w, 256 w + 256)
+// 2048 queries per chunk: the scatter writes runs of about 8 queries per
+// bucket.  Chunks of 4096 were slower (scatter 0.139 against 0.122 ms per 10^7
+// queries), and so were 1024 (more histogram and scan work) and 8192.
+constexpr uint32_t kOrdPer = 4;
+constexpr uint32_t kChunk = kOrdThreads * kOrdPer;  // queries per CTA; warp w owns [128 w, 128 w + 128)
 constexpr uint64_t kOrderMinQueries = 1ull << 16;
 constexpr size_t kOrderMinTreeBytes = (size_t)64 << 20;
 
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(kOrdThreads) order_hist_kernel(const __grid_co
 // warps are then prefix-summed), giving the chunk's permutation; the queries
 // are then copied out in permuted order (their second read hits L1), so
 // consecutive threads write consecutive slots of one bucket's run.
-__global__ void __launch_bounds__(kOrdThreads, 3) order_scatter_kernel(const __grid_constant__ TreeDesc t, OrderKey ok,
+__global__ void __launch_bounds__(kOrdThreads, 4) order_scatter_kernel(const __grid_constant__ TreeDesc t, OrderKey ok,
                                                                        OrdIn in, uint64_t q, uint32_t shift,
                                                                        const uint64_t* __restrict__ offs,
                                                                        uint64_t nchunks, OrdOut out) {
