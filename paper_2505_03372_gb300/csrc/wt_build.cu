@@ -450,6 +450,7 @@ __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V,
                                               uint32_t j0, uint32_t count, uint32_t shift) {
     constexpr int W = sizeof(T);
     constexpr int EPW = 4 / W;
+    constexpr uint32_t SC = ABS ? W : 1;  // slot unit: bytes when ABS, elements otherwise
     const uint32_t wv[4] = {V.x, V.y, V.z, V.w};
     const uint32_t A0x2 = A0 * 0x00010001u, A1x2 = A1 * 0x00010001u;
 #pragma unroll
@@ -458,8 +459,8 @@ __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V,
         const uint32_t jw = j0 + i * EPW;
         // ones among the lane's earlier words
         const uint32_t ci = (i == 0) ? 0u : __popc(m & ((1u << (i * EPW)) - 1u));
-        const uint32_t b1 = A1x2 + ci * 0x00010001u;                                 // one-slot base, paired
-        const uint32_t b0 = (A0x2 + (uint32_t)(i * EPW) * 0x00010001u) - ci * 0x00010001u;  // zero-slot base, paired
+        const uint32_t b1 = A1x2 + ci * (SC * 0x00010001u);                                     // one-slot base, paired
+        const uint32_t b0 = (A0x2 + (uint32_t)(i * EPW * SC) * 0x00010001u) - ci * (SC * 0x00010001u);  // zero-slot base
         if (W == 1) {
             // bytes of y: level bits of the word's 4 elements; pre: ones before each element
             const uint32_t y = (w >> shift) & 0x01010101u;
@@ -478,13 +479,13 @@ __device__ __forceinline__ void scatter_group(const uint32_t out, const uint4 V,
             const uint32_t bb = (m >> (2 * i)) & 3u;
             const uint32_t sel = (bb & 1u ? 0x0000FFFFu : 0u) | (bb & 2u ? 0xFFFF0000u : 0u);
             // second element: ones before it if it is a one, zeros before it otherwise
-            const uint32_t off = ((bb ^ (bb >> 1)) & 1u) ? 0u : 0x00010000u;
+            const uint32_t off = ((bb ^ (bb >> 1)) & 1u) ? 0u : (SC << 16);
             const uint32_t I = ((b1 & sel) | (b0 & ~sel)) + off;
-            if (FULL || jw + 0 < count) sts_b16(out + 2 * (I & 0xFFFFu), w);
-            if (FULL || jw + 1 < count) sts_b16(out + 2 * (I >> 16), w >> 16);
+            if (FULL || jw + 0 < count) sts_b16(ABS ? (I & 0xFFFFu) : out + 2 * (I & 0xFFFFu), w);
+            if (FULL || jw + 1 < count) sts_b16(ABS ? (I >> 16) : out + 2 * (I >> 16), w >> 16);
         } else {
             const uint32_t bit = (m >> i) & 1u;
-            if (FULL || jw < count) sts_b32(out + 4 * ((bit ? b1 : b0) & 0xFFFFu), w);
+            if (FULL || jw < count) sts_b32(ABS ? ((bit ? b1 : b0) & 0xFFFFu) : out + 4 * ((bit ? b1 : b0) & 0xFFFFu), w);
         }
     }
 }
@@ -773,7 +774,9 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
         // every warp partitions its own GPW groups, two at a time: one scan of
         // the lanes' one counts (16-bit halves) serves both groups
         const uint16_t* m16 = reinterpret_cast<const uint16_t*>(wbytes);
-        const bool abs_ok = W == 1 && out_s + kTileBytes <= 65536u;
+        // slots as shared byte addresses (bytes and half-words): the image sits
+        // first, so they fit the 16-bit halves of a pair
+        const bool abs_ok = W <= 2 && out_s + kTileBytes <= 65536u;
 #pragma unroll 1
         for (int pr = 0; pr < GPW / 2; pr++) {
             const int g = warp * GPW + 2 * pr;
@@ -811,8 +814,8 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             const uint32_t ja = g * GE + lane * VEPL, jb = ja + GE;
             const uint4 Va = in4[g * 32 + lane], Vb = in4[(g + 1) * 32 + lane];
             if (full && abs_ok) {
-                scatter_group<T, true, true>(out_s, Va, ma, out_s + ja - oba, out_s + Z + oba, ja, count, shift);
-                scatter_group<T, true, true>(out_s, Vb, mb, out_s + jb - obb, out_s + Z + obb, jb, count, shift);
+                scatter_group<T, true, true>(out_s, Va, ma, out_s + W * (ja - oba), out_s + W * (Z + oba), ja, count, shift);
+                scatter_group<T, true, true>(out_s, Vb, mb, out_s + W * (jb - obb), out_s + W * (Z + obb), jb, count, shift);
             } else if (full) {
                 scatter_group<T, true>(out_s, Va, ma, ja - oba, Z + oba, ja, count, shift);
                 scatter_group<T, true>(out_s, Vb, mb, jb - obb, Z + obb, jb, count, shift);
