@@ -774,9 +774,9 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
         // every warp partitions its own GPW groups, two at a time: one scan of
         // the lanes' one counts (16-bit halves) serves both groups
         const uint16_t* m16 = reinterpret_cast<const uint16_t*>(wbytes);
-        // slots as shared byte addresses (bytes and half-words): the image sits
-        // first, so they fit the 16-bit halves of a pair
-        const bool abs_ok = W <= 2 && out_s + kTileBytes <= 65536u;
+        // slots as shared byte addresses: the image sits first in shared
+        // memory, so they fit the 16-bit halves of a pair
+        const bool abs_ok = out_s + kTileBytes <= 65536u;
 #pragma unroll 1
         for (int pr = 0; pr < GPW / 2; pr++) {
             const int g = warp * GPW + 2 * pr;
