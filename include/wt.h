@@ -54,8 +54,10 @@ typedef enum {
     WT_EQUERY = 5,      /* some query argument was out of range; that output holds a sentinel */
     WT_ETIMEOUT = 6,    /* a bounded device-side wait gave up; results of that call are not valid */
     WT_EUNSUPPORTED = 7, /* operation not available for this tree (e.g. no trained select model) */
-    WT_EBOUNDS = 8      /* debug library only (libwt_debug.so): a query walk's load failed its
-                           bounds check and was skipped; results of that call are not valid */
+    WT_EBOUNDS = 8      /* a bounds check failed and the access was skipped; results of that
+                           call are not valid.  Query walks check every load in the debug
+                           library (libwt_debug.so) only; the build checks its node-table
+                           lookups in both libraries */
 } wt_status;
 
 /*

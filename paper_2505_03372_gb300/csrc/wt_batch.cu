@@ -332,6 +332,7 @@ wt_status wt_batch_create(uint32_t ntrees, const void* const* h_symbols, const u
             a.level = l;
             a.shift_bit = L - 1 - l;
             a.pshift = L - l;
+            a.level_nodes = 1ull << l;
             a.k_log2 = kl;
             a.ctab_n = 0;
             a.cp = cps[i];

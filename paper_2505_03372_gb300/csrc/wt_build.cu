@@ -927,6 +927,14 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
     const bool cnt_next = a.next_cnt != nullptr;
     const uint32_t nsh = a.shift_bit - 1;  // bit of level l + 1 (valid when cnt_next)
     auto next_ones = [&](uint32_t x) { return (uint32_t)__popc((x >> nsh) & LOWB); };
+    // A node index comes from an element's code prefix, which the build keeps
+    // below the level's node count; a tile whose prefix is not (a corrupted
+    // T_l) sets WT_EBOUNDS and skips its write-out instead of reading past
+    // the node table.
+    if (s_single != 0 && s_p >= a.level_nodes) {
+        if (tid == 0) set_status(a.status, kStBounds);
+        return used_mbar;
+    }
     if (s_single != 0) {
         // two contiguous runs: zeros to off0 + R0, ones to off1 + E.  Global 4-byte
         // words are assembled from two shared words with a funnel shift.
@@ -1007,18 +1015,24 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
             const uint32_t c = __popc(__ballot_sync(am, bit) & grp);
             if (lane == __ffs(grp) - 1 && c) atomicAdd(a.next_cnt + tl, (unsigned long long)c);
         };
+        bool bad_node = false;
         for (uint32_t i = tid; i < zeros; i += kLpThreads) {
             const T x = out[i];
-            const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off0) + R0 + i;
+            const uint64_t nd = (uint64_t)x >> ps;
+            bad_node |= nd >= a.level_nodes;
+            const uint64_t Dx = nd < a.level_nodes ? __ldg(&a.nodes[nd].off0) + R0 + i : lim;
             if (Dx < lim) dst[Dx] = x;
             if (cnt_next) count_multi(x, Dx);
         }
         for (uint32_t i = tid; i < ones; i += kLpThreads) {
             const T x = out[Z + i];
-            const uint64_t Dx = __ldg(&a.nodes[(uint64_t)x >> ps].off1) + E + i;
+            const uint64_t nd = (uint64_t)x >> ps;
+            bad_node |= nd >= a.level_nodes;
+            const uint64_t Dx = nd < a.level_nodes ? __ldg(&a.nodes[nd].off1) + E + i : lim;
             if (Dx < lim) dst[Dx] = x;
             if (cnt_next) count_multi(x, Dx);
         }
+        if (bad_node) set_status(a.status, kStBounds);
     }
     return used_mbar;
 }
@@ -1429,6 +1443,7 @@ wt_status build_tree(const void* d_symbols, uint64_t n, uint32_t sigma, uint32_t
             a.level = l;
             a.shift_bit = L - 1 - l;
             a.pshift = matrix ? 32 : L - l;  // the matrix: every tile lies in the level's one node
+            a.level_nodes = matrix ? 1 : (1ull << l);
             a.k_log2 = k_log2;
             a.cp = cp;
             // level 0 re-encodes bytes of a small alphabet with few segments

@@ -212,6 +212,7 @@ struct LevelPassArgs {
     uint32_t shift_bit;  // L - 1 - l
     uint32_t pshift;     // L - l (prefix = code >> pshift), unused at level 0
     uint32_t k_log2;
+    uint64_t level_nodes;  // entries of the level's node-table slice: every element's code prefix is below it
     uint32_t ctab_n;     // level 0 re-encoding: table size (0 = compute codes arithmetically)
     uint32_t swar_codes; // level 0, bytes: codes by per-segment SWAR arithmetic (sigma <= 128, <= 3 segments)
     CodeParams cp;       // used when re-encoding at level 0
