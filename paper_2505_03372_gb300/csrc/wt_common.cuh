@@ -297,8 +297,35 @@ __device__ __forceinline__ T ld_chk(const T* p, uint64_t i, uint64_t n, uint32_t
 
 // Binary rank_1 (Algorithm 1 with 64-bit words): ones in B_l[0, pos), and the
 // bit at pos (needed by access, returned with the rank as in Section 5.2.1).
-// Reads the L1 and L2 counters and the words of pos's 512-bit block up to pos.
+// Reads the L1 and L2 counters and the words of pos's 512-bit block up to pos;
+// counts the half holding pos by three popcounts and a select, the other half
+// (if before pos) by four.
 __device__ __forceinline__ uint64_t rank1_bit(const LevelDesc& lv, uint64_t pos, uint32_t& bit) {
+    const uint64_t blk = pos >> 9;
+    const uint32_t wi = (uint32_t)(pos >> 6) & 7u;
+    const uint32_t bi = (uint32_t)pos & 63u;
+    const bool second = wi >= 4;  // pos lies in the block's second 32-byte half
+    uint64_t a0, a1, a2, a3, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    ld_words4(lv, blk << 3, a0, a1, a2, a3);  // 64-byte aligned block
+    if (second) ld_words4(lv, (blk << 3) + 4, b0, b1, b2, b3);
+    const uint64_t r = ld_chk(lv.l1, pos >> 16, lv_nl1(lv), lv.status) + (uint64_t)ld_chk(lv.l2, blk, lv_nl2(lv), lv.status);
+    // ones of the first half if pos is past it, then the full words of pos's
+    // half before pos's word, then pos's word below bit bi
+    const uint32_t first = second ? __popcll(a0) + __popcll(a1) + __popcll(a2) + __popcll(a3) : 0u;
+    const uint64_t x0 = second ? b0 : a0, x1 = second ? b1 : a1, x2 = second ? b2 : a2, x3 = second ? b3 : a3;
+    const uint32_t q = wi & 3u;
+    const uint32_t before = (q > 0 ? (uint32_t)__popcll(x0) : 0u) + (q > 1 ? (uint32_t)__popcll(x1) : 0u) +
+                            (q > 2 ? (uint32_t)__popcll(x2) : 0u);
+    const uint64_t xq = q == 0 ? x0 : (q == 1 ? x1 : (q == 2 ? x2 : x3));
+    bit = (uint32_t)(xq >> bi) & 1u;
+    return r + first + before + (uint32_t)__popcll(xq & ((1ull << bi) - 1ull));
+}
+
+// rank_1 alone (rank walks, bitvector rank): one masked popcount per word of
+// the block, which measured faster than rank1_bit's form when the bit is not
+// needed (text rank walk 0.61 against 0.68 ms per 10^7); access, which needs
+// the bit, is faster with rank1_bit's (0.70 -> 0.53 ms)
+__device__ __forceinline__ uint64_t rank1(const LevelDesc& lv, uint64_t pos) {
     const uint64_t blk = pos >> 9;
     const uint32_t wi = (uint32_t)(pos >> 6) & 7u;
     const uint32_t bi = (uint32_t)pos & 63u;
@@ -306,23 +333,14 @@ __device__ __forceinline__ uint64_t rank1_bit(const LevelDesc& lv, uint64_t pos,
     ld_words4(lv, blk << 3, w[0], w[1], w[2], w[3]);  // 64-byte aligned block
     w[4] = w[5] = w[6] = w[7] = 0;
     if (wi >= 4) ld_words4(lv, (blk << 3) + 4, w[4], w[5], w[6], w[7]);
-    uint64_t r = ld_chk(lv.l1, pos >> 16, lv_nl1(lv), lv.status) + (uint64_t)ld_chk(lv.l2, blk, lv_nl2(lv), lv.status);
+    const uint64_t r = ld_chk(lv.l1, pos >> 16, lv_nl1(lv), lv.status) + (uint64_t)ld_chk(lv.l2, blk, lv_nl2(lv), lv.status);
     uint32_t c = 0;
 #pragma unroll
     for (uint32_t k = 0; k < 8; k++) {
-        uint64_t m = k < wi ? ~0ull : (k == wi ? ((1ull << bi) - 1ull) : 0ull);
+        const uint64_t m = k < wi ? ~0ull : (k == wi ? ((1ull << bi) - 1ull) : 0ull);
         c += __popcll(w[k] & m);
     }
-    uint64_t cur = w[0];
-#pragma unroll
-    for (uint32_t k = 1; k < 8; k++) cur = (k == wi) ? w[k] : cur;
-    bit = (uint32_t)(cur >> bi) & 1u;
     return r + c;
-}
-
-__device__ __forceinline__ uint64_t rank1(const LevelDesc& lv, uint64_t pos) {
-    uint32_t b;
-    return rank1_bit(lv, pos, b);
 }
 
 __device__ __forceinline__ uint32_t bit_at(const LevelDesc& lv, uint64_t pos) {
