@@ -206,6 +206,8 @@ struct LevelPassArgs {
     uint64_t* state;         // ntiles look-back words, zeroed (used when tile_excl is null)
     const uint64_t* tile_excl;           // ones of T_l before each tile (ntiles + 1), or null: look-back
     unsigned long long* next_cnt;        // ones of T_{l+1} per tile of T_{l+1}, zeroed; or null
+    uint64_t* words2;  // level l+1's words (zeroed) when this pass also writes level l+1's bits
+                       // (the level before the last; dst is then null), else null
     uint32_t* counter;       // tile counter, zeroed
     uint32_t* status;
     uint32_t level;
