@@ -722,22 +722,27 @@ def _e2e(args, wl, sym, q, outs, step, barrier, dist, world, Q):
                 t.query_host(3, h_q["mixed_arg"], c=h_q["mixed_c"], kinds=h_q["mixed_kind"], out=h_out["mixed"])
             t.close()
 
-    run(2)
-    torch.cuda.synchronize()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    run(args.steps)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
-    ms = job_ms(e0.elapsed_time(e1) / args.steps, dist)
+    run(max(args.warmup, 3))
+    # three windows of the timed steps, the median reported: the host side of
+    # this leg varies between windows far more than the device work does
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        runs.append(job_ms(e0.elapsed_time(e1) / args.steps, dist))
+    ms = statistics.median(runs)
     # the answers of the last step, checked against the device-resident run
     for k in h_out:
         if not torch.equal(h_out[k], outs[k].cpu()):
             raise RuntimeError(f"e2e answers differ from the device-resident run ({k})")
-    return {"value": job_value(world, Q, ms), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h,
+    return {"value": job_value(world, Q, ms), "unit": UNIT, "ms_per_step": ms, "ms_per_step_windows": runs,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "path": "pinned host symbols -> wt_build_host (64 MiB chunks copied while the histogram runs; the "
                     "next step's copy overlaps this step's passes) ; pinned host queries -> wt_query_host (chunked "
                     "H2D, walk, D2H on two copy streams) -> pinned host answers"}
