@@ -142,6 +142,15 @@ CASES = [
     (50000, 5, 4, "uniform", 256),
     (100001, (1 << 20) - 3, 4, "uniform", 1024),
     (262144, 1 << 20, 4, "uniform", 4096),
+    # the level before the last also writes the last level's bits (its nodes
+    # average 16 tiles or more): every width, level 0 re-encoding or not,
+    # tiles that span two nodes, ragged ends
+    (300001, 3, 1, "uniform", 256),       # u8, L = 2: level 0 re-encodes and folds
+    (600001, 7, 1, "uniform", 256),       # u8, L = 3: folds at level 1
+    (300001, 4, 2, "uniform", 256),       # u16, L = 2
+    (300001, 6, 2, "uniform", 512),       # u16, L = 3
+    (150001, 4, 4, "uniform", 256),       # u32, L = 2
+    (200003, 6, 4, "uniform", 256),       # u32, L = 3
 ]
 
 
