@@ -625,19 +625,35 @@ __device__ __forceinline__ bool level_pass_tile(const LevelPassArgs& a, const ui
                 const uint32_t add = ((1u << i) - 1u) << (L - i);
                 return ((x & (((1u << e) - 1u) * 0x01010101u)) << (L - len)) + add * 0x01010101u;
             };
+            if (r == 2) {
+                // two segments, [0, 2^e0) and [2^e0, sigma): the codes are s and
+                // 2^e0 + ((s & (2^e1 - 1)) << (e0 - e1)), and bit e0 of s tells
+                // the segment (no sum carries out of a byte)
+                const uint32_t e0 = a.cp.e[0], e1 = a.cp.e[1];
+                const uint32_t bmask = ((1u << e1) - 1u) * 0x01010101u;
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const uint32_t x = wv[i];
-                uint32_t code = seg(x, 0);
-#pragma unroll
-                for (uint32_t k = 1; k < 3; k++) {
-                    if (k < r) {
-                        const uint32_t g = (x + (128u - (uint32_t)a.cp.P[k]) * 0x01010101u) & 0x80808080u;
-                        const uint32_t m = (g >> 7) * 0xFFu;
-                        code = (code & ~m) | (seg(x, k) & m);
-                    }
+                for (int i = 0; i < 4; i++) {
+                    const uint32_t x = wv[i];
+                    const uint32_t hi = (x >> e0) & 0x01010101u;
+                    const uint32_t m = hi * 0xFFu;
+                    const uint32_t c1 = ((x & bmask) << (e0 - e1)) + (hi << e0);
+                    wv[i] = (x & ~m) | (c1 & m);
                 }
-                wv[i] = code;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const uint32_t x = wv[i];
+                    uint32_t code = seg(x, 0);
+#pragma unroll
+                    for (uint32_t k = 1; k < 3; k++) {
+                        if (k < r) {
+                            const uint32_t g = (x + (128u - (uint32_t)a.cp.P[k]) * 0x01010101u) & 0x80808080u;
+                            const uint32_t m = (g >> 7) * 0xFFu;
+                            code = (code & ~m) | (seg(x, k) & m);
+                        }
+                    }
+                    wv[i] = code;
+                }
             }
             in4[g * 32 + lane] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         } else if (ENCODE && W == 1 && a.ctab_n == 256) {
